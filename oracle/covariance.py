@@ -1,0 +1,38 @@
+"""Particle covariance, its regularisation and Cholesky factor (App. A: one
+Gaussian covariance estimated from the particle population at every outer step).
+
+Test infrastructure (see ``oracle/__init__``).
+
+Reading where the paper is silent: the covariance is the unweighted sample
+covariance of the (already resampled) population with divisor N - 1; a ridge
+delta * I with delta = jitter_rel * trace / D is added before factorising, and
+the ridge is multiplied by 10 (up to ``max_tries`` times) while the matrix is
+not numerically positive definite.
+"""
+import numpy as np
+
+
+def sample_covariance(X):
+    """mean and Sigma = Xc^T Xc / (N - 1) with Xc = X - mean (rows are particles)."""
+    X = np.asarray(X, dtype=np.float64)
+    n = X.shape[0]
+    mu = X.mean(axis=0)
+    Xc = X - mu
+    return mu, (Xc.T @ Xc) / (n - 1)
+
+
+def cholesky_lower(A):
+    """Lower factor of A = L L^T (library routine; raises LinAlgError when not PD)."""
+    return np.linalg.cholesky(np.asarray(A, dtype=np.float64))
+
+
+def regularised_cholesky(Sigma, jitter_rel=1e-8, max_tries=6):
+    """Returns (L, delta, tries) with L L^T = Sigma + delta I."""
+    D = Sigma.shape[0]
+    delta = jitter_rel * np.trace(Sigma) / D
+    for tries in range(1, max_tries + 1):
+        try:
+            return cholesky_lower(Sigma + delta * np.eye(D)), delta, tries
+        except np.linalg.LinAlgError:
+            delta *= 10.0
+    raise np.linalg.LinAlgError("covariance not positive definite after %d ridge increases" % max_tries)

@@ -1,0 +1,41 @@
+"""Pins for the nested-sampling oracle: the exact prior bracket, evidence on
+one site against quadrature and the error bar against the spread."""
+import math
+
+import numpy as np
+import pytest
+
+import closed_forms as cf
+import inputs
+from oracle import ns
+
+
+def test_prior_bracket_roots():
+    g = inputs.rng(1)
+    for _ in range(20):
+        x, d = g.standard_normal(6), g.standard_normal(6)
+        E = float(g.exponential())
+        lo, hi = ns.prior_bracket(x, d, E)
+        assert lo < 0 < hi
+        for t in (lo, hi):
+            assert np.dot(x + t * d, x + t * d) == pytest.approx(np.dot(x, x) + 2 * E, rel=1e-10)
+
+
+def test_one_site_evidence_and_error_bar():
+    ref = cf.one_site_logz(-4.0, 8.0)
+    res = [ns.NS(ns.NSConfig(L=1, N=64, m2=-4.0, lam=8.0, n_delete=32, seed=s)).run() for s in range(4)]
+    lz = np.array([r["logz"] for r in res])
+    err = np.mean([r["logz_err"] for r in res])
+    assert abs(lz.mean() - ref) < 4.0 * err / math.sqrt(len(lz)) + 0.02
+    assert 0.02 < err < 0.5
+    assert all(r["capped"] == 0 for r in res)
+
+
+def test_volume_bookkeeping_single_deletion():
+    s = ns.NS(ns.NSConfig(L=1, N=16, m2=-4.0, lam=8.0, n_delete=1, seed=2))
+    for _ in range(10):
+        s.replace_step()
+    # each single deletion shrinks log X by exactly 1/N
+    assert s.logX == pytest.approx(-10.0 / 16, rel=1e-14)
+    w = np.exp(np.array(s.dead_logw))
+    assert w.sum() == pytest.approx(1.0 - math.exp(s.logX), rel=1e-12)
