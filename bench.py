@@ -1,0 +1,350 @@
+"""Benchmark of the SMC temperature step on GB300.
+
+Workload (default): adaptive tempered SMC with random-walk moves on the broken
+phase of lattice phi^4, L = 64 (D = 4096 sites), N = 8192 particles, m2 = -4,
+lambda = 8, 20 Metropolis sweeps per temperature, target ESS 0.5 N, proposal and
+covariance GEMMs on the tcgen05 tensor cores in bf16 with fp32 accumulation,
+FP64 Cholesky, acceptance test and compensated log Z.
+
+One step = one temperature: ESS bisection and reweighting, systematic
+resampling, particle gather, covariance, Cholesky, 20 x (normals, proposal GEMM,
+stencil accept). Metric: site updates per second = N * D * n_mcmc per step over
+the whole step's device time (K steps timed with CUDA events on the run's stream,
+barrier + synchronize on both sides, max over ranks). The state (fields,
+proposals, normals: about 320 MiB per sweep) is larger than L2, so no flush is
+needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp32|fp64]
+  python bench.py --impl reference     # the FP64 CPU oracle on a bounded sample
+
+With --gpus N > 1 (torchrun) each rank advances its own independent replica
+(the sampler has no data-parallel exchange at this size: "replicas only").
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PREC = {"mixed": 2, "fp32": 1, "fp64": 0}
+PREC_DTYPE = {"mixed": "bf16-gemm/fp32-state/fp64-accept", "fp32": "fp32 (fp64 log Z)", "fp64": "fp64"}
+METRIC = "site-updates/s in mutation; time-to-logZ(±0.05) mixed vs FP32 at L=64, 1 GB300"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=list(PREC))
+    ap.add_argument("--L", type=int, default=64)
+    ap.add_argument("--N", type=int, default=8192)
+    ap.add_argument("--n-mcmc", type=int, default=20)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=256, help="particles in the oracle's bounded sample")
+    return ap.parse_args()
+
+
+def workload(a):
+    D = a.L * a.L
+    return {"workload": "SMC-RW tempering step, broken-phase phi^4 L=%d (D=%d), N=%d, m2=-4, lambda=8, "
+                        "%d RWM sweeps/temperature, ESS 0.5N, %s" % (a.L, D, a.N, a.n_mcmc, a.precision),
+            "L": a.L, "D": D, "N": a.N, "n_mcmc": a.n_mcmc, "m2": -4.0, "lambda": 8.0, "ess_target": 0.5,
+            "precision": a.precision,
+            "l2": "inputs larger than L2 (fields %d MiB + proposals + normals per sweep)" % (a.N * D * 4 >> 20)}
+
+
+def dist_setup(a):
+    if a.gpus <= 1 and "WORLD_SIZE" not in os.environ:
+        return 0, 1, None
+    import torch.distributed as dist
+    dist.init_process_group("gloo")
+    return dist.get_rank(), dist.get_world_size(), dist
+
+
+def max_over_ranks(x, dist):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.f is None:
+            return None
+        try:
+            rows = [l.strip().split(", ") for l in open(self.f.name) if l.strip()]
+            os.unlink(self.f.name)
+        except Exception:
+            return None
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        if not sm:
+            return None
+        mx = max(float(r[2]) for r in rows if len(r) >= 9 and r[2].replace(".", "").isdigit())
+        load = [x for x in sm if x > 0.5 * mx] or sm
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for k, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(k)
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6786.6), d.get("bf16_tflops", 1897.7), d.get("bf16_tflops_sustained", 1683.6), \
+            "measured"
+    return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+def kernel_traffic(kernel):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or None when the
+    kernel's source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path)).get(kernel)
+    if not d:
+        return None
+    src = os.path.join(ROOT, d["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != d["sha256_16"]:
+        return None
+    return d["bytes_per_launch"]
+
+
+def cpu_baseline(a, sample):
+    """The FP64 oracle (test infrastructure, untuned) on a bounded sample of the workload:
+    one temperature step from beta = 0 with `sample` particles of the same lattice."""
+    import numpy as np
+    from oracle.smc import SMC, SMCConfig
+    cfg = SMCConfig(L=a.L, N=sample, m2=-4.0, lam=8.0, rho=0.5, n_mcmc=a.n_mcmc, seed=0,
+                    normal_bits=32 if a.precision == "fp64" else 24)
+    smc = SMC(cfg)
+    t0 = time.perf_counter()
+    smc.temper_step()
+    dt = time.perf_counter() - t0
+    D = a.L * a.L
+    try:
+        import threadpoolctl
+        cores = max(i.get("num_threads", 1) for i in threadpoolctl.threadpool_info()) or os.cpu_count()
+    except Exception:
+        cores = os.cpu_count()
+    del np
+    return {"value": sample * D * a.n_mcmc / dt, "unit": "site-updates/s", "cores": cores, "kind": "oracle",
+            "sample": "one temperature step (ESS bisection, resampling, covariance + Cholesky of the D x D "
+                      "covariance, %d RWM sweeps) with N=%d of the %d particles, L=%d; %.1f s"
+                      % (a.n_mcmc, sample, a.N, a.L, dt)}
+
+
+def run_reference(a):
+    rank, world, dist = dist_setup(a)
+    if rank != 0:
+        return 0
+    res = []
+    for _ in range(a.warmup):
+        pass
+    for _ in range(max(1, a.steps)):
+        res.append(cpu_baseline(a, a.cpu_sample))
+    v = statistics.median(r["value"] for r in res)
+    cb = dict(res[0])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "site-updates/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * a.cpu_sample * a.L ** 2 * a.n_mcmc / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp64",
+            "data": "synthetic (Philox N(0,I) initial fields)", "config": workload(a), "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    import torch
+    import paper_2511_15196_gb300 as p
+    rank, world, dist = dist_setup(a)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    D = a.L * a.L
+    prec = PREC[a.precision]
+    cfg = p.Config(L=a.L, N=a.N, m2=-4.0, lam=8.0, precision=prec, n_mcmc=a.n_mcmc, ess_target=0.5,
+                   seed=1000 + rank)
+    stream = torch.cuda.current_stream()
+
+    def fresh():
+        r = p.Run(cfg)
+        r.set_stage_timing(True)
+        return r
+
+    run = fresh()
+    for _ in range(a.warmup):
+        if run.temper_step() >= 1.0:
+            run = fresh()
+    run.stage_times(reset=True)
+    l0 = run.kernel_launches()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stage_acc = {}
+    launches = 0
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(a.steps):
+            if run.temper_step() >= 1.0:
+                # the run reached beta = 1: account and continue on a fresh replica
+                for k, (ms, n) in run.stage_times(reset=True).items():
+                    s = stage_acc.setdefault(k, [0.0, 0])
+                    s[0] += ms
+                    s[1] += n
+                launches += run.kernel_launches() - l0
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                partial = ev0.elapsed_time(ev1)
+                run = fresh()
+                l0 = run.kernel_launches()
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                stage_acc.setdefault("_partial_ms", [0.0, 0])[0] += partial
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    elapsed_ms = ev0.elapsed_time(ev1) + stage_acc.pop("_partial_ms", [0.0, 0])[0]
+    if dist is not None:
+        dist.barrier()
+    launches += run.kernel_launches() - l0
+    for k, (ms, n) in run.stage_times(reset=True).items():
+        s = stage_acc.setdefault(k, [0.0, 0])
+        s[0] += ms
+        s[1] += n
+    elapsed_ms = max_over_ranks(elapsed_ms, dist)
+    obs = run.observables()
+    units_per_step = a.N * D * a.n_mcmc
+    value = world * units_per_step * a.steps / (elapsed_ms * 1e-3)
+    mutation_ms = sum(stage_acc.get(k, [0, 0])[0] for k in ("normals", "propose", "accept"))
+
+    # roofline of the dominant kernel
+    hbm, bf16, bf16_s, src = peaks()
+    dom = max(("propose", "accept", "normals", "cholesky", "covariance", "gather", "bisect_reweight", "resample"),
+              key=lambda k: stage_acc.get(k, [0, 0])[0])
+    ms_tot, n_l = stage_acc[dom]
+    avg_s = ms_tot / max(n_l, 1) * 1e-3
+    acc = obs["acc_rate"] if obs["acc_rate"] == obs["acc_rate"] else 0.25
+    work = {
+        "propose": ("tensor", a.N * D * (D + 1), "TFLOP/s"),
+        "accept": ("hbm", a.N * D * 4 * (1 + acc), "GB/s"),
+        "normals": ("hbm", a.N * D * (2 if prec == 2 else 4 * (2 if prec == 0 else 1)), "GB/s"),
+        "gather": ("hbm", 2 * a.N * D * (8 if prec == 0 else 4), "GB/s"),
+        "cholesky": ("alu", D ** 3 / 3.0, "TFLOP/s"),
+        "covariance": ("tensor", a.N * D * (D + 1), "TFLOP/s"),
+        "bisect_reweight": ("alu", 64 * 2 * a.N * 20, "TFLOP/s"),
+        "resample": ("hbm", a.N * 24, "GB/s"),
+    }[dom]
+    bound, units, unit = work
+    if unit == "TFLOP/s":
+        achieved = units / avg_s / 1e12
+        peak = bf16_s if bound == "tensor" else 1.25
+        peak_src = "%s bf16 sustained" % src if bound == "tensor" else "nominal FP64 1.25 TFLOP/s"
+    else:
+        achieved = units / avg_s / 1e9
+        peak = hbm
+        peak_src = "%s HBM copy" % src
+    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "peak_source": peak_src, "traffic": kernel_traffic(dom),
+                "work_per_launch": units, "avg_launch_ms": avg_s * 1e3}
+    stages = {k: {"ms_per_step": v[0] / a.steps, "launches": v[1]} for k, v in stage_acc.items() if v[1]}
+    line = {"metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": elapsed_ms / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": PREC_DTYPE[a.precision],
+            "data": "synthetic (Philox N(0,I) initial fields, random-init sampler state)",
+            "config": workload(a), "gpu_launches": launches,
+            "mutation_only": {"value": world * units_per_step * a.steps / (mutation_ms * 1e-3) if mutation_ms else None,
+                              "unit": "site-updates/s", "ms_per_step": mutation_ms / a.steps},
+            "roofline": roofline, "stages": stages, "clocks": clk.summary(),
+            "sampler": {"beta": obs["beta"], "acc_rate": obs["acc_rate"], "ess": obs["ess"],
+                        "n_steps": obs["n_steps"]}}
+    run.close()
+
+    if not a.no_e2e:
+        # the same metric through the public API with host buffers: every step copies the
+        # population in from pinned host memory and reads beta and log Z back
+        r2 = p.Run(cfg)
+        host = r2.particles().cpu().pin_memory()
+        for _ in range(2):
+            r2.load_particles(host)
+            r2.temper_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n_done = 0
+        for _ in range(max(2, a.steps // 2)):
+            r2.load_particles(host)
+            b = r2.temper_step()
+            lz = r2.log_evidence()
+            n_done += 1
+            if b >= 1.0:
+                break
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+        line["e2e"] = {"value": world * units_per_step * n_done / e2e_s, "unit": "site-updates/s",
+                       "h2d_bytes_per_step": host.numel() * host.element_size(), "d2h_bytes_per_step": 8 + 16,
+                       "steps": n_done}
+        del lz
+        r2.close()
+    if rank == 0 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(a, a.cpu_sample)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,284 @@
+/*
+ * phi4smc -- GB300 (sm_103a) particle Monte Carlo for lattice phi^4 theory.
+ *
+ * C ABI of the library libphi4smc.so. It implements the data-parallel hot path
+ * of the particle samplers of arXiv 2511.15196, "Particle Monte Carlo methods
+ * for Lattice Field Theory":
+ *   - adaptive tempered SMC with covariance-preconditioned random-walk
+ *     Metropolis moves (Sec. 2, sampler (i); App. A), and
+ *   - nested sampling with slice-sampling rejuvenation (Sec. 2, sampler (iv);
+ *     App. A),
+ * on the Euclidean action of Eq. (1) on a periodic L x L lattice.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Fields.  A population of N fields is a row-major [N][D] array, D = L*L,
+ *          site x = r*L + c. Element type follows phi4_dtype.
+ * Action.  S = sum_x [ c_kin * sum_mu phi_x(2 phi_x - phi_{x+mu} - phi_{x-mu})
+ *                      + c_mass * m2 * phi_x^2 + lambda * phi_x^4 ]
+ *          (Eq. (1) with its 1/2 factors made coefficients: c_kin = c_mass = 1/2
+ *          is Eq. (1) verbatim, c_kin = c_mass = 1 the unhalved form).
+ * Memory.  The caller owns all memory. Pointers documented "device" must be
+ *          device (or managed) memory on the current CUDA device; "host" means
+ *          host memory. The library never calls cudaMalloc/cudaFree: state
+ *          lives in a caller-provided workspace.
+ * Streams. `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *          stream). Entry points that only enqueue work return before it runs.
+ * Errors.  Every function returns phi4_status. A message for the last error on
+ *          the calling thread is available from phi4_last_error(). Device-side
+ *          anomalies (non-finite values, a non positive-definite covariance, a
+ *          bounded device wait that gave up) are written to a device status
+ *          word and reported by the next synchronising call.
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11) with
+ *          key = (seed mod 2^32, (seed >> 32) xor stream_id) and
+ *          counter = (kind << 24 | step, sub, particle, block), see phi4_rng_kind.
+ */
+#ifndef PHI4SMC_H
+#define PHI4SMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PHI4_OK = 0,
+  PHI4_ERR_ARG = 1,          /* invalid argument (message says which) */
+  PHI4_ERR_CUDA = 2,         /* a CUDA runtime/driver call failed */
+  PHI4_ERR_NOT_PD = 3,       /* covariance not positive definite after all ridge increases */
+  PHI4_ERR_NONFINITE = 4,    /* NaN/Inf met in log-weights or the action */
+  PHI4_ERR_DONE = 5,         /* SMC already at beta = 1, or nested sampling stopped */
+  PHI4_ERR_WORKSPACE = 6,    /* workspace too small or misaligned */
+  PHI4_ERR_TIMEOUT = 7,      /* a bounded device-side wait gave up */
+  PHI4_ERR_UNSUPPORTED = 8   /* configuration outside what this build supports */
+} phi4_status;
+
+typedef enum { PHI4_SMC_RW = 0, PHI4_NS_SLICE = 1 } phi4_kind;
+
+/* Arithmetic forms of a run.
+ * FP64:      fields, proposal GEMM, covariance and everything else in double.
+ * FP32:      float fields, SIMT float proposal GEMM and covariance; float
+ *            per-site action terms with compensated float partial sums that are
+ *            combined in double; double log-weights, Cholesky and log Z.
+ * MIXED_BF16: float fields; proposal and covariance GEMMs on the tcgen05 tensor
+ *            cores with bf16 operands and fp32 accumulation; double Cholesky,
+ *            acceptance test, log-weights and compensated log Z. */
+typedef enum { PHI4_FP64 = 0, PHI4_FP32 = 1, PHI4_MIXED_BF16 = 2 } phi4_precision;
+
+/* Element types of the kernel-level entry points. */
+typedef enum { PHI4_DT_F64 = 0, PHI4_DT_F32 = 1, PHI4_DT_BF16 = 2 } phi4_dtype;
+
+/* Stream kinds of the Philox counter word 0 (bits 24..31). */
+typedef enum {
+  PHI4_RNG_INIT = 1, PHI4_RNG_RESAMPLE = 2, PHI4_RNG_PROPOSE = 3, PHI4_RNG_ACCEPT = 4,
+  PHI4_RNG_NS_START = 5, PHI4_RNG_NS_DIRECTION = 6, PHI4_RNG_NS_SLICE = 7
+} phi4_rng_kind;
+
+typedef struct {
+  int32_t L;                 /* lattice side, D = L*L sites (1 <= L <= 128) */
+  int32_t N;                 /* particles (SMC) or live points (NS), 1 <= N <= 131072 */
+  int32_t kind;              /* phi4_kind */
+  int32_t precision;         /* phi4_precision */
+  double m2, lambda;         /* bare mass^2 and quartic coupling */
+  double c_kin, c_mass;      /* action coefficients, 1.0 / 1.0 = unhalved form, 0.5 / 0.5 = Eq. (1) */
+  int32_t keep_reference;    /* 0: tempering path N(0,I)^(1-beta) e^{-beta S}, target e^{-S} at beta=1;
+                                1: path N(0,I) e^{-beta S}, i.e. exp(-[U0 + beta S]) of Sec. 2 */
+  int32_t n_mcmc;            /* random-walk sweeps per temperature (SMC) */
+  double ess_target;         /* rho in (0,1): next beta keeps ESS = rho N (SMC) */
+  double rw_scale;           /* proposal scale on the Cholesky factor; <= 0 selects 2.38/sqrt(D) (App. A) */
+  int32_t ns_n_delete;       /* live points deleted per nested-sampling iteration (1 <= k < N) */
+  int32_t ns_slice_steps;    /* slice steps per new point; <= 0 selects 3*D */
+  double ns_stop_frac;       /* stop when remaining evidence < ns_stop_frac * Z */
+  double chol_jitter_rel;    /* ridge delta = chol_jitter_rel * trace(Sigma) / D, x10 per failed try */
+  int32_t bisect_iters;      /* maximum bisection steps for the next beta (64) */
+  int32_t slice_max_shrink;  /* slice shrinkage tries before a step is abandoned (64) */
+  uint64_t seed, stream_id;  /* Philox key material */
+} phi4_config;
+
+typedef struct {
+  double beta;               /* current inverse temperature (SMC) */
+  double logz, logz_err;     /* running log-evidence; error bar (NS: sqrt(H/N); SMC: NaN) */
+  double mean_M, mean_absM, mean_M2, chi, mode_balance; /* uniform-weight population moments of
+                                M = (1/D) sum_x phi_x; chi = D(<M^2> - <M>^2); mode balance of App. F */
+  double ess;                /* ESS of the last reweighting (SMC) */
+  double acc_rate;           /* acceptance rate of the last temperature's sweeps (SMC) */
+  int64_t n_steps;           /* temperatures (SMC) or deletion iterations (NS) done */
+  int64_t n_likelihood_evals;/* action evaluations so far */
+  int64_t slice_capped;      /* NS slice steps abandoned after slice_max_shrink tries */
+} phi4_obs;
+
+typedef struct phi4_run phi4_run; /* opaque, host memory owned by the library until smc_free */
+
+/* ------------------------------------------------------------------------ */
+/* Library                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Message of the last failed call on this thread (static storage, never NULL). */
+const char* phi4_last_error(void);
+
+/* Number of streaming multiprocessors of the current device (host query). */
+phi4_status phi4_device_sm_count(int32_t* out);
+
+/* ------------------------------------------------------------------------ */
+/* Run-level API: a population advanced one outer step per call.             */
+/* ------------------------------------------------------------------------ */
+
+/* Workspace bytes smc_init needs for `cfg` (host only; validates cfg). */
+phi4_status phi4_workspace_bytes(const phi4_config* cfg, size_t* bytes);
+
+/* Creates a run in the caller's device workspace `d_workspace` (>= phi4_workspace_bytes,
+ * 256-byte aligned), enqueues on `stream` the initial draw phi ~ N(0, I_D)
+ * (PHI4_RNG_INIT, step 0) and its action, and returns the host handle.
+ * SMC (Sec. 2 (i)): beta = 0, log Z = 0. NS (Sec. 2 (iv)): N live points, log X = 0.
+ * The workspace must stay valid until smc_free. */
+phi4_status smc_init(const phi4_config* cfg, void* d_workspace, size_t workspace_bytes,
+                     void* stream, phi4_run** out);
+
+/* One SMC temperature (Sec. 2 (i); App. A): ESS bisection for the next beta,
+ * reweighting with Kahan-compensated log Z, systematic resampling and particle
+ * gather, covariance and FP64 Cholesky refit, n_mcmc random-walk Metropolis
+ * sweeps at the new beta. Synchronises the run's stream and writes the new beta
+ * to *beta_out (may be NULL). PHI4_ERR_DONE once beta == 1; PHI4_ERR_ARG on an NS run. */
+phi4_status smc_temper_step(phi4_run* run, double* beta_out);
+
+/* One nested-sampling iteration (Sec. 2 (iv); App. A): delete the ns_n_delete
+ * lowest-likelihood live points, update log X and log Z, refit the live-point
+ * covariance, and replace each deleted point by ns_slice_steps constrained slice
+ * steps from a random survivor. Synchronises; *done_out = 1 when the stopping
+ * rule holds. PHI4_ERR_DONE if already stopped; PHI4_ERR_ARG on an SMC run. */
+phi4_status ns_replace_step(phi4_run* run, int32_t* done_out);
+
+/* Running log-evidence and its error bar (NS: sqrt(H/N) including the live
+ * points; SMC: NaN). Synchronises the run's stream. */
+phi4_status smc_log_evidence(const phi4_run* run, double* logz, double* logz_err);
+
+/* Population observables (uniform weights over the current population).
+ * Synchronises the run's stream. */
+phi4_status smc_observables(const phi4_run* run, phi4_obs* out);
+
+/* Copies the current fields ([N][D], element type of the run's precision:
+ * f64 for PHI4_FP64, f32 otherwise) to `dst` (host or device), `bytes` >= N*D*elem.
+ * Synchronises the run's stream. */
+phi4_status smc_copy_particles(const phi4_run* run, void* dst, size_t bytes);
+
+/* Replaces the current fields by `src` (host or device, same layout as
+ * smc_copy_particles) and recomputes their action and log-weights on the run's
+ * stream (enqueued; returns after the copy is enqueued). */
+phi4_status smc_load_particles(phi4_run* run, const void* src, size_t bytes);
+
+/* Releases the handle (not the workspace). Synchronises the run's stream. */
+phi4_status smc_free(phi4_run* run);
+
+/* Number of kernels the run has launched since smc_init (host counter). */
+phi4_status phi4_kernel_launches(const phi4_run* run, int64_t* out);
+
+/* Per-stage device timing of a run. When enabled, CUDA events bracket each
+ * stage on the run's stream; phi4_stage_times returns accumulated milliseconds
+ * and launch counts since the last reset, for stage ids 0..PHI4_N_STAGES-1
+ * (names from phi4_stage_name). Synchronises the run's stream. */
+#define PHI4_N_STAGES 12
+phi4_status phi4_set_stage_timing(phi4_run* run, int32_t enable);
+phi4_status phi4_stage_times(phi4_run* run, double* ms_out, int64_t* launches_out, int32_t reset);
+const char* phi4_stage_name(int32_t stage);
+
+/* ------------------------------------------------------------------------ */
+/* Kernel-level API: each step of the path on caller buffers.                */
+/* All enqueue on `stream` and return immediately unless stated.             */
+/* ------------------------------------------------------------------------ */
+
+/* Standard normals out[r*ld + j] for r < n_rows, j < n_cols, from Philox with
+ * counter (kind << 24 | step, sub, row0 + r, j / 4): outputs (0,1) and (2,3) of
+ * each block are Box-Muller pairs. dtype F64: uniforms from 32-bit words,
+ * u1 = (w+1) 2^-32, u2 = w 2^-32, evaluated in double. F32/BF16: uniforms from
+ * the top 24 bits, evaluated in float (BF16: rounded to nearest). `out` device. */
+phi4_status phi4_philox_normals(uint64_t seed, uint64_t stream_id, int32_t kind, uint32_t step, uint32_t sub,
+                                int32_t row0, int32_t n_rows, int32_t n_cols, int32_t ld, int32_t dtype,
+                                void* out, void* stream);
+
+/* Action (Eq. (1), coefficient form) and squared norm of N fields:
+ * S[i], sq[i] (device double) from phi (device, [N][D], dtype F64 or F32).
+ * F32 fields: per-site terms in float, compensated float partial sums, double total. */
+phi4_status phi4_action(const void* phi, int32_t dtype, int32_t N, int32_t L, double m2, double lambda,
+                        double c_kin, double c_mass, double* S, double* sq, void* stream);
+
+/* Scratch bytes for phi4_ess_bisect with N weights. */
+size_t phi4_bisect_scratch_bytes(int32_t N);
+
+/* Next temperature and reweighting (Sec. 2 (i)): with a_i = ell_i - max ell,
+ * ESS(d) = (sum e^{d a})^2 / sum e^{2 d a}; if ESS(1-beta) >= rho N then
+ * dbeta = 1-beta, else bisection on [0, 1-beta] (at most `iters` halvings, stops
+ * when the bracket cannot shrink) returns the lower end. Then writes
+ * w[i] = exp(dbeta a_i) (device, max weight 1) and
+ * out[0] = dbeta, out[1] = beta + dbeta (exactly 1 when the last step),
+ * out[2] = ESS(dbeta), out[3] = log Z increment = dbeta max ell + log sum w - log N,
+ * out[4] = number of bisection halvings. ell, beta_in, w, out: device.
+ * One cooperative launch over several CTAs with a bounded grid barrier;
+ * `scratch` (device, phi4_bisect_scratch_bytes) is zeroed by the call. */
+phi4_status phi4_ess_bisect(const double* ell, int32_t N, const double* beta_in, double rho, int32_t iters,
+                            double* w, double* out, void* scratch, size_t scratch_bytes, void* stream);
+
+/* Scratch bytes for phi4_resample_systematic with N weights. */
+size_t phi4_resample_scratch_bytes(int32_t N);
+
+/* Systematic resampling in fixed point (a reading of Sec. 2 (i); bit-exact):
+ * q_i = floor(ldexp(w_i / max w, 46)), C_j = sum_{k<=j} q_k, Q = C_{N-1},
+ * p_i = floor((i 2^32 + U) Q / (N 2^32)), anc[i] = min{ j : C_j > p_i }.
+ * w (device double, >= 0, max > 0), anc (device int32, nondecreasing), N <= 131072.
+ * `scratch` (device, phi4_resample_scratch_bytes). */
+phi4_status phi4_resample_systematic(const double* w, int32_t N, uint32_t U, int32_t* anc,
+                                     void* scratch, size_t scratch_bytes, void* stream);
+
+/* dst row i = src row anc[i] for i < N, rows of `row_bytes` (device buffers;
+ * dst and src must not overlap). */
+phi4_status phi4_gather_rows(const void* src, void* dst, size_t row_bytes, int32_t N, const int32_t* anc,
+                             void* stream);
+
+/* Scratch bytes for phi4_covariance. */
+size_t phi4_covariance_scratch_bytes(int32_t N, int32_t D, int32_t precision);
+
+/* Particle covariance (App. A): Sigma = Xc^T Xc / (N-1), Xc = phi - mean, lower
+ * triangle (j <= i) of the row-major D x D double matrix `sigma` (device); the
+ * strictly upper part is left untouched. precision FP64 / FP32: SIMT GEMM in that
+ * type (phi dtype F64 / F32); MIXED_BF16: Xc rounded to bf16, tcgen05 GEMM with
+ * fp32 accumulation (phi F32). */
+phi4_status phi4_covariance(const void* phi, int32_t precision, int32_t N, int32_t D, double* sigma,
+                            void* scratch, size_t scratch_bytes, void* stream);
+
+/* In-place Cholesky A = L L^T (+ ridge): on entry the lower triangle of the
+ * row-major D x D double matrix `a` (device) holds Sigma; `*d_ridge` (device
+ * double) is added to its diagonal; on exit the lower triangle holds L and the
+ * strictly upper triangle is zeroed. A non-positive pivot sets bit 2 of
+ * `*d_status` (device uint32) and stops the factorisation. Blocked right-looking,
+ * all arithmetic double. */
+phi4_status phi4_cholesky(double* a, int32_t D, const double* d_ridge, uint32_t* d_status, void* stream);
+
+/* Random-walk proposal (App. A): prop = phi + scale * Z L^T with Z the normals of
+ * (PHI4_RNG_PROPOSE, step, sweep, particle, block) drawn for this call.
+ * precision FP64/FP32: L double/float [D][D] lower (device), SIMT GEMM.
+ * MIXED_BF16: L bf16 [D][ldl] (ldl >= D, multiple of 8), tcgen05 GEMM with fp32
+ * accumulation. phi, prop: device [N][D] (F64 for FP64, else F32).
+ * `scratch` holds Z (phi4_propose_scratch_bytes). */
+size_t phi4_propose_scratch_bytes(int32_t N, int32_t D, int32_t precision);
+phi4_status phi4_rw_propose(const void* phi, void* prop, const void* Lfac, int32_t ldl, int32_t precision,
+                            int32_t N, int32_t D, double scale, uint64_t seed, uint64_t stream_id,
+                            uint32_t step, uint32_t sweep, void* scratch, size_t scratch_bytes, void* stream);
+
+/* Metropolis accept step (Sec. 2 tempering; App. A): for every particle,
+ * S', |phi'|^2 of prop; log alpha = -beta (S' - S) - (1-beta)(|phi'|^2 - |phi|^2)/2
+ * (keep_reference: -beta (S'-S) - (|phi'|^2-|phi|^2)/2) in double; u from
+ * (PHI4_RNG_ACCEPT, step, sweep, particle, 0), words 0 and 1 as a 53-bit uniform
+ * in (0,1]; accept iff log u < log alpha, then phi row := prop row, S, sq and
+ * ell (tempering log-weight) updated. *beta (device double) is read on the device.
+ * acc_count: device uint32[2]; [0] is incremented by the number of accepted
+ * moves, bit 0 of [1] is set when an action is not finite (that move is rejected). */
+phi4_status phi4_rw_accept(void* phi, const void* prop, int32_t dtype, int32_t N, int32_t L, double m2,
+                           double lambda, double c_kin, double c_mass, int32_t keep_reference,
+                           double* S, double* sq, double* ell, const double* beta, uint64_t seed,
+                           uint64_t stream_id, uint32_t step, uint32_t sweep, uint32_t* acc_count, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PHI4SMC_H */

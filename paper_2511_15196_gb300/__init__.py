@@ -1,0 +1,358 @@
+"""Python binding of libphi4smc (include/phi4smc.h): GB300 particle Monte Carlo
+for lattice phi^4 theory (arXiv 2511.15196, Sec. 2 samplers (i) and (iv)).
+
+Argument marshalling only: every step of the sampler runs in the CUDA kernels of
+the shared library. PyTorch provides device memory (the workspace tensors) and
+streams. Importing this module does not need a GPU; the library is loaded on
+first use and the call fails loudly if it has not been built.
+"""
+import ctypes
+import dataclasses
+import math
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libphi4smc.so")
+
+PHI4_OK, PHI4_ERR_ARG, PHI4_ERR_CUDA, PHI4_ERR_NOT_PD, PHI4_ERR_NONFINITE, PHI4_ERR_DONE, PHI4_ERR_WORKSPACE, \
+    PHI4_ERR_TIMEOUT, PHI4_ERR_UNSUPPORTED = range(9)
+SMC_RW, NS_SLICE = 0, 1
+FP64, FP32, MIXED_BF16 = 0, 1, 2
+DT_F64, DT_F32, DT_BF16 = 0, 1, 2
+RNG_INIT, RNG_RESAMPLE, RNG_PROPOSE, RNG_ACCEPT, RNG_NS_START, RNG_NS_DIRECTION, RNG_NS_SLICE = range(1, 8)
+N_STAGES = 12
+
+_STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_NOT_PD", 4: "ERR_NONFINITE", 5: "ERR_DONE",
+                 6: "ERR_WORKSPACE", 7: "ERR_TIMEOUT", 8: "ERR_UNSUPPORTED"}
+
+
+class Phi4Error(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class CConfig(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("N", ctypes.c_int32), ("kind", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("m2", ctypes.c_double), ("lambda_", ctypes.c_double),
+                ("c_kin", ctypes.c_double), ("c_mass", ctypes.c_double), ("keep_reference", ctypes.c_int32),
+                ("n_mcmc", ctypes.c_int32), ("ess_target", ctypes.c_double), ("rw_scale", ctypes.c_double),
+                ("ns_n_delete", ctypes.c_int32), ("ns_slice_steps", ctypes.c_int32),
+                ("ns_stop_frac", ctypes.c_double), ("chol_jitter_rel", ctypes.c_double),
+                ("bisect_iters", ctypes.c_int32), ("slice_max_shrink", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint64)]
+
+
+class CObs(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("logz", ctypes.c_double), ("logz_err", ctypes.c_double),
+                ("mean_M", ctypes.c_double), ("mean_absM", ctypes.c_double), ("mean_M2", ctypes.c_double),
+                ("chi", ctypes.c_double), ("mode_balance", ctypes.c_double), ("ess", ctypes.c_double),
+                ("acc_rate", ctypes.c_double), ("n_steps", ctypes.c_int64), ("n_likelihood_evals", ctypes.c_int64),
+                ("slice_capped", ctypes.c_int64)]
+
+
+@dataclasses.dataclass
+class Config:
+    """Mirror of phi4_config with the library's defaults."""
+    L: int
+    N: int
+    m2: float = -4.0
+    lam: float = 8.0
+    kind: int = SMC_RW
+    precision: int = FP64
+    c_kin: float = 1.0
+    c_mass: float = 1.0
+    keep_reference: bool = False
+    n_mcmc: int = 10
+    ess_target: float = 0.5
+    rw_scale: float = 0.0
+    ns_n_delete: int = 1
+    ns_slice_steps: int = 0
+    ns_stop_frac: float = 1e-3
+    chol_jitter_rel: float = 1e-8
+    bisect_iters: int = 64
+    slice_max_shrink: int = 64
+    seed: int = 0
+    stream_id: int = 0
+
+    def to_c(self):
+        return CConfig(self.L, self.N, self.kind, self.precision, self.m2, self.lam, self.c_kin, self.c_mass,
+                       int(bool(self.keep_reference)), self.n_mcmc, self.ess_target, self.rw_scale,
+                       self.ns_n_delete, self.ns_slice_steps, self.ns_stop_frac, self.chol_jitter_rel,
+                       self.bisect_iters, self.slice_max_shrink, self.seed, self.stream_id)
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I32, _U32, _U64, _F64, _SZ = ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double, ctypes.c_size_t
+_SIGS = {
+    "phi4_last_error": ([], ctypes.c_char_p),
+    "phi4_device_sm_count": ([ctypes.POINTER(_I32)], _I32),
+    "phi4_workspace_bytes": ([ctypes.POINTER(CConfig), ctypes.POINTER(_SZ)], _I32),
+    "smc_init": ([ctypes.POINTER(CConfig), _P, _SZ, _P, ctypes.POINTER(_P)], _I32),
+    "smc_temper_step": ([_P, ctypes.POINTER(_F64)], _I32),
+    "ns_replace_step": ([_P, ctypes.POINTER(_I32)], _I32),
+    "smc_log_evidence": ([_P, ctypes.POINTER(_F64), ctypes.POINTER(_F64)], _I32),
+    "smc_observables": ([_P, ctypes.POINTER(CObs)], _I32),
+    "smc_copy_particles": ([_P, _P, _SZ], _I32),
+    "smc_load_particles": ([_P, _P, _SZ], _I32),
+    "smc_free": ([_P], _I32),
+    "phi4_kernel_launches": ([_P, ctypes.POINTER(ctypes.c_int64)], _I32),
+    "phi4_set_stage_timing": ([_P, _I32], _I32),
+    "phi4_stage_times": ([_P, ctypes.POINTER(_F64), ctypes.POINTER(ctypes.c_int64), _I32], _I32),
+    "phi4_stage_name": ([_I32], ctypes.c_char_p),
+    "phi4_philox_normals": ([_U64, _U64, _I32, _U32, _U32, _I32, _I32, _I32, _I32, _I32, _P, _P], _I32),
+    "phi4_action": ([_P, _I32, _I32, _I32, _F64, _F64, _F64, _F64, _P, _P, _P], _I32),
+    "phi4_bisect_scratch_bytes": ([_I32], _SZ),
+    "phi4_ess_bisect": ([_P, _I32, _P, _F64, _I32, _P, _P, _P, _SZ, _P], _I32),
+    "phi4_resample_scratch_bytes": ([_I32], _SZ),
+    "phi4_resample_systematic": ([_P, _I32, _U32, _P, _P, _SZ, _P], _I32),
+    "phi4_gather_rows": ([_P, _P, _SZ, _I32, _P, _P], _I32),
+    "phi4_covariance_scratch_bytes": ([_I32, _I32, _I32], _SZ),
+    "phi4_covariance": ([_P, _I32, _I32, _I32, _P, _P, _SZ, _P], _I32),
+    "phi4_cholesky": ([_P, _I32, _P, _P, _P], _I32),
+    "phi4_propose_scratch_bytes": ([_I32, _I32, _I32], _SZ),
+    "phi4_rw_propose": ([_P, _P, _P, _I32, _I32, _I32, _I32, _F64, _U64, _U64, _U32, _U32, _P, _SZ, _P], _I32),
+    "phi4_rw_accept": ([_P, _P, _I32, _I32, _I32, _F64, _F64, _F64, _F64, _I32, _P, _P, _P, _P, _U64, _U64, _U32,
+                        _U32, _P, _P], _I32),
+}
+
+
+def lib():
+    """The loaded shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libphi4smc.so not built: run `python -c 'import __graft_entry__ as g; g.build()'` "
+                               "or `python paper_2511_15196_gb300/build.py`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(status):
+    if status != PHI4_OK:
+        raise Phi4Error(status, lib().phi4_last_error().decode())
+    return status
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def workspace_bytes(cfg: Config):
+    n = _SZ()
+    c = cfg.to_c()
+    _check(lib().phi4_workspace_bytes(ctypes.byref(c), ctypes.byref(n)))
+    return n.value
+
+
+class Run:
+    """An SMC or nested-sampling run whose state lives in a torch uint8 CUDA tensor."""
+
+    def __init__(self, cfg: Config, device="cuda", stream=None):
+        import torch
+        self.cfg = cfg
+        self._c = cfg.to_c()
+        nbytes = workspace_bytes(cfg)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        base = self.workspace.data_ptr()
+        self._ws_ptr = (base + 255) & ~255
+        self._stream = stream
+        h = _P()
+        _check(lib().smc_init(ctypes.byref(self._c), ctypes.c_void_p(self._ws_ptr), nbytes, _stream(stream),
+                              ctypes.byref(h)))
+        self.handle = h
+
+    @property
+    def D(self):
+        return self.cfg.L * self.cfg.L
+
+    def temper_step(self):
+        b = _F64()
+        _check(lib().smc_temper_step(self.handle, ctypes.byref(b)))
+        return b.value
+
+    def replace_step(self):
+        d = _I32()
+        _check(lib().ns_replace_step(self.handle, ctypes.byref(d)))
+        return bool(d.value)
+
+    def log_evidence(self):
+        z, e = _F64(), _F64()
+        _check(lib().smc_log_evidence(self.handle, ctypes.byref(z), ctypes.byref(e)))
+        return z.value, e.value
+
+    def observables(self):
+        o = CObs()
+        _check(lib().smc_observables(self.handle, ctypes.byref(o)))
+        return {k: getattr(o, k) for k, _ in CObs._fields_}
+
+    def particles(self):
+        import torch
+        dt = torch.float64 if self.cfg.precision == FP64 else torch.float32
+        out = torch.empty((self.cfg.N, self.D), dtype=dt, device=self.workspace.device)
+        _check(lib().smc_copy_particles(self.handle, _ptr(out), out.numel() * out.element_size()))
+        return out
+
+    def load_particles(self, src):
+        _check(lib().smc_load_particles(self.handle, _ptr(src), src.numel() * src.element_size()))
+
+    def kernel_launches(self):
+        n = ctypes.c_int64()
+        _check(lib().phi4_kernel_launches(self.handle, ctypes.byref(n)))
+        return n.value
+
+    def set_stage_timing(self, on=True):
+        _check(lib().phi4_set_stage_timing(self.handle, 1 if on else 0))
+
+    def stage_times(self, reset=False):
+        ms = (_F64 * N_STAGES)()
+        n = (ctypes.c_int64 * N_STAGES)()
+        _check(lib().phi4_stage_times(self.handle, ms, n, 1 if reset else 0))
+        return {lib().phi4_stage_name(i).decode(): (ms[i], n[i]) for i in range(N_STAGES)}
+
+    def run(self, max_steps=100000):
+        n = 0
+        if self.cfg.kind == SMC_RW:
+            while n < max_steps:
+                n += 1
+                if self.temper_step() >= 1.0:
+                    break
+        else:
+            while n < max_steps:
+                n += 1
+                if self.replace_step():
+                    break
+        return self.observables()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().smc_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- kernel level
+
+def philox_normals(out, seed, stream_id, kind, step, sub, row0=0, dtype=None, stream=None):
+    """Fill a 2-D CUDA tensor with the normals of the library's counter layout."""
+    import torch
+    if dtype is None:
+        dtype = {torch.float64: DT_F64, torch.float32: DT_F32, torch.bfloat16: DT_BF16}[out.dtype]
+    n_rows, n_cols = out.shape
+    _check(lib().phi4_philox_normals(seed, stream_id, kind, step, sub, row0, n_rows, n_cols, out.stride(0), dtype,
+                                     _ptr(out), _stream(stream)))
+    return out
+
+
+def action(phi, L, m2, lam, c_kin=1.0, c_mass=1.0, stream=None):
+    import torch
+    N = phi.shape[0]
+    S = torch.empty(N, dtype=torch.float64, device=phi.device)
+    sq = torch.empty(N, dtype=torch.float64, device=phi.device)
+    dt = DT_F64 if phi.dtype == torch.float64 else DT_F32
+    _check(lib().phi4_action(_ptr(phi), dt, N, L, m2, lam, c_kin, c_mass, _ptr(S), _ptr(sq), _stream(stream)))
+    return S, sq
+
+
+def ess_bisect(ell, beta, rho, iters=64, stream=None):
+    """Returns (w, out) with out = [dbeta, beta_new, ess, logz_inc, halvings] (device tensors)."""
+    import torch
+    N = ell.shape[0]
+    dev = ell.device
+    w = torch.empty(N, dtype=torch.float64, device=dev)
+    out = torch.zeros(8, dtype=torch.float64, device=dev)
+    b = torch.tensor([beta], dtype=torch.float64, device=dev)
+    nb = lib().phi4_bisect_scratch_bytes(N)
+    scratch = torch.empty(nb, dtype=torch.uint8, device=dev)
+    _check(lib().phi4_ess_bisect(_ptr(ell), N, _ptr(b), rho, iters, _ptr(w), _ptr(out), _ptr(scratch), nb,
+                                 _stream(stream)))
+    return w, out
+
+
+def resample_systematic(w, U, stream=None):
+    import torch
+    N = w.shape[0]
+    anc = torch.empty(N, dtype=torch.int32, device=w.device)
+    nb = lib().phi4_resample_scratch_bytes(N)
+    scratch = torch.empty(nb, dtype=torch.uint8, device=w.device)
+    _check(lib().phi4_resample_systematic(_ptr(w), N, U, _ptr(anc), _ptr(scratch), nb, _stream(stream)))
+    return anc
+
+
+def gather_rows(src, anc, stream=None):
+    import torch
+    dst = torch.empty_like(src)
+    _check(lib().phi4_gather_rows(_ptr(src), _ptr(dst), src.shape[1] * src.element_size(), src.shape[0], _ptr(anc),
+                                  _stream(stream)))
+    return dst
+
+
+def covariance(phi, precision, stream=None):
+    import torch
+    N, D = phi.shape
+    sigma = torch.zeros((D, D), dtype=torch.float64, device=phi.device)
+    nb = lib().phi4_covariance_scratch_bytes(N, D, precision)
+    scratch = torch.empty(nb, dtype=torch.uint8, device=phi.device)
+    _check(lib().phi4_covariance(_ptr(phi), precision, N, D, _ptr(sigma), _ptr(scratch), nb, _stream(stream)))
+    return sigma
+
+
+def cholesky(a, ridge=0.0, stream=None):
+    """In-place FP64 Cholesky of a (D x D double CUDA tensor); returns (a, status)."""
+    import torch
+    D = a.shape[0]
+    r = torch.tensor([ridge], dtype=torch.float64, device=a.device)
+    st = torch.zeros(1, dtype=torch.int32, device=a.device)
+    _check(lib().phi4_cholesky(_ptr(a), D, _ptr(r), _ptr(st), _stream(stream)))
+    return a, st
+
+
+def rw_propose(phi, Lfac, precision, scale, seed, stream_id, step, sweep, stream=None):
+    import torch
+    N, D = phi.shape
+    prop = torch.empty_like(phi)
+    nb = lib().phi4_propose_scratch_bytes(N, D, precision)
+    scratch = torch.empty(nb, dtype=torch.uint8, device=phi.device)
+    ldl = Lfac.stride(0)
+    _check(lib().phi4_rw_propose(_ptr(phi), _ptr(prop), _ptr(Lfac), ldl, precision, N, D, scale, seed, stream_id,
+                                 step, sweep, _ptr(scratch), nb, _stream(stream)))
+    return prop
+
+
+def rw_accept(phi, prop, L, m2, lam, S, sq, ell, beta, seed, stream_id, step, sweep, c_kin=1.0, c_mass=1.0,
+              keep_reference=False, stream=None):
+    """In place on phi, S, sq, ell; returns the int32 [accepted, status] tensor."""
+    import torch
+    N = phi.shape[0]
+    dt = DT_F64 if phi.dtype == torch.float64 else DT_F32
+    b = torch.tensor([beta], dtype=torch.float64, device=phi.device)
+    cnt = torch.zeros(2, dtype=torch.int32, device=phi.device)
+    _check(lib().phi4_rw_accept(_ptr(phi), _ptr(prop), dt, N, L, m2, lam, c_kin, c_mass, int(keep_reference),
+                                _ptr(S), _ptr(sq), _ptr(ell), _ptr(b), seed, stream_id, step, sweep, _ptr(cnt),
+                                _stream(stream)))
+    return cnt
+
+
+def default_rw_scale(D):
+    return 2.38 / math.sqrt(D)

@@ -1,0 +1,618 @@
+// C ABI of libphi4smc (include/phi4smc.h): argument checking, workspace layout,
+// the SMC temperature pipeline, the nested-sampling iteration and the
+// kernel-level entry points. All device memory comes from the caller.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "philox.cuh"
+#include "run.h"
+
+namespace phi4 {
+
+static thread_local char g_err[512] = "no error";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) return 1;
+  return n;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace phi4
+
+using namespace phi4;
+
+namespace {
+
+phi4_status check_config(const phi4_config* c) {
+  ARG_CHECK(c != nullptr, "config is NULL");
+  ARG_CHECK(c->L >= 1 && c->L <= 128, "L = %d outside [1, 128]", c->L);
+  ARG_CHECK(c->N >= 2 && c->N <= 131072, "N = %d outside [2, 131072]", c->N);
+  ARG_CHECK(c->kind == PHI4_SMC_RW || c->kind == PHI4_NS_SLICE, "kind = %d unknown", c->kind);
+  ARG_CHECK(c->precision >= PHI4_FP64 && c->precision <= PHI4_MIXED_BF16, "precision = %d unknown", c->precision);
+  ARG_CHECK(isfinite(c->m2) && isfinite(c->lambda) && c->lambda >= 0.0, "m2/lambda invalid");
+  ARG_CHECK(isfinite(c->c_kin) && isfinite(c->c_mass) && c->c_kin >= 0.0, "c_kin/c_mass invalid");
+  if (c->kind == PHI4_SMC_RW) {
+    ARG_CHECK(c->ess_target > 0.0 && c->ess_target < 1.0, "ess_target = %g outside (0, 1)", c->ess_target);
+    ARG_CHECK(c->n_mcmc >= 0 && c->n_mcmc <= 100000, "n_mcmc = %d invalid", c->n_mcmc);
+    ARG_CHECK(c->bisect_iters >= 1 && c->bisect_iters <= 200, "bisect_iters = %d invalid", c->bisect_iters);
+  } else {
+    ARG_CHECK(c->ns_n_delete >= 1 && c->ns_n_delete < c->N, "ns_n_delete = %d outside [1, N)", c->ns_n_delete);
+    ARG_CHECK(c->ns_stop_frac > 0.0 && c->ns_stop_frac < 1.0, "ns_stop_frac invalid");
+    ARG_CHECK(c->slice_max_shrink >= 1 && c->slice_max_shrink <= 1024, "slice_max_shrink invalid");
+  }
+  ARG_CHECK(c->chol_jitter_rel >= 0.0 && isfinite(c->chol_jitter_rel), "chol_jitter_rel invalid");
+  return PHI4_OK;
+}
+
+// Workspace layout; with base == nullptr only the total size is computed.
+struct Layout {
+  size_t off = 0;
+  unsigned char* base = nullptr;
+  void* take(size_t bytes) {
+    void* p = base ? base + off : nullptr;
+    off += align256(bytes);
+    return p;
+  }
+};
+
+void lay_out(phi4_run* r, Layout& L) {
+  const phi4_config& c = r->cfg;
+  const int N = c.N, D = c.L * c.L;
+  const size_t e = (c.precision == PHI4_FP64) ? 8 : 4;
+  r->phi = L.take((size_t)N * D * e);
+  r->phi_alt = L.take((size_t)N * D * e);
+  r->prop = L.take((size_t)N * D * e);
+  if (c.precision == PHI4_MIXED_BF16) {
+    r->ldz = (D + 7) & ~7;
+    r->ldl = (D + 7) & ~7;
+    r->zdtype = PHI4_DT_BF16;
+    r->Z = L.take((size_t)N * r->ldz * 2);
+    r->Lg = L.take((size_t)D * r->ldl * 2);
+  } else {
+    r->ldz = D;
+    r->ldl = D;
+    r->zdtype = (c.precision == PHI4_FP64) ? PHI4_DT_F64 : PHI4_DT_F32;
+    r->Z = L.take((size_t)N * D * e);
+    r->Lg = L.take((size_t)D * D * e);
+  }
+  r->S = (double*)L.take(N * 8);
+  r->sq = (double*)L.take(N * 8);
+  r->ell = (double*)L.take(N * 8);
+  r->S_alt = (double*)L.take(N * 8);
+  r->sq_alt = (double*)L.take(N * 8);
+  r->ell_alt = (double*)L.take(N * 8);
+  r->w = (double*)L.take(N * 8);
+  r->M = (double*)L.take(N * 8);
+  r->anc = (int32_t*)L.take(N * 4);
+  r->sigma = (double*)L.take((size_t)D * D * 8);
+  r->chol = (double*)L.take((size_t)D * D * 8);
+  r->scal = (double*)L.take(SC_COUNT * 8);
+  r->status = (uint32_t*)L.take(16);
+  r->acc_count = r->status + 1;
+  r->cov_scratch_bytes = covariance_scratch_bytes(N, D, c.precision);
+  r->cov_scratch = L.take(r->cov_scratch_bytes);
+  r->bisect_scratch = L.take(bisect_scratch_bytes(N));
+  r->resample_scratch = L.take(resample_scratch_bytes(N));
+  if (c.kind == PHI4_NS_SLICE) {
+    r->ns_dead_cap = (int64_t)4 * 1024 * 1024;
+    r->ns_dead = (double*)L.take((size_t)r->ns_dead_cap * 2 * 8);
+    r->ns_order = (int32_t*)L.take(N * 4);
+    r->ns_start = (int32_t*)L.take(N * 4);
+  }
+}
+
+}  // namespace
+
+namespace phi4 {
+ActionParams action_params(const phi4_run* r) {
+  ActionParams p;
+  p.L = r->cfg.L;
+  p.D = r->D;
+  p.N = r->cfg.N;
+  p.m2 = r->cfg.m2;
+  p.lam = r->cfg.lambda;
+  p.c_kin = r->cfg.c_kin;
+  p.c_mass = r->cfg.c_mass;
+  p.half_d_log2pi = 0.5 * r->D * log(2.0 * M_PI);
+  return p;
+}
+
+phi4_status read_status(phi4_run* r, uint32_t* st) {
+  CUDA_TRY(cudaMemcpyAsync(st, r->status, 4, cudaMemcpyDeviceToHost, r->stream));
+  CUDA_TRY(cudaStreamSynchronize(r->stream));
+  return PHI4_OK;
+}
+
+phi4_status status_to_error(uint32_t st) {
+  if (st & ST_TIMEOUT) { set_error("a bounded device wait gave up (status 0x%x)", st); return PHI4_ERR_TIMEOUT; }
+  if (st & ST_NONFINITE) { set_error("non-finite action or log-weight (status 0x%x)", st); return PHI4_ERR_NONFINITE; }
+  if (st & ST_NOT_PD) { set_error("covariance not positive definite (status 0x%x)", st); return PHI4_ERR_NOT_PD; }
+  return PHI4_OK;
+}
+
+// Covariance, regularised FP64 Cholesky (ridge x10 per failed try, up to 6 tries)
+// and the GEMM copy of the factor.
+phi4_status refit_factor(phi4_run* r, const void* pts, int n_pts) {
+  const int D = r->D;
+  cudaStream_t s = r->stream;
+  {
+    StageScope sc(r, STG_COV);
+    CUDA_TRY(launch_covariance(pts, r->cfg.precision, n_pts, D, r->sigma, r->cov_scratch, r->status, s));
+    CUDA_TRY(launch_ridge(r->sigma, D, r->cfg.chol_jitter_rel, r->scal + SC_RIDGE, s));
+    r->kernel_launches += 4;
+  }
+  for (int tries = 0; tries < 6; ++tries) {
+    {
+      StageScope sc(r, STG_CHOL);
+      CUDA_TRY(launch_copy_lower(r->sigma, r->chol, D, s));
+      CUDA_TRY(launch_cholesky(r->chol, D, r->scal + SC_RIDGE, r->status, s));
+      r->kernel_launches += 1 + cholesky_launches(D);
+    }
+    uint32_t st = 0;
+    phi4_status ps = read_status(r, &st);
+    if (ps != PHI4_OK) return ps;
+    if (st & (ST_TIMEOUT | ST_NONFINITE)) return status_to_error(st);
+    if (!(st & ST_NOT_PD)) {
+      StageScope sc(r, STG_CHOL);
+      CUDA_TRY(launch_factor_convert(r->chol, D, r->zdtype, r->Lg, r->ldl, s));
+      r->kernel_launches += 1;
+      return PHI4_OK;
+    }
+    double ridge = 0.0;
+    CUDA_TRY(cudaMemcpy(&ridge, r->scal + SC_RIDGE, 8, cudaMemcpyDeviceToHost));
+    ridge = ridge > 0.0 ? ridge * 10.0 : 1e-12;
+    const uint32_t clear = st & ~ST_NOT_PD;
+    CUDA_TRY(cudaMemcpy(r->scal + SC_RIDGE, &ridge, 8, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(r->status, &clear, 4, cudaMemcpyHostToDevice));
+  }
+  set_error("covariance not positive definite after 6 ridge increases");
+  return PHI4_ERR_NOT_PD;
+}
+
+}  // namespace phi4
+
+namespace {
+phi4_status propose(phi4_run* r, uint32_t step, uint32_t sweep) {
+  const int N = r->cfg.N, D = r->D;
+  cudaStream_t s = r->stream;
+  {
+    StageScope sc(r, STG_NORMALS);
+    CUDA_TRY(launch_normals(r->cfg.seed, r->cfg.stream_id, RNG_PROPOSE, step, sweep, 0, N, D, r->ldz, r->zdtype,
+                            r->Z, s));
+  }
+  r->kernel_launches += 2;
+  StageScope sc(r, STG_PROPOSE);
+  if (r->cfg.precision == PHI4_MIXED_BF16)
+    CUDA_TRY(launch_propose_tc((const float*)r->phi, (float*)r->prop, r->Z, r->ldz, r->Lg, r->ldl, N, D,
+                               (float)r->scale, r->status, s));
+  else
+    CUDA_TRY(launch_propose_simt(r->phi, r->prop, r->Z, r->Lg, r->dtype, N, D, r->scale, s));
+  return PHI4_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* phi4_last_error(void) { return g_err; }
+
+phi4_status phi4_device_sm_count(int32_t* out) {
+  ARG_CHECK(out, "out is NULL");
+  *out = sm_count();
+  return PHI4_OK;
+}
+
+const char* phi4_stage_name(int32_t stage) {
+  return (stage >= 0 && stage < PHI4_N_STAGES) ? kStageNames[stage] : "unknown";
+}
+
+phi4_status phi4_workspace_bytes(const phi4_config* cfg, size_t* bytes) {
+  phi4_status st = check_config(cfg);
+  if (st != PHI4_OK) return st;
+  ARG_CHECK(bytes, "bytes is NULL");
+  phi4_run tmp;
+  tmp.cfg = *cfg;
+  Layout L;
+  lay_out(&tmp, L);
+  *bytes = L.off;
+  return PHI4_OK;
+}
+
+phi4_status smc_init(const phi4_config* cfg, void* d_workspace, size_t workspace_bytes, void* stream,
+                     phi4_run** out) {
+  phi4_status st = check_config(cfg);
+  if (st != PHI4_OK) return st;
+  ARG_CHECK(out, "out is NULL");
+  ARG_CHECK(d_workspace && ((uintptr_t)d_workspace & 255) == 0, "workspace must be non-NULL and 256-byte aligned");
+  size_t need = 0;
+  phi4_workspace_bytes(cfg, &need);
+  if (workspace_bytes < need) {
+    set_error("workspace of %zu bytes, need %zu", workspace_bytes, need);
+    return PHI4_ERR_WORKSPACE;
+  }
+  if (cfg->precision == PHI4_MIXED_BF16 && !tc_available()) {
+    set_error("tensor-map encoder unavailable from the CUDA driver");
+    return PHI4_ERR_UNSUPPORTED;
+  }
+  phi4_run* r = new phi4_run();
+  r->cfg = *cfg;
+  r->D = cfg->L * cfg->L;
+  r->dtype = cfg->precision == PHI4_FP64 ? PHI4_DT_F64 : PHI4_DT_F32;
+  r->elem = cfg->precision == PHI4_FP64 ? 8 : 4;
+  r->stream = (cudaStream_t)stream;
+  r->scale = cfg->rw_scale > 0.0 ? cfg->rw_scale : 2.38 / sqrt((double)r->D);
+  Layout L;
+  L.base = (unsigned char*)d_workspace;
+  lay_out(r, L);
+  cudaStream_t s = r->stream;
+  auto fail = [&](cudaError_t e, const char* what) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    delete r;
+    return PHI4_ERR_CUDA;
+  };
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(r->scal, 0, SC_COUNT * 8, s)) != cudaSuccess) return fail(e, "memset");
+  if ((e = cudaMemsetAsync(r->status, 0, 16, s)) != cudaSuccess) return fail(e, "memset");
+  if ((e = launch_normals(cfg->seed, cfg->stream_id, RNG_INIT, 0, 0, 0, cfg->N, r->D, r->D, r->dtype, r->phi, s)) !=
+      cudaSuccess)
+    return fail(e, "initial draw");
+  const ActionParams ap = action_params(r);
+  if ((e = launch_action(r->phi, r->dtype, ap, r->S, r->sq, r->ell, cfg->keep_reference, s)) != cudaSuccess)
+    return fail(e, "initial action");
+  r->n_evals = cfg->N;
+  *out = r;
+  return PHI4_OK;
+}
+
+phi4_status smc_temper_step(phi4_run* r, double* beta_out) {
+  ARG_CHECK(r, "run is NULL");
+  ARG_CHECK(r->cfg.kind == PHI4_SMC_RW, "smc_temper_step on a nested-sampling run");
+  if (r->done) {
+    set_error("beta already 1");
+    return PHI4_ERR_DONE;
+  }
+  const phi4_config& c = r->cfg;
+  const int N = c.N, D = r->D;
+  cudaStream_t s = r->stream;
+  const uint32_t t = (uint32_t)(++r->t);
+  double* out = r->scal + SC_OUT;
+  {
+    StageScope sc(r, STG_BISECT);
+    CUDA_TRY(launch_bisect(r->ell, N, r->scal + SC_BETA, c.ess_target, c.bisect_iters, r->w, out, r->bisect_scratch,
+                           r->status, s));
+    CUDA_TRY(launch_logz_accumulate(out, r->scal + SC_KAHAN, r->scal + SC_BETA, s));
+    r->kernel_launches += 2;
+  }
+  {
+    StageScope sc(r, STG_RESAMPLE);
+    const uint4 wd = philox4x32_10_host(make_uint4(counter_word0(RNG_RESAMPLE, t), 0u, 0u, 0u),
+                                        philox_key(c.seed, c.stream_id));
+    CUDA_TRY(launch_resample(r->w, N, wd.x, nullptr, r->anc, r->resample_scratch, s));
+    r->kernel_launches += 1;
+  }
+  {
+    StageScope sc(r, STG_GATHER);
+    CUDA_TRY(launch_gather(r->phi, r->phi_alt, (size_t)D * r->elem, N, r->anc, s));
+    CUDA_TRY(launch_gather_f64(r->S, r->S_alt, N, r->anc, s));
+    CUDA_TRY(launch_gather_f64(r->sq, r->sq_alt, N, r->anc, s));
+    CUDA_TRY(launch_gather_f64(r->ell, r->ell_alt, N, r->anc, s));
+    r->kernel_launches += 4;
+    std::swap(r->phi, r->phi_alt);
+    std::swap(r->S, r->S_alt);
+    std::swap(r->sq, r->sq_alt);
+    std::swap(r->ell, r->ell_alt);
+  }
+  phi4_status ps = refit_factor(r, r->phi, N);
+  if (ps != PHI4_OK) return ps;
+  CUDA_TRY(cudaMemsetAsync(r->acc_count, 0, 4, s));
+  const ActionParams ap = action_params(r);
+  for (int sweep = 0; sweep < c.n_mcmc; ++sweep) {
+    ps = propose(r, t, (uint32_t)sweep);
+    if (ps != PHI4_OK) return ps;
+    StageScope sc(r, STG_ACCEPT);
+    CUDA_TRY(launch_accept(r->phi, r->prop, r->dtype, ap, c.keep_reference, r->S, r->sq, r->ell, r->scal + SC_BETA,
+                           c.seed, c.stream_id, t, (uint32_t)sweep, r->acc_count, r->status, s));
+    r->kernel_launches += 1;
+  }
+  r->n_evals += (int64_t)N * c.n_mcmc;
+  double h[8];
+  uint32_t st[2];
+  CUDA_TRY(cudaMemcpyAsync(h, out, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(st, r->status, 8, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (r->timing) collect_stage_times(r);
+  ps = status_to_error(st[0]);
+  if (ps != PHI4_OK) return ps;
+  r->beta = h[1];
+  r->last_ess = h[2];
+  r->last_acc = c.n_mcmc > 0 ? (double)st[1] / ((double)N * c.n_mcmc) : NAN;
+  if (r->beta >= 1.0) r->done = true;
+  if (beta_out) *beta_out = r->beta;
+  return PHI4_OK;
+}
+
+phi4_status ns_replace_step(phi4_run* r, int32_t* done_out) {
+  ARG_CHECK(r, "run is NULL");
+  ARG_CHECK(r->cfg.kind == PHI4_NS_SLICE, "ns_replace_step on an SMC run");
+  if (r->done) {
+    set_error("nested sampling already stopped");
+    return PHI4_ERR_DONE;
+  }
+  return ns_replace(r, done_out);
+}
+
+phi4_status smc_log_evidence(const phi4_run* rc, double* logz, double* logz_err) {
+  ARG_CHECK(rc, "run is NULL");
+  phi4_run* r = const_cast<phi4_run*>(rc);
+  if (r->cfg.kind == PHI4_SMC_RW) {
+    double k[2];
+    CUDA_TRY(cudaMemcpyAsync(k, r->scal + SC_KAHAN, 16, cudaMemcpyDeviceToHost, r->stream));
+    CUDA_TRY(cudaStreamSynchronize(r->stream));
+    if (logz) *logz = k[0];
+    if (logz_err) *logz_err = NAN;
+    return PHI4_OK;
+  }
+  return ns_evidence(r, logz, logz_err);
+}
+
+phi4_status smc_observables(const phi4_run* rc, phi4_obs* o) {
+  ARG_CHECK(rc && o, "NULL argument");
+  phi4_run* r = const_cast<phi4_run*>(rc);
+  const int N = r->cfg.N;
+  {
+    StageScope sc(r, STG_OBS);
+    CUDA_TRY(launch_magnetisation(r->phi, r->dtype, N, r->D, r->M, r->stream));
+  }
+  std::vector<double> M(N);
+  CUDA_TRY(cudaMemcpyAsync(M.data(), r->M, (size_t)N * 8, cudaMemcpyDeviceToHost, r->stream));
+  CUDA_TRY(cudaStreamSynchronize(r->stream));
+  if (r->timing) collect_stage_times(r);
+  double s1 = 0, sa = 0, s2 = 0, pos = 0, neg = 0;
+  for (int i = 0; i < N; ++i) {
+    s1 += M[i];
+    sa += fabs(M[i]);
+    s2 += M[i] * M[i];
+    if (M[i] > 0) pos += 1;
+    else if (M[i] < 0) neg += 1;
+  }
+  memset(o, 0, sizeof(*o));
+  o->beta = r->beta;
+  double lz = NAN, le = NAN;
+  phi4_status ps = smc_log_evidence(r, &lz, &le);
+  if (ps != PHI4_OK) return ps;
+  o->logz = lz;
+  o->logz_err = le;
+  o->mean_M = s1 / N;
+  o->mean_absM = sa / N;
+  o->mean_M2 = s2 / N;
+  o->chi = r->D * (o->mean_M2 - o->mean_M * o->mean_M);
+  o->mode_balance = neg > 0 ? pos / neg : (pos > 0 ? INFINITY : NAN);
+  o->ess = r->last_ess;
+  o->acc_rate = r->last_acc;
+  o->n_steps = r->t;
+  o->n_likelihood_evals = r->n_evals;
+  o->slice_capped = r->slice_capped;
+  return PHI4_OK;
+}
+
+phi4_status smc_copy_particles(const phi4_run* rc, void* dst, size_t bytes) {
+  ARG_CHECK(rc && dst, "NULL argument");
+  phi4_run* r = const_cast<phi4_run*>(rc);
+  const size_t need = (size_t)r->cfg.N * r->D * r->elem;
+  ARG_CHECK(bytes >= need, "destination of %zu bytes, need %zu", bytes, need);
+  CUDA_TRY(cudaMemcpyAsync(dst, r->phi, need, cudaMemcpyDefault, r->stream));
+  CUDA_TRY(cudaStreamSynchronize(r->stream));
+  return PHI4_OK;
+}
+
+phi4_status smc_load_particles(phi4_run* r, const void* src, size_t bytes) {
+  ARG_CHECK(r && src, "NULL argument");
+  const size_t need = (size_t)r->cfg.N * r->D * r->elem;
+  ARG_CHECK(bytes >= need, "source of %zu bytes, need %zu", bytes, need);
+  CUDA_TRY(cudaMemcpyAsync(r->phi, src, need, cudaMemcpyDefault, r->stream));
+  const ActionParams ap = action_params(r);
+  CUDA_TRY(launch_action(r->phi, r->dtype, ap, r->S, r->sq, r->ell, r->cfg.keep_reference, r->stream));
+  return PHI4_OK;
+}
+
+phi4_status smc_free(phi4_run* r) {
+  if (!r) return PHI4_OK;
+  cudaStreamSynchronize(r->stream);
+  for (auto& rec : r->pending) {
+    cudaEventDestroy(rec.a);
+    cudaEventDestroy(rec.b);
+  }
+  for (auto e : r->pool) cudaEventDestroy(e);
+  delete r;
+  return PHI4_OK;
+}
+
+phi4_status phi4_kernel_launches(const phi4_run* r, int64_t* out) {
+  ARG_CHECK(r && out, "NULL argument");
+  *out = r->kernel_launches;
+  return PHI4_OK;
+}
+
+phi4_status phi4_set_stage_timing(phi4_run* r, int32_t enable) {
+  ARG_CHECK(r, "run is NULL");
+  r->timing = enable != 0;
+  return PHI4_OK;
+}
+
+phi4_status phi4_stage_times(phi4_run* r, double* ms_out, int64_t* launches_out, int32_t reset) {
+  ARG_CHECK(r, "run is NULL");
+  CUDA_TRY(cudaStreamSynchronize(r->stream));
+  collect_stage_times(r);
+  for (int i = 0; i < PHI4_N_STAGES; ++i) {
+    if (ms_out) ms_out[i] = r->stage_ms[i];
+    if (launches_out) launches_out[i] = r->stage_launches[i];
+    if (reset) {
+      r->stage_ms[i] = 0;
+      r->stage_launches[i] = 0;
+    }
+  }
+  return PHI4_OK;
+}
+
+/* -------------------------- kernel-level API -------------------------- */
+
+phi4_status phi4_philox_normals(uint64_t seed, uint64_t stream_id, int32_t kind, uint32_t step, uint32_t sub,
+                                int32_t row0, int32_t n_rows, int32_t n_cols, int32_t ld, int32_t dtype, void* out,
+                                void* stream) {
+  ARG_CHECK(out, "out is NULL");
+  ARG_CHECK(n_rows >= 0 && n_cols >= 0 && ld >= n_cols && row0 >= 0, "bad sizes");
+  ARG_CHECK(dtype >= 0 && dtype <= 2, "dtype %d unknown", dtype);
+  ARG_CHECK(kind >= 0 && kind < 256, "kind %d outside [0, 256)", kind);
+  CUDA_TRY(launch_normals(seed, stream_id, (uint32_t)kind, step, sub, row0, n_rows, n_cols, ld, dtype, out,
+                          (cudaStream_t)stream));
+  return PHI4_OK;
+}
+
+phi4_status phi4_action(const void* phi, int32_t dtype, int32_t N, int32_t L, double m2, double lambda,
+                        double c_kin, double c_mass, double* S, double* sq, void* stream) {
+  ARG_CHECK(phi && S && sq, "NULL argument");
+  ARG_CHECK(N >= 0 && L >= 1 && L <= 128, "bad sizes");
+  ARG_CHECK(dtype == PHI4_DT_F64 || dtype == PHI4_DT_F32, "dtype must be F64 or F32");
+  ActionParams p{L, L * L, N, m2, lambda, c_kin, c_mass, 0.5 * L * L * log(2.0 * M_PI)};
+  CUDA_TRY(launch_action(phi, dtype, p, S, sq, nullptr, 0, (cudaStream_t)stream));
+  return PHI4_OK;
+}
+
+size_t phi4_bisect_scratch_bytes(int32_t N) { return bisect_scratch_bytes(N) + 256; }
+
+phi4_status phi4_ess_bisect(const double* ell, int32_t N, const double* beta_in, double rho, int32_t iters,
+                            double* w, double* out, void* scratch, size_t scratch_bytes, void* stream) {
+  ARG_CHECK(ell && beta_in && w && out && scratch, "NULL argument");
+  ARG_CHECK(N >= 1 && N <= 131072, "N = %d outside [1, 131072]", N);
+  ARG_CHECK(rho > 0 && rho < 1 && iters >= 0 && iters <= 200, "rho/iters invalid");
+  ARG_CHECK(scratch_bytes >= phi4_bisect_scratch_bytes(N), "scratch too small");
+  uint32_t* status = (uint32_t*)((unsigned char*)scratch + bisect_scratch_bytes(N));
+  cudaStream_t s = (cudaStream_t)stream;
+  CUDA_TRY(cudaMemsetAsync(status, 0, 4, s));
+  CUDA_TRY(launch_bisect(ell, N, beta_in, rho, iters, w, out, scratch, status, s));
+  uint32_t st = 0;
+  CUDA_TRY(cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return status_to_error(st & ~ST_BISECT_FLOOR);
+}
+
+size_t phi4_resample_scratch_bytes(int32_t N) { return resample_scratch_bytes(N); }
+
+phi4_status phi4_resample_systematic(const double* w, int32_t N, uint32_t U, int32_t* anc, void* scratch,
+                                     size_t scratch_bytes, void* stream) {
+  ARG_CHECK(w && anc && scratch, "NULL argument");
+  ARG_CHECK(N >= 1 && N <= 131072, "N = %d outside [1, 131072]", N);
+  ARG_CHECK(scratch_bytes >= resample_scratch_bytes(N), "scratch too small");
+  CUDA_TRY(launch_resample(w, N, U, nullptr, anc, scratch, (cudaStream_t)stream));
+  return PHI4_OK;
+}
+
+phi4_status phi4_gather_rows(const void* src, void* dst, size_t row_bytes, int32_t N, const int32_t* anc,
+                             void* stream) {
+  ARG_CHECK(src && dst && anc, "NULL argument");
+  ARG_CHECK(N >= 0, "N < 0");
+  CUDA_TRY(launch_gather(src, dst, row_bytes, N, anc, (cudaStream_t)stream));
+  return PHI4_OK;
+}
+
+size_t phi4_covariance_scratch_bytes(int32_t N, int32_t D, int32_t precision) {
+  return covariance_scratch_bytes(N, D, precision) + 256;
+}
+
+phi4_status phi4_covariance(const void* phi, int32_t precision, int32_t N, int32_t D, double* sigma, void* scratch,
+                            size_t scratch_bytes, void* stream) {
+  ARG_CHECK(phi && sigma && scratch, "NULL argument");
+  ARG_CHECK(N >= 2 && D >= 1 && D <= 16384, "bad sizes");
+  ARG_CHECK(precision >= 0 && precision <= 2, "precision %d unknown", precision);
+  ARG_CHECK(scratch_bytes >= phi4_covariance_scratch_bytes(N, D, precision), "scratch too small");
+  if (precision == PHI4_MIXED_BF16 && !tc_available()) {
+    set_error("tensor-map encoder unavailable");
+    return PHI4_ERR_UNSUPPORTED;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t* status = (uint32_t*)((unsigned char*)scratch + covariance_scratch_bytes(N, D, precision));
+  CUDA_TRY(cudaMemsetAsync(status, 0, 4, s));
+  CUDA_TRY(launch_covariance(phi, precision, N, D, sigma, scratch, status, s));
+  uint32_t st = 0;
+  CUDA_TRY(cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return status_to_error(st);
+}
+
+phi4_status phi4_cholesky(double* a, int32_t D, const double* d_ridge, uint32_t* d_status, void* stream) {
+  ARG_CHECK(a && d_status, "NULL argument");
+  ARG_CHECK(D >= 1 && D <= 16384, "D = %d outside [1, 16384]", D);
+  cudaStream_t s = (cudaStream_t)stream;
+  CUDA_TRY(launch_copy_lower(a, a, D, s));
+  CUDA_TRY(launch_cholesky(a, D, d_ridge, d_status, s));
+  return PHI4_OK;
+}
+
+size_t phi4_propose_scratch_bytes(int32_t N, int32_t D, int32_t precision) {
+  if (precision == PHI4_MIXED_BF16) return align256((size_t)N * (((size_t)D + 7) & ~(size_t)7) * 2) + 256;
+  return align256((size_t)N * D * (precision == PHI4_FP64 ? 8 : 4)) + 256;
+}
+
+phi4_status phi4_rw_propose(const void* phi, void* prop, const void* Lfac, int32_t ldl, int32_t precision, int32_t N,
+                            int32_t D, double scale, uint64_t seed, uint64_t stream_id, uint32_t step, uint32_t sweep,
+                            void* scratch, size_t scratch_bytes, void* stream) {
+  ARG_CHECK(phi && prop && Lfac && scratch, "NULL argument");
+  ARG_CHECK(N >= 1 && D >= 1 && D <= 16384, "bad sizes");
+  ARG_CHECK(precision >= 0 && precision <= 2, "precision %d unknown", precision);
+  ARG_CHECK(scratch_bytes >= phi4_propose_scratch_bytes(N, D, precision), "scratch too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (precision == PHI4_MIXED_BF16) {
+    ARG_CHECK(ldl >= D && ldl % 8 == 0, "ldl must be >= D and a multiple of 8");
+    ARG_CHECK(((uintptr_t)Lfac & 15) == 0 && ((uintptr_t)scratch & 15) == 0, "operands must be 16-byte aligned");
+    if (!tc_available()) {
+      set_error("tensor-map encoder unavailable");
+      return PHI4_ERR_UNSUPPORTED;
+    }
+    const int ldz = (D + 7) & ~7;
+    uint32_t* status = (uint32_t*)((unsigned char*)scratch + align256((size_t)N * ldz * 2));
+    CUDA_TRY(cudaMemsetAsync(status, 0, 4, s));
+    CUDA_TRY(launch_normals(seed, stream_id, RNG_PROPOSE, step, sweep, 0, N, D, ldz, PHI4_DT_BF16, scratch, s));
+    CUDA_TRY(launch_propose_tc((const float*)phi, (float*)prop, scratch, ldz, Lfac, ldl, N, D, (float)scale, status,
+                               s));
+    uint32_t st = 0;
+    CUDA_TRY(cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return status_to_error(st);
+  }
+  ARG_CHECK(ldl == D, "ldl must equal D for the FP64/FP32 forms");
+  const int dt = precision == PHI4_FP64 ? PHI4_DT_F64 : PHI4_DT_F32;
+  CUDA_TRY(launch_normals(seed, stream_id, RNG_PROPOSE, step, sweep, 0, N, D, D, dt, scratch, s));
+  CUDA_TRY(launch_propose_simt(phi, prop, scratch, Lfac, dt, N, D, scale, s));
+  return PHI4_OK;
+}
+
+phi4_status phi4_rw_accept(void* phi, const void* prop, int32_t dtype, int32_t N, int32_t L, double m2, double lambda,
+                           double c_kin, double c_mass, int32_t keep_reference, double* S, double* sq, double* ell,
+                           const double* beta, uint64_t seed, uint64_t stream_id, uint32_t step, uint32_t sweep,
+                           uint32_t* acc_count, void* stream) {
+  ARG_CHECK(phi && prop && S && sq && ell && beta && acc_count, "NULL argument");
+  ARG_CHECK(N >= 0 && L >= 1 && L <= 128, "bad sizes");
+  ARG_CHECK(dtype == PHI4_DT_F64 || dtype == PHI4_DT_F32, "dtype must be F64 or F32");
+  ActionParams p{L, L * L, N, m2, lambda, c_kin, c_mass, 0.5 * L * L * log(2.0 * M_PI)};
+  // the status word shares the counter's allocation: acc_count[1]
+  CUDA_TRY(launch_accept(phi, prop, dtype, p, keep_reference, S, sq, ell, beta, seed, stream_id, step, sweep,
+                         acc_count, acc_count + 1, (cudaStream_t)stream));
+  return PHI4_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+// Shared device helpers of the phi4smc kernels (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#define PHI4_DEV __device__ __forceinline__
+
+namespace phi4 {
+
+// Bits of the device status word.
+enum : uint32_t {
+  ST_NONFINITE = 1u,     // NaN/Inf in log-weights or the action
+  ST_NOT_PD = 2u,        // non-positive Cholesky pivot
+  ST_TIMEOUT = 4u,       // a bounded device wait gave up
+  ST_BISECT_FLOOR = 8u,  // no positive dbeta kept ESS >= rho N
+};
+
+// About one second of SM clock: every spin-wait in this library gives up after it.
+constexpr long long kSpinLimitCycles = 2000000000LL;
+
+PHI4_DEV double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+PHI4_DEV float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+PHI4_DEV double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+PHI4_DEV unsigned long long warp_incl_scan(unsigned long long v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// Block-wide sum of one double per thread; every thread gets the result.
+// `red` is shared scratch of >= 32 doubles. Deterministic order.
+PHI4_DEV double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+  if (wid == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) red[0] = t;
+  __syncthreads();
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+PHI4_DEV double block_max(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_max(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = (threadIdx.x < nw) ? red[threadIdx.x] : -INFINITY;
+  if (wid == 0) t = warp_max(t);
+  if (threadIdx.x == 0) red[0] = t;
+  __syncthreads();
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// Compensated float accumulator (Kahan): cheap on the FP32 pipes, keeps the
+// per-thread partial sums of float site terms close to their exact value.
+struct KahanF {
+  float s = 0.f, c = 0.f;
+  PHI4_DEV void add(float x) {
+    float y = x - c;
+    float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  PHI4_DEV double value() const { return (double)s - (double)c; }
+};
+
+template <typename T> PHI4_DEV T to_t(float x);
+template <> PHI4_DEV float to_t<float>(float x) { return x; }
+template <> PHI4_DEV __nv_bfloat16 to_t<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+
+}  // namespace phi4

@@ -1,0 +1,73 @@
+// Host-side launchers shared by the translation units of libphi4smc (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace phi4 {
+
+struct ActionParams {
+  int L, D, N;
+  double m2, lam, c_kin, c_mass;
+  double half_d_log2pi;  // (D/2) log(2 pi): minus the log-normaliser of N(0, I_D)
+};
+
+// Per-thread error message of the last failed call (capi.cu).
+void set_error(const char* fmt, ...);
+
+// kernels_rng.cu
+cudaError_t launch_normals(uint64_t seed, uint64_t stream_id, uint32_t kind, uint32_t step, uint32_t sub,
+                           int row0, int n_rows, int n_cols, int ld, int dtype, void* out, cudaStream_t s);
+
+// kernels_lattice.cu
+cudaError_t launch_action(const void* phi, int dtype, const ActionParams& p, double* S, double* sq,
+                          double* ell, int keep_reference, cudaStream_t s);
+cudaError_t launch_accept(void* phi, const void* prop, int dtype, const ActionParams& p, int keep_reference,
+                          double* S, double* sq, double* ell, const double* beta, uint64_t seed,
+                          uint64_t stream_id, uint32_t step, uint32_t sweep, uint32_t* acc_count,
+                          uint32_t* status, cudaStream_t s);
+cudaError_t launch_magnetisation(const void* phi, int dtype, int N, int D, double* M, cudaStream_t s);
+
+// kernels_temper.cu
+size_t bisect_scratch_bytes(int N);
+cudaError_t launch_bisect(const double* ell, int N, const double* beta_in, double rho, int iters, double* w,
+                          double* out, void* scratch, uint32_t* status, cudaStream_t s);
+cudaError_t launch_logz_accumulate(const double* out, double* logz_kahan, double* beta, cudaStream_t s);
+
+// kernels_resample.cu
+size_t resample_scratch_bytes(int N);
+cudaError_t launch_resample(const double* w, int N, uint32_t U, const uint32_t* U_dev, int32_t* anc,
+                            void* scratch, cudaStream_t s);
+cudaError_t launch_gather(const void* src, void* dst, size_t row_bytes, int N, const int32_t* anc,
+                          cudaStream_t s);
+cudaError_t launch_gather_f64(const double* src, double* dst, int N, const int32_t* anc, cudaStream_t s);
+
+// kernels_cov.cu
+size_t covariance_scratch_bytes(int N, int D, int precision);
+cudaError_t launch_covariance(const void* phi, int precision, int N, int D, double* sigma, void* scratch,
+                              uint32_t* status, cudaStream_t s);
+cudaError_t launch_ridge(const double* sigma, int D, double jitter_rel, double* ridge, cudaStream_t s);
+
+// kernels_chol.cu
+cudaError_t launch_copy_lower(const double* src, double* dst, int D, cudaStream_t s);
+cudaError_t launch_cholesky(double* a, int D, const double* ridge, uint32_t* status, cudaStream_t s);
+int cholesky_launches(int D);  // kernels one launch_cholesky enqueues
+cudaError_t launch_factor_convert(const double* Lc, int D, int dtype, void* out, int ld, cudaStream_t s);
+
+// kernels_gemm_simt.cu
+cudaError_t launch_propose_simt(const void* phi, void* prop, const void* Z, const void* Lf, int dtype, int N,
+                                int D, double scale, cudaStream_t s);
+cudaError_t launch_syrk_simt(const void* XcT, int dtype, int D, int N, int ldx, double inv_nm1, double* sigma,
+                             cudaStream_t s);
+
+// kernels_tc.cu (tcgen05 / TMA)
+bool tc_available();
+cudaError_t launch_propose_tc(const float* phi, float* prop, const void* Zb, int ldz, const void* Lb, int ldl,
+                              int N, int D, float scale, uint32_t* status, cudaStream_t s);
+cudaError_t launch_syrk_tc(const void* XcTb, int ldx, int D, int N, double inv_nm1, double* sigma,
+                           uint32_t* status, cudaStream_t s);
+
+// device properties (capi.cu)
+int sm_count();
+
+}  // namespace phi4

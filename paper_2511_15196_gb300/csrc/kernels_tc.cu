@@ -1,0 +1,376 @@
+// tcgen05 tensor-core GEMM with TMA operand staging (sm_103a), for the one
+// dense contraction of the sampler:
+//   proposal   Phi' = Phi + s Z L^T  (Z: N x D normals, L: D x D lower Cholesky
+//              factor; a 256-column tile [n0, n0+256) only needs k < n0+256), and
+//   covariance Sigma = Xc^T Xc / (N-1) on the lower triangle (Xc^T: D x N).
+// Both operands are bf16, K-contiguous, loaded by TMA into 128B-swizzled shared
+// tiles; one elected thread issues tcgen05.mma (M=128, N=256, K=16, fp32
+// accumulate) into one of two TMEM accumulators while four epilogue warps drain
+// the other one with tcgen05.ld and apply the epilogue to global memory.
+// Persistent CTAs (one per SM) walk a static tile list; warp 0 = TMA producer,
+// warp 1 = MMA issuer (and TMEM owner), warps 2..5 = epilogue.
+// Every mbarrier wait is bounded (about one second); a wait that gives up sets
+// ST_TIMEOUT and an abort flag that stops the other roles.
+#include <cuda.h>
+#include <algorithm>
+#include "internal.h"
+#include "common.cuh"
+
+namespace phi4 {
+namespace tc {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;
+constexpr int B_BYTES = BN * BK * 2;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int TMEM_COLS = 2 * BN;
+constexpr int NUM_THREADS = 192;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* alignment */ + 256 /* barriers */;
+
+// kind::f16 instruction descriptor: D fp32 (bits 4-5 = 1), A and B bf16 (bits 7-9,
+// 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+struct Params {
+  int M, Nn, K;
+  int tiles_m, tiles_n, num_tiles;
+  const float* phi;
+  float* prop;
+  float scale;
+  double* sigma;
+  double inv;
+  uint32_t* status;
+};
+
+PHI4_DEV uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+PHI4_DEV void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+PHI4_DEV void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+PHI4_DEV void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+PHI4_DEV bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for completion of the phase with the given parity.
+PHI4_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kSpinLimitCycles) return false;
+  }
+}
+
+PHI4_DEV void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor, K-major, 128-byte swizzle: start address >> 4
+// (bits 0-13), leading byte offset 16 >> 4 (unused for this layout), stride byte
+// offset 1024 >> 4 (8 rows x 128 B, bits 32-45), version 1 (bit 46), layout
+// SWIZZLE_128B = 2 (bits 61-63). Tile bases are 1024-byte aligned.
+PHI4_DEV uint64_t sdesc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+PHI4_DEV void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
+      : "memory");
+}
+PHI4_DEV void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+PHI4_DEV void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+PHI4_DEV void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+PHI4_DEV void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Tile u of the work list -> (mb, nb, number of K blocks).
+template <int MODE>
+PHI4_DEV void get_tile(const Params& p, int u, int& mb, int& nb, int& kblocks) {
+  if (MODE == 0) {
+    // proposal: column tiles in decreasing K extent (heaviest first)
+    nb = p.tiles_n - 1 - u / p.tiles_m;
+    mb = u % p.tiles_m;
+    const int kend = min(p.K, (nb + 1) * BN);
+    kblocks = (kend + BK - 1) / BK;
+  } else {
+    // covariance: tiles that touch the lower triangle, row-block by row-block
+    int m = 0, base = 0;
+    for (;;) {
+      const int cnt = min(p.tiles_n, (m * BM + BM - 1) / BN + 1);
+      if (u < base + cnt) break;
+      base += cnt;
+      ++m;
+    }
+    mb = m;
+    nb = u - base;
+    kblocks = (p.K + BK - 1) / BK;
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Params p) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 4);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  auto give_up = [&]() {
+    *abort_flag = 1;
+    atomicOr(p.status, ST_TIMEOUT);
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      for (int u = blockIdx.x; u < p.num_tiles && !*abort_flag; u += gridDim.x) {
+        int mb, nb, kblocks;
+        get_tile<MODE>(p, u, mb, nb, kblocks);
+        for (int kb = 0; kb < kblocks; ++kb) {
+          if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) { give_up(); break; }
+          uint8_t* sa = smem + stage * STAGE_BYTES;
+          mbar_expect_tx(&full[stage], STAGE_BYTES);
+          tma_load_2d(&tmA, &full[stage], sa, kb * BK, mb * BM);
+          tma_load_2d(&tmB, &full[stage], sa + A_BYTES, kb * BK, nb * BN);
+          if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int stage = 0, acc = 0;
+      uint32_t phase = 0, acc_phase = 0;
+      for (int u = blockIdx.x; u < p.num_tiles && !*abort_flag; u += gridDim.x) {
+        int mb, nb, kblocks;
+        get_tile<MODE>(p, u, mb, nb, kblocks);
+        if (!mbar_wait(&tempty[acc], acc_phase ^ 1u, abort_flag)) { give_up(); break; }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+        bool ok = true;
+        for (int kb = 0; kb < kblocks; ++kb) {
+          if (!mbar_wait(&full[stage], phase, abort_flag)) { give_up(); ok = false; break; }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(smem + stage * STAGE_BYTES), b0 = a0 + A_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk)
+            umma_bf16(d_tmem, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), (kb | kk) != 0);
+          umma_commit(&empty[stage]);
+          if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+        }
+        if (!ok) break;
+        umma_commit(&tfull[acc]);
+        acc ^= 1;
+        if (acc == 0) acc_phase ^= 1u;
+      }
+    }
+  } else {
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int r = q * 32 + lane;
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    for (int u = blockIdx.x; u < p.num_tiles; u += gridDim.x) {
+      int mb, nb, kblocks;
+      get_tile<MODE>(p, u, mb, nb, kblocks);
+      if (!mbar_wait(&tfull[acc], acc_phase, abort_flag)) { give_up(); break; }
+      tc_fence_after();
+      const int gm = mb * BM + r;
+      const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        float v[32];
+        tmem_ld32(trow + (uint32_t)(c * 32), v);
+        const int gn0 = nb * BN + c * 32;
+        if (gm < p.M && gn0 < p.Nn) {
+          if (MODE == 0) {
+            const size_t o = (size_t)gm * p.Nn + gn0;
+            if (gn0 + 32 <= p.Nn && (p.Nn & 3) == 0) {
+              const float4* src = reinterpret_cast<const float4*>(p.phi + o);
+              float4* dst = reinterpret_cast<float4*>(p.prop + o);
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                float4 f = src[j];
+                f.x += p.scale * v[4 * j];
+                f.y += p.scale * v[4 * j + 1];
+                f.z += p.scale * v[4 * j + 2];
+                f.w += p.scale * v[4 * j + 3];
+                dst[j] = f;
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if (gn0 + j < p.Nn) p.prop[o + j] = p.phi[o + j] + p.scale * v[j];
+            }
+          } else {
+            double* row = p.sigma + (size_t)gm * p.Nn;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int gn = gn0 + j;
+              if (gn < p.Nn && gn <= gm) row[gn] = (double)v[j] * p.inv;
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[acc]);
+      acc ^= 1;
+      if (acc == 0) acc_phase ^= 1u;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)ptr;
+  }
+  return fn;
+}
+
+// 2-D bf16 tensor map over rows x inner (row pitch `ld` elements), box 64 x box_rows, 128B swizzle.
+static bool make_map(CUtensorMap* map, const void* ptr, int inner, int rows, int ld, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  if (((uintptr_t)ptr & 15) || (ld % 8)) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1u, 1u};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int MODE>
+static cudaError_t launch(const CUtensorMap& a, const CUtensorMap& b, const Params& p, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  int grid = sm_count();
+  if (grid > p.num_tiles) grid = p.num_tiles;
+  if (grid < 1) return cudaSuccess;
+  tc_gemm_kernel<MODE><<<grid, NUM_THREADS, SMEM_BYTES, s>>>(a, b, p);
+  return cudaGetLastError();
+}
+
+}  // namespace tc
+
+bool tc_available() { return tc::encode_fn() != nullptr; }
+
+cudaError_t launch_propose_tc(const float* phi, float* prop, const void* Zb, int ldz, const void* Lb, int ldl, int N,
+                              int D, float scale, uint32_t* status, cudaStream_t s) {
+  CUtensorMap ma, mb;
+  if (!tc::make_map(&ma, Zb, D, N, ldz, tc::BM) || !tc::make_map(&mb, Lb, D, D, ldl, tc::BN))
+    return cudaErrorInvalidValue;
+  tc::Params p{};
+  p.M = N;
+  p.Nn = D;
+  p.K = D;
+  p.tiles_m = (N + tc::BM - 1) / tc::BM;
+  p.tiles_n = (D + tc::BN - 1) / tc::BN;
+  p.num_tiles = p.tiles_m * p.tiles_n;
+  p.phi = phi;
+  p.prop = prop;
+  p.scale = scale;
+  p.status = status;
+  return tc::launch<0>(ma, mb, p, s);
+}
+
+cudaError_t launch_syrk_tc(const void* XcTb, int ldx, int D, int N, double inv_nm1, double* sigma, uint32_t* status,
+                           cudaStream_t s) {
+  CUtensorMap ma, mb;
+  if (!tc::make_map(&ma, XcTb, N, D, ldx, tc::BM) || !tc::make_map(&mb, XcTb, N, D, ldx, tc::BN))
+    return cudaErrorInvalidValue;
+  tc::Params p{};
+  p.M = D;
+  p.Nn = D;
+  p.K = N;
+  p.tiles_m = (D + tc::BM - 1) / tc::BM;
+  p.tiles_n = (D + tc::BN - 1) / tc::BN;
+  int count = 0;
+  for (int m = 0; m < p.tiles_m; ++m) count += std::min(p.tiles_n, (m * tc::BM + tc::BM - 1) / tc::BN + 1);
+  p.num_tiles = count;
+  p.sigma = sigma;
+  p.inv = inv_nm1;
+  p.status = status;
+  return tc::launch<1>(ma, mb, p, s);
+}
+
+}  // namespace phi4

@@ -1,0 +1,118 @@
+// Run state shared by the drivers in capi.cu (SMC) and ns.cu (nested sampling).
+#pragma once
+#include <math.h>
+#include <vector>
+#include "../../include/phi4smc.h"
+#include "internal.h"
+
+static const char* const kStageNames[PHI4_N_STAGES] = {"bisect_reweight", "resample", "gather", "covariance",
+                                                 "cholesky",        "normals",  "propose", "accept",
+                                                 "observables",     "ns_select", "ns_slice", "other"};
+enum { STG_BISECT, STG_RESAMPLE, STG_GATHER, STG_COV, STG_CHOL, STG_NORMALS, STG_PROPOSE, STG_ACCEPT, STG_OBS,
+       STG_NS_SELECT, STG_NS_SLICE, STG_OTHER };
+
+// Device scalars of a run (one 256-byte block).
+enum { SC_OUT = 0 /* 8 doubles: bisection results */, SC_KAHAN = 8 /* 2 */, SC_BETA = 10, SC_RIDGE = 11,
+       SC_NS = 12 /* NS bookkeeping, 8 doubles */, SC_COUNT = 32 };
+
+struct phi4_run {
+  phi4_config cfg;
+  int D = 0, dtype = 0;
+  size_t elem = 0;
+  cudaStream_t stream = nullptr;
+  // device buffers (inside the caller's workspace)
+  void *phi = nullptr, *phi_alt = nullptr, *prop = nullptr, *Z = nullptr, *Lg = nullptr;
+  int ldz = 0, ldl = 0, zdtype = 0;
+  double *S = nullptr, *sq = nullptr, *ell = nullptr, *S_alt = nullptr, *sq_alt = nullptr, *ell_alt = nullptr;
+  double *w = nullptr, *M = nullptr, *sigma = nullptr, *chol = nullptr, *scal = nullptr;
+  int32_t* anc = nullptr;
+  uint32_t *status = nullptr, *acc_count = nullptr;
+  void *cov_scratch = nullptr, *bisect_scratch = nullptr, *resample_scratch = nullptr;
+  size_t cov_scratch_bytes = 0;
+  // NS state (device)
+  double *ns_dead = nullptr;  // [capacity][2]: (log L, log w)
+  int64_t ns_dead_cap = 0, ns_dead_n = 0;
+  int32_t *ns_order = nullptr, *ns_start = nullptr;
+  // host mirrors
+  double beta = 0.0, last_ess = NAN, last_acc = NAN, logz_ns = -INFINITY, logX = 0.0;
+  int64_t t = 0, n_evals = 0, slice_capped = 0;
+  bool done = false;
+  double scale = 0.0;
+  // stage timing
+  bool timing = false;
+  struct Rec { int stage; cudaEvent_t a, b; };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  double stage_ms[PHI4_N_STAGES] = {0};
+  int64_t kernel_launches = 0;  // kernels this run has launched
+  int64_t stage_launches[PHI4_N_STAGES] = {0};
+};
+
+
+namespace phi4 {
+struct StageScope {
+  phi4_run* r;
+  int stage;
+  cudaEvent_t a = nullptr, b = nullptr;
+  StageScope(phi4_run* run, int st) : r(run), stage(st) {
+    if (!r->timing) return;
+    a = take();
+    b = take();
+    cudaEventRecord(a, r->stream);
+  }
+  ~StageScope() {
+    if (!r->timing) return;
+    cudaEventRecord(b, r->stream);
+    r->pending.push_back({stage, a, b});
+  }
+  cudaEvent_t take() {
+    if (!r->pool.empty()) {
+      cudaEvent_t e = r->pool.back();
+      r->pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+};
+
+inline void collect_stage_times(phi4_run* r) {
+  for (auto& rec : r->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, rec.a, rec.b) == cudaSuccess) {
+      r->stage_ms[rec.stage] += ms;
+      r->stage_launches[rec.stage] += 1;
+    }
+    r->pool.push_back(rec.a);
+    r->pool.push_back(rec.b);
+  }
+  r->pending.clear();
+}
+
+
+ActionParams action_params(const phi4_run* r);
+phi4_status read_status(phi4_run* r, uint32_t* st);
+phi4_status status_to_error(uint32_t st);
+phi4_status refit_factor(phi4_run* r, const void* pts, int n_pts);
+phi4_status ns_replace(phi4_run* r, int32_t* done_out);
+phi4_status ns_evidence(phi4_run* r, double* logz, double* logz_err);
+
+}  // namespace phi4
+
+#define CUDA_TRY(expr)                                                                         \
+  do {                                                                                         \
+    cudaError_t e_ = (expr);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      phi4::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return PHI4_ERR_CUDA;                                                                    \
+    }                                                                                          \
+  } while (0)
+
+#define ARG_CHECK(cond, ...)        \
+  do {                              \
+    if (!(cond)) {                  \
+      phi4::set_error(__VA_ARGS__); \
+      return PHI4_ERR_ARG;          \
+    }                               \
+  } while (0)

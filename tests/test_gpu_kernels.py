@@ -1,0 +1,319 @@
+"""Per-kernel parity of the CUDA path (through the C ABI) with the FP64 oracle on
+identical seeded inputs. Tolerances:
+  * FP64 kernels: relative 1e-12 (action), rounding-order bounds elsewhere;
+  * FP32 kernels: action relative 1e-5; GEMMs within the worst-case float
+    dot-product bound gamma_K = K u / (1 - K u), u = 2^-24, on sum |a||b|;
+  * bf16 tensor-core GEMMs: operand rounding 2 u_b + u_b^2 (u_b = 2^-8) plus gamma_K,
+    both on sum |a||b|;
+  * integer and index results (resampling, gather): bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import inputs
+from oracle import covariance as ocov
+from oracle import lattice as olat
+from oracle import mutation as omut
+from oracle import philox as oph
+from oracle import resample as ores
+from oracle import tempering as otemp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2511_15196_gb300 as p  # noqa: E402
+
+U32 = 2.0 ** -24
+UB = 2.0 ** -8
+
+
+def cuda(x, dtype=None):
+    t = torch.as_tensor(np.ascontiguousarray(x))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def gamma(k, u=U32):
+    return k * u / (1 - k * u)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    assert torch.cuda.is_available()
+    p.lib()
+
+
+# ------------------------------------------------------------------ Philox normals
+
+@pytest.mark.parametrize("n_rows,n_cols,row0", [(3, 1, 0), (17, 7, 5), (64, 64, 0), (300, 257, 11), (2, 4096, 100)])
+def test_normals_fp64(n_rows, n_cols, row0):
+    out = torch.empty((n_rows, n_cols + 3), dtype=torch.float64, device="cuda")[:, :n_cols]
+    p.philox_normals(out, 1234, 5, p.RNG_PROPOSE, 9, 2, row0=row0)
+    ref = oph.normals(1234, 5, oph.KIND_PROPOSE, 9, 2, n_rows, n_cols, bits=32, row0=row0)
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16_normals"])
+def test_normals_single(dtype):
+    tdt = torch.float32 if dtype == "f32" else torch.bfloat16
+    out = torch.empty((513, 130), dtype=tdt, device="cuda")
+    p.philox_normals(out, 99, 0, p.RNG_INIT, 0, 0)
+    ref = oph.normals(99, 0, oph.KIND_INIT, 0, 0, 513, 130, bits=24)
+    got = out.float().cpu().numpy().astype(np.float64)
+    if dtype == "f32":
+        # float log / sqrt / sincospi of exact 24-bit uniforms: a few float ulps of |z| <= 6
+        np.testing.assert_allclose(got, ref, rtol=4 * U32, atol=8 * U32 * 6)
+    else:
+        np.testing.assert_allclose(got, ref, rtol=UB * 1.01, atol=8 * U32 * 6)
+
+
+# ------------------------------------------------------------------ action
+
+@pytest.mark.parametrize("L", [1, 2, 3, 8, 12, 31, 33, 64])
+@pytest.mark.parametrize("coef", [(-4.0, 8.0, 1.0, 1.0), (-4.0, 1.0, 0.5, 0.5), (1.0, 0.0, 1.0, 1.0)])
+def test_action_fp64(L, coef):
+    m2, lam, ck, cm = coef
+    N = 37
+    phi = inputs.broken_phase_fields(N, L * L, seed=L)
+    S, sq = p.action(cuda(phi), L, m2, lam, ck, cm)
+    Sr = olat.action(phi, L, m2, lam, ck, cm)
+    np.testing.assert_allclose(S.cpu().numpy(), Sr, rtol=1e-12, atol=1e-12 * np.abs(Sr).max())
+    np.testing.assert_allclose(sq.cpu().numpy(), olat.sq_norm(phi), rtol=1e-12)
+
+
+@pytest.mark.parametrize("L", [2, 8, 16, 32, 64])
+def test_action_fp32(L):
+    N = 200
+    phi = inputs.broken_phase_fields(N, L * L, seed=100 + L).astype(np.float32)
+    S, sq = p.action(cuda(phi), L, -4.0, 8.0)
+    Sr = olat.action(phi.astype(np.float64), L, -4.0, 8.0)
+    rel = np.abs(S.cpu().numpy() - Sr) / np.abs(Sr)
+    assert rel.max() <= 1e-5, rel.max()
+    np.testing.assert_allclose(sq.cpu().numpy(), olat.sq_norm(phi.astype(np.float64)), rtol=1e-6)
+
+
+# ------------------------------------------------------------------ ESS bisection + reweighting
+
+@pytest.mark.parametrize("N", [1, 2, 7, 1000, 1024, 8192, 50000])
+@pytest.mark.parametrize("beta,rho", [(0.0, 0.5), (0.3, 0.9), (0.97, 0.5)])
+def test_bisection_and_reweight(N, beta, rho):
+    ell = inputs.log_weights(N, seed=N, spread=20.0, offset=-500.0)
+    w, out = p.ess_bisect(cuda(ell), beta, rho, 64)
+    out = out.cpu().numpy()
+    d_ref, used = otemp.bisect_dbeta(ell, beta, rho, 64)
+    w_ref, inc_ref = otemp.reweight(ell, d_ref)
+    assert out[0] == pytest.approx(d_ref, rel=1e-12, abs=1e-300)
+    b_ref = 1.0 if d_ref >= 1.0 - beta else beta + d_ref
+    assert out[1] == pytest.approx(b_ref, rel=1e-12)
+    assert out[2] == pytest.approx(w_ref.sum() ** 2 / (w_ref ** 2).sum(), rel=1e-11)
+    assert out[3] == pytest.approx(inc_ref, rel=1e-12, abs=1e-12)
+    np.testing.assert_allclose(w.cpu().numpy(), w_ref, rtol=1e-11, atol=1e-300)
+    assert abs(out[4] - used) <= 2
+
+
+def test_bisection_steps_to_one():
+    ell = inputs.log_weights(4096, seed=3, spread=1e-4)
+    _, out = p.ess_bisect(cuda(ell), 0.6, 0.5)
+    out = out.cpu().numpy()
+    assert out[0] == 0.4 and out[1] == 1.0 and out[4] == 0
+
+
+# ------------------------------------------------------------------ resampling and gather
+
+@pytest.mark.parametrize("N", [1, 2, 3, 17, 1000, 1024, 8192, 65537])
+@pytest.mark.parametrize("kind", ["plain", "zeros", "heavy"])
+def test_resample_bit_exact(N, kind):
+    w = inputs.positive_weights(N, seed=N + len(kind), zeros=(N // 3 if kind == "zeros" else 0),
+                                heavy=(kind == "heavy"))
+    for U in (0, inputs.word32(N), 2 ** 32 - 1):
+        anc = p.resample_systematic(cuda(w), U).cpu().numpy()
+        ref = ores.systematic(w, U)
+        np.testing.assert_array_equal(anc, ref)
+
+
+def test_gather_rows_exact():
+    g = inputs.rng(4)
+    for (N, D, dt) in ((1000, 64, torch.float64), (513, 4096, torch.float32), (77, 9, torch.float32)):
+        src = torch.as_tensor(g.standard_normal((N, D))).to(dt).cuda()
+        anc = np.sort(g.integers(0, N, N)).astype(np.int32)
+        dst = p.gather_rows(src, cuda(anc))
+        assert torch.equal(dst, src[torch.as_tensor(anc, dtype=torch.long).cuda()])
+
+
+# ------------------------------------------------------------------ covariance
+
+def _cov_bound_terms(X):
+    Xc = X - X.mean(0)
+    A = np.abs(Xc).T @ np.abs(Xc) / (X.shape[0] - 1)
+    return Xc, A
+
+
+@pytest.mark.parametrize("N,L", [(1000, 12), (257, 24), (4096, 32), (300, 3)])
+@pytest.mark.parametrize("precision", [p.FP64, p.FP32, p.MIXED_BF16], ids=["fp64", "fp32", "bf16"])
+def test_covariance(N, L, precision):
+    D = L * L
+    X = inputs.broken_phase_fields(N, D, seed=N + D)
+    if precision != p.FP64:
+        X = X.astype(np.float32).astype(np.float64)
+    sig = p.covariance(cuda(X, torch.float64 if precision == p.FP64 else torch.float32), precision).cpu().numpy()
+    _, ref = ocov.sample_covariance(X)
+    _, A = _cov_bound_terms(X)
+    low = np.tril_indices(D)
+    err = np.abs(sig - ref)[low]
+    if precision == p.FP64:
+        bound = 1e-12 * A[low] + 1e-300
+    elif precision == p.FP32:
+        bound = (2 * U32 + gamma(N)) * A[low] * 1.0001 + 1e-30
+    else:
+        bound = (2 * UB + UB * UB + gamma(N)) * A[low] * 1.0001 + 1e-30
+    assert (err <= bound).all(), (err / bound).max()
+    # the strictly upper triangle is untouched
+    assert (sig[np.triu_indices(D, 1)] == 0).all()
+
+
+# ------------------------------------------------------------------ Cholesky
+
+@pytest.mark.parametrize("D", [1, 5, 63, 64, 65, 130, 1024])
+def test_cholesky_fp64(D):
+    A = inputs.spd_matrix(D, seed=D, cond=1e3)
+    ridge = 1e-3
+    a = cuda(A)
+    a, st = p.cholesky(a, ridge)
+    assert int(st.cpu()[0]) == 0
+    Lg = a.cpu().numpy()
+    ref = np.linalg.cholesky(A + ridge * np.eye(D))
+    np.testing.assert_allclose(Lg, ref, rtol=0, atol=1e-11 * np.abs(ref).max())
+    assert (np.triu(Lg, 1) == 0).all()
+
+
+def test_cholesky_flags_indefinite():
+    D = 100
+    A = inputs.spd_matrix(D, seed=1)
+    A[70, 70] = -1.0
+    _, st = p.cholesky(cuda(A), 0.0)
+    assert int(st.cpu()[0]) & 2
+
+
+# ------------------------------------------------------------------ proposal GEMM
+
+def _propose_ref(phi, Lc, scale, N, D, bits, step, sweep, seed=11, sid=3):
+    Z = oph.normals(seed, sid, oph.KIND_PROPOSE, step, sweep, N, D, bits=bits)
+    return omut.propose(phi, Z, Lc, scale), Z
+
+
+@pytest.mark.parametrize("N,L", [(300, 12), (1000, 8), (257, 32), (130, 10)])
+def test_propose_fp64(N, L):
+    D = L * L
+    phi = inputs.broken_phase_fields(N, D, seed=5)
+    Lc = inputs.lower_factor(D, seed=D)
+    s = 2.38 / L
+    got = p.rw_propose(cuda(phi), cuda(Lc), p.FP64, s, 11, 3, 4, 2).cpu().numpy()
+    ref, Z = _propose_ref(phi, Lc, s, N, D, 32, 4, 2)
+    bound = s * (gamma(D, 2.0 ** -53) * 4 * (np.abs(Z) @ np.abs(Lc).T) + 1e-13 * (np.ones_like(Z) @ np.abs(Lc).T)) \
+        + 4 * 2.0 ** -53 * np.abs(ref)
+    assert (np.abs(got - ref) <= bound).all()
+
+
+@pytest.mark.parametrize("N,L", [(300, 12), (1000, 8), (257, 32), (130, 10)])
+@pytest.mark.parametrize("precision", [p.FP32, p.MIXED_BF16], ids=["fp32", "bf16"])
+def test_propose_single(N, L, precision):
+    D = L * L
+    phi = inputs.broken_phase_fields(N, D, seed=6).astype(np.float32)
+    Lc = inputs.lower_factor(D, seed=D + 1)
+    s = 2.38 / L
+    if precision == p.FP32:
+        Lt = cuda(Lc, torch.float32)
+        Lr = Lt.double().cpu().numpy()
+        op_err = 0.0
+    else:
+        ld = (D + 7) // 8 * 8
+        Lt = torch.zeros((D, ld), dtype=torch.bfloat16, device="cuda")
+        Lt[:, :D] = cuda(Lc, torch.bfloat16)
+        Lt = Lt  # row pitch ld (multiple of 8)
+        Lr = Lc
+        op_err = 2 * UB + UB * UB
+    got = p.rw_propose(cuda(phi), Lt, precision, s, 11, 3, 4, 2).cpu().numpy().astype(np.float64)
+    ref, Z = _propose_ref(phi.astype(np.float64), Lr, s, N, D, 24, 4, 2)
+    absprod = np.abs(Z) @ np.abs(Lr).T
+    bound = s * ((op_err + gamma(D)) * absprod + 8 * U32 * 6 * (np.ones_like(Z) @ np.abs(Lr).T)) \
+        + 2 * U32 * (np.abs(ref) + np.abs(phi))
+    err = np.abs(got - ref)
+    assert (err <= bound).all(), (err / bound).max()
+
+
+def test_propose_bf16_full_size_sampled_rows():
+    # the timed workload's shape: N = 8192 particles, D = 4096 sites (L = 64)
+    N, L = 8192, 64
+    D = L * L
+    g = inputs.rng(8)
+    phi = (0.5 * g.standard_normal((N, D))).astype(np.float32)
+    Lc = np.tril(0.02 * g.standard_normal((D, D)))
+    Lc[np.diag_indices(D)] = 0.3 + 0.1 * g.random(D)
+    Lt = cuda(Lc, torch.bfloat16)
+    s = 2.38 / L
+    got = p.rw_propose(cuda(phi), Lt, p.MIXED_BF16, s, 21, 0, 1, 0)
+    rows = np.concatenate([g.choice(N, 48, replace=False), [0, N - 1]])
+    got = got[torch.as_tensor(rows).cuda()].cpu().numpy().astype(np.float64)
+    Z = np.stack([oph.normals(21, 0, oph.KIND_PROPOSE, 1, 0, 1, D, bits=24, row0=int(r))[0] for r in rows])
+    ref = phi[rows].astype(np.float64) + s * (Z @ Lc.T)
+    absprod = np.abs(Z) @ np.abs(Lc).T
+    bound = s * ((2 * UB + UB * UB + gamma(D)) * absprod + 8 * U32 * 6 * np.abs(Lc).sum(1)[None, :]) \
+        + 2 * U32 * (np.abs(ref) + np.abs(phi[rows]))
+    err = np.abs(got - ref)
+    assert (err <= bound).all(), (err / bound).max()
+
+
+# ------------------------------------------------------------------ accept
+
+@pytest.mark.parametrize("L,N", [(8, 1024), (33, 50), (2, 64)])
+@pytest.mark.parametrize("keep_reference", [False, True])
+def test_accept_fp64(L, N, keep_reference):
+    D = L * L
+    phi = inputs.broken_phase_fields(N, D, seed=L)
+    prop = phi + 0.05 * inputs.fields(N, D, seed=L + 1)
+    m2, lam, beta = -4.0, 8.0, 0.37
+    S = olat.action(phi, L, m2, lam)
+    sq = olat.sq_norm(phi)
+    ell = olat.tempering_loglik(S, sq, D, keep_reference)
+    tphi, tS, tsq, tell = cuda(phi), cuda(S), cuda(sq), cuda(ell)
+    cnt = p.rw_accept(tphi, cuda(prop), L, m2, lam, tS, tsq, tell, beta, 17, 0, 3, 1,
+                      keep_reference=keep_reference).cpu().numpy()
+    u = oph.uniform53(17, 0, oph.KIND_ACCEPT, 3, 1, np.arange(N))
+    rphi, rS, rsq, acc, _, _, la = omut.accept(phi, S, sq, prop, np.log(u), beta, L, m2, lam, 1.0, 1.0,
+                                                keep_reference)
+    near = np.abs(np.log(u) - la) < 1e-9
+    gphi = tphi.cpu().numpy()
+    gacc = np.all(gphi == prop, axis=1)
+    assert (gacc[~near] == acc[~near]).all()
+    assert cnt[0] == gacc.sum() and cnt[1] == 0
+    np.testing.assert_allclose(gphi[~near], rphi[~near], rtol=0, atol=0)
+    np.testing.assert_allclose(tS.cpu().numpy()[~near], rS[~near], rtol=1e-12)
+    np.testing.assert_allclose(tsq.cpu().numpy()[~near], rsq[~near], rtol=1e-12)
+    rell = olat.tempering_loglik(rS, rsq, D, keep_reference)
+    np.testing.assert_allclose(tell.cpu().numpy()[~near], rell[~near], rtol=1e-12)
+
+
+def test_accept_fp32_decisions():
+    L, N = 32, 2000
+    D = L * L
+    phi = inputs.broken_phase_fields(N, D, seed=2).astype(np.float32)
+    prop = (phi + 0.02 * inputs.fields(N, D, seed=3)).astype(np.float32)
+    m2, lam, beta = -4.0, 8.0, 0.8
+    phi64, prop64 = phi.astype(np.float64), prop.astype(np.float64)
+    S = olat.action(phi64, L, m2, lam)
+    sq = olat.sq_norm(phi64)
+    ell = olat.tempering_loglik(S, sq, D)
+    tphi = cuda(phi)
+    tS, tsq, tell = cuda(S), cuda(sq), cuda(ell)
+    p.rw_accept(tphi, cuda(prop), L, m2, lam, tS, tsq, tell, beta, 5, 0, 2, 0)
+    u = oph.uniform53(5, 0, oph.KIND_ACCEPT, 2, 0, np.arange(N))
+    _, _, _, acc, S2, _, la = omut.accept(phi64, S, sq, prop64, np.log(u), beta, L, m2, lam, 1.0, 1.0)
+    # the float action of the proposal is within 1e-5 relative: decisions can only differ inside that band
+    band = beta * 1e-5 * (np.abs(S2) + np.abs(S)) + 1e-9
+    near = np.abs(np.log(u) - la) < band
+    gacc = np.all(tphi.cpu().numpy() == prop, axis=1)
+    assert (gacc[~near] == acc[~near]).all()
+    assert 0.05 < acc.mean() < 0.95
