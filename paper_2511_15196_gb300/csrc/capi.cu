@@ -54,6 +54,7 @@ phi4_status check_config(const phi4_config* c) {
     ARG_CHECK(c->ns_n_delete >= 1 && c->ns_n_delete < c->N, "ns_n_delete = %d outside [1, N)", c->ns_n_delete);
     ARG_CHECK(c->ns_stop_frac > 0.0 && c->ns_stop_frac < 1.0, "ns_stop_frac invalid");
     ARG_CHECK(c->slice_max_shrink >= 1 && c->slice_max_shrink <= 1024, "slice_max_shrink invalid");
+    ARG_CHECK(c->N <= 8192, "nested sampling supports N <= 8192 live points (N = %d)", c->N);
   }
   ARG_CHECK(c->chol_jitter_rel >= 0.0 && isfinite(c->chol_jitter_rel), "chol_jitter_rel invalid");
   return PHI4_OK;
@@ -77,7 +78,7 @@ void lay_out(phi4_run* r, Layout& L) {
   r->phi = L.take((size_t)N * D * e);
   r->phi_alt = L.take((size_t)N * D * e);
   r->prop = L.take((size_t)N * D * e);
-  if (c.precision == PHI4_MIXED_BF16) {
+  if (c.precision == PHI4_MIXED_BF16 && c.kind == PHI4_SMC_RW) {
     r->ldz = (D + 7) & ~7;
     r->ldl = (D + 7) & ~7;
     r->zdtype = PHI4_DT_BF16;
@@ -105,11 +106,12 @@ void lay_out(phi4_run* r, Layout& L) {
   r->status = (uint32_t*)L.take(16);
   r->acc_count = r->status + 1;
   r->cov_scratch_bytes = covariance_scratch_bytes(N, D, c.precision);
+  r->ns_dead_n = 0;
   r->cov_scratch = L.take(r->cov_scratch_bytes);
   r->bisect_scratch = L.take(bisect_scratch_bytes(N));
   r->resample_scratch = L.take(resample_scratch_bytes(N));
   if (c.kind == PHI4_NS_SLICE) {
-    r->ns_dead_cap = (int64_t)4 * 1024 * 1024;
+    r->ns_dead_cap = std::min<int64_t>((int64_t)4 * 1024 * 1024, (int64_t)512 * N);
     r->ns_dead = (double*)L.take((size_t)r->ns_dead_cap * 2 * 8);
     r->ns_order = (int32_t*)L.take(N * 4);
     r->ns_start = (int32_t*)L.take(N * 4);
@@ -275,6 +277,12 @@ phi4_status smc_init(const phi4_config* cfg, void* d_workspace, size_t workspace
   if ((e = launch_action(r->phi, r->dtype, ap, r->S, r->sq, r->ell, cfg->keep_reference, s)) != cudaSuccess)
     return fail(e, "initial action");
   r->n_evals = cfg->N;
+  if (cfg->kind == PHI4_NS_SLICE) {
+    const double init_ns[4] = {0.0, -INFINITY, -INFINITY, 0.0};
+    if ((e = cudaMemcpyAsync(r->scal + SC_NS, init_ns, sizeof(init_ns), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      return fail(e, "NS init");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(e, "NS init");
+  }
   *out = r;
   return PHI4_OK;
 }

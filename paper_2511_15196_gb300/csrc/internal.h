@@ -67,6 +67,20 @@ cudaError_t launch_propose_tc(const float* phi, float* prop, const void* Zb, int
 cudaError_t launch_syrk_tc(const void* XcTb, int ldx, int D, int N, double inv_nm1, double* sigma,
                            uint32_t* status, cudaStream_t s);
 
+// kernels_ns.cu
+cudaError_t launch_ns_select(const double* logl, int N, int k, int32_t* order, double* ns, double* dead,
+                             long long dead_cap, uint32_t* status, cudaStream_t s);
+cudaError_t launch_ns_start(const void* live, int dtype, const int32_t* order, int N, int k, int D, uint64_t seed,
+                            uint64_t stream_id, uint32_t it, void* X, cudaStream_t s);
+cudaError_t launch_ns_slice(void* X, int dtype, double* logl_out, const void* Lf, int k, int L, double c_kin,
+                            double c_mass_m2, double lam, const double* lstar, int steps, int max_shrink,
+                            uint64_t seed, uint64_t stream_id, uint32_t it, uint32_t* capped, cudaStream_t s);
+cudaError_t launch_ns_replace(void* live, int dtype, double* logl, const int32_t* order, const void* X,
+                              const double* xl, int k, int D, cudaStream_t s);
+cudaError_t launch_ns_stop(const double* logl, int N, double log_stop, double* ns, cudaStream_t s);
+cudaError_t launch_ns_final(const double* dead, long long n_dead, const double* logl, int N, double* ns,
+                            cudaStream_t s);
+
 // device properties (capi.cu)
 int sm_count();
 
