@@ -5,9 +5,10 @@ Test infrastructure (see ``oracle/__init__``).
 
 Reading where the paper is silent: the covariance is the unweighted sample
 covariance of the (already resampled) population with divisor N - 1; a ridge
-delta * I with delta = jitter_rel * trace / D is added before factorising, and
-the ridge is multiplied by 10 (up to ``max_tries`` times) while the matrix is
-not numerically positive definite.
+delta * I with delta = jitter_rel * 10^level * trace / D is added before
+factorising, and the ridge is multiplied by 10 (up to ``max_tries`` times) while
+the matrix is not numerically positive definite. A run starts at level 0 and each
+outer step starts from the level that succeeded at the previous one.
 """
 import numpy as np
 
@@ -26,13 +27,16 @@ def cholesky_lower(A):
     return np.linalg.cholesky(np.asarray(A, dtype=np.float64))
 
 
-def regularised_cholesky(Sigma, jitter_rel=1e-8, max_tries=6):
-    """Returns (L, delta, tries) with L L^T = Sigma + delta I."""
+def regularised_cholesky(Sigma, jitter_rel=1e-8, max_tries=6, start_level=0):
+    """Returns (L, delta, tries, level) with L L^T = Sigma + delta I and
+    delta = jitter_rel 10^level trace / D."""
     D = Sigma.shape[0]
     delta = jitter_rel * np.trace(Sigma) / D
+    for _ in range(start_level):
+        delta *= 10.0
     for tries in range(1, max_tries + 1):
         try:
-            return cholesky_lower(Sigma + delta * np.eye(D)), delta, tries
+            return cholesky_lower(Sigma + delta * np.eye(D)), delta, tries, start_level + tries - 1
         except np.linalg.LinAlgError:
             delta *= 10.0
     raise np.linalg.LinAlgError("covariance not positive definite after %d ridge increases" % max_tries)

@@ -135,6 +135,7 @@ class NS:
         self.dead_logw = []
         self.it = 0
         self.capped = 0
+        self.ridge_level = 0
         self.done = False
 
     def remaining_log_evidence(self):
@@ -159,7 +160,8 @@ class NS:
             self.logZ = logaddexp(self.logZ, lj + logw)
         self.logX = logX
         _, Sigma = covariance.sample_covariance(self.live[survivors])
-        Lc, _, _ = covariance.regularised_cholesky(Sigma, c.jitter_rel)
+        Lc, _, _, self.ridge_level = covariance.regularised_cholesky(Sigma, c.jitter_rel,
+                                                                     start_level=self.ridge_level)
         new_pts = []
         for slot in range(k):
             w = philox.words(c.seed, c.stream, philox.KIND_NS_START, it, 0, [slot], [0])[0, 0]

@@ -7,7 +7,8 @@ Outer step at temperature index t (t = 1, 2, ...), in the paper's order:
   1. choose dbeta by ESS bisection (``tempering.bisect_dbeta``);
   2. reweight, log Z += log mean exp(dbeta ell) (Kahan);
   3. systematic resampling with offset word (KIND_RESAMPLE, t, 0, 0, 0)[0];
-  4. re-estimate the particle covariance and its Cholesky factor;
+  4. re-estimate the particle covariance and its Cholesky factor (ridge level
+     carried over from the previous step);
   5. n_mcmc random-walk Metropolis sweeps targeting gamma_{beta + dbeta};
   6. refresh ell from the cached S and |phi|^2.
 Initial particles are N(0, I_D) draws (KIND_INIT, 0, 0, particle, block).
@@ -59,6 +60,7 @@ class SMC:
         self.beta = 0.0
         self.logz = tempering.KahanSum()
         self.t = 0
+        self.ridge_level = 0
         self.history = []
 
     @property
@@ -85,7 +87,8 @@ class SMC:
         anc = resample.systematic(w, U)
         self.phi, self.S, self.sq = self.phi[anc], self.S[anc], self.sq[anc]
         _, Sigma = covariance.sample_covariance(self.phi)
-        Lc, delta, _ = covariance.regularised_cholesky(Sigma, c.jitter_rel)
+        Lc, delta, _, self.ridge_level = covariance.regularised_cholesky(Sigma, c.jitter_rel,
+                                                                         start_level=self.ridge_level)
         n_acc = 0
         for s in range(c.n_mcmc):
             self.phi, self.S, self.sq, acc = mutation.rw_sweep(

@@ -147,15 +147,16 @@ phi4_status status_to_error(uint32_t st) {
   return PHI4_OK;
 }
 
-// Covariance, regularised FP64 Cholesky (ridge x10 per failed try, up to 6 tries)
-// and the GEMM copy of the factor.
+// Covariance, regularised FP64 Cholesky and the GEMM copy of the factor. The ridge
+// starts at chol_jitter_rel * 10^level * trace / D with the level that succeeded at
+// the previous outer step, and grows x10 per failed try (up to 6 tries).
 phi4_status refit_factor(phi4_run* r, const void* pts, int n_pts) {
   const int D = r->D;
   cudaStream_t s = r->stream;
   {
     StageScope sc(r, STG_COV);
     CUDA_TRY(launch_covariance(pts, r->cfg.precision, n_pts, D, r->sigma, r->cov_scratch, r->status, s));
-    CUDA_TRY(launch_ridge(r->sigma, D, r->cfg.chol_jitter_rel, r->scal + SC_RIDGE, s));
+    CUDA_TRY(launch_ridge(r->sigma, D, r->cfg.chol_jitter_rel * pow(10.0, r->ridge_level), r->scal + SC_RIDGE, s));
     r->kernel_launches += 4;
   }
   for (int tries = 0; tries < 6; ++tries) {
@@ -170,6 +171,7 @@ phi4_status refit_factor(phi4_run* r, const void* pts, int n_pts) {
     if (ps != PHI4_OK) return ps;
     if (st & (ST_TIMEOUT | ST_NONFINITE)) return status_to_error(st);
     if (!(st & ST_NOT_PD)) {
+      r->ridge_level += tries;  // the next outer step starts from the level that worked
       StageScope sc(r, STG_CHOL);
       CUDA_TRY(launch_factor_convert(r->chol, D, r->zdtype, r->Lg, r->ldl, s));
       r->kernel_launches += 1;

@@ -45,6 +45,7 @@ struct phi4_run {
   std::vector<cudaEvent_t> pool;
   double stage_ms[PHI4_N_STAGES] = {0};
   int64_t kernel_launches = 0;  // kernels this run has launched
+  int ridge_level = 0;          // decades above chol_jitter_rel that made the last Cholesky succeed
   int64_t stage_launches[PHI4_N_STAGES] = {0};
 };
 

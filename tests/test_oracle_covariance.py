@@ -27,7 +27,14 @@ def test_cholesky_known_factor():
 def test_regularised_cholesky_rank_deficient():
     X = inputs.fields(5, 12, seed=1)  # N < D: rank 4
     _, S = covariance.sample_covariance(X)
-    L, delta, tries = covariance.regularised_cholesky(S, 1e-8)
-    assert delta > 0 and tries >= 1
+    L, delta, tries, level = covariance.regularised_cholesky(S, 1e-8)
+    assert delta > 0 and tries >= 1 and level == tries - 1
     np.testing.assert_allclose(L @ L.T, S + delta * np.eye(12), rtol=1e-8, atol=1e-10 * np.trace(S))
     assert delta == pytest.approx(1e-8 * np.trace(S) / 12 * 10 ** (tries - 1), rel=1e-12)
+    # a later step starts from the level that worked
+    L2, delta2, tries2, level2 = covariance.regularised_cholesky(S, 1e-8, start_level=level)
+    assert tries2 == 1 and level2 == level and delta2 == pytest.approx(delta, rel=1e-12)
+    # an SPD matrix at a raised level keeps that level and its larger ridge
+    A = inputs.spd_matrix(6, seed=2)
+    _, d3, t3, l3 = covariance.regularised_cholesky(A, 1e-8, start_level=3)
+    assert t3 == 1 and l3 == 3 and d3 == pytest.approx(1e-5 * np.trace(A) / 6, rel=1e-12)
