@@ -230,6 +230,24 @@ size_t phi4_resample_scratch_bytes(int32_t N);
 phi4_status phi4_resample_systematic(const double* w, int32_t N, uint32_t U, int32_t* anc,
                                      void* scratch, size_t scratch_bytes, void* stream);
 
+/* Same systematic resampling as phi4_resample_systematic, for callers that cannot
+ * allocate device memory and have no scratch buffer to pass: for example code that
+ * only receives the weight and ancestor buffers from a host framework whose allocator
+ * owns the device memory, or a latency-critical loop that must not enter any
+ * allocator. The paper has no counterpart; this entry point only changes where the
+ * scratch lives. It allocates nothing: its N 64-bit prefix sums use an array of
+ * PHI4_RESAMPLE_STATIC_MAX_N words (512 KiB) built into the library, which every GPU
+ * that loads the library keeps until the process exits.
+ * w: device double[N] (>= 0, max > 0); anc: device int32[N]; stream as elsewhere.
+ * N > PHI4_RESAMPLE_STATIC_MAX_N returns PHI4_ERR_ARG (use phi4_resample_systematic).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress
+ * with that device current) and caches it; make that first call before any stream
+ * capture. All calls share the one array and it keeps the last call's contents (each
+ * launch writes every entry it reads, so nothing needs clearing): calls that overlap
+ * on the GPU, e.g. on two streams, race and must be serialised by the caller. */
+#define PHI4_RESAMPLE_STATIC_MAX_N 65536
+phi4_status phi4_resample_systematic_static(const double* w, int32_t N, uint32_t U, int32_t* anc, void* stream);
+
 /* dst row i = src row anc[i] for i < N, rows of `row_bytes` (device buffers;
  * dst and src must not overlap). */
 phi4_status phi4_gather_rows(const void* src, void* dst, size_t row_bytes, int32_t N, const int32_t* anc,

@@ -107,6 +107,7 @@ _SIGS = {
     "phi4_ess_bisect": ([_P, _I32, _P, _F64, _I32, _P, _P, _P, _SZ, _P], _I32),
     "phi4_resample_scratch_bytes": ([_I32], _SZ),
     "phi4_resample_systematic": ([_P, _I32, _U32, _P, _P, _SZ, _P], _I32),
+    "phi4_resample_systematic_static": ([_P, _I32, _U32, _P, _P], _I32),
     "phi4_gather_rows": ([_P, _P, _SZ, _I32, _P, _P], _I32),
     "phi4_covariance_scratch_bytes": ([_I32, _I32, _I32], _SZ),
     "phi4_covariance": ([_P, _I32, _I32, _I32, _P, _P, _SZ, _P], _I32),
@@ -297,6 +298,15 @@ def resample_systematic(w, U, stream=None):
     nb = lib().phi4_resample_scratch_bytes(N)
     scratch = torch.empty(nb, dtype=torch.uint8, device=w.device)
     _check(lib().phi4_resample_systematic(_ptr(w), N, U, _ptr(anc), _ptr(scratch), nb, _stream(stream)))
+    return anc
+
+
+def resample_systematic_static(w, U, stream=None):
+    """phi4_resample_systematic without scratch memory from the caller (N <= 65536)."""
+    import torch
+    N = w.shape[0]
+    anc = torch.empty(N, dtype=torch.int32, device=w.device)
+    _check(lib().phi4_resample_systematic_static(_ptr(w), N, U, _ptr(anc), _stream(stream)))
     return anc
 
 

@@ -16,7 +16,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", "-diag-suppress", "177"]
 SOURCES = ["capi.cu", "ns.cu", "kernels_rng.cu", "kernels_lattice.cu", "kernels_temper.cu", "kernels_resample.cu",
-           "kernels_cov.cu", "kernels_chol.cu", "kernels_gemm_simt.cu", "kernels_tc.cu", "kernels_ns.cu"]
+           "kernels_cov.cu", "kernels_chol.cu", "kernels_gemm_simt.cu", "kernels_tc.cu", "kernels_ns.cu",
+           "resample_static.cu"]
 
 
 def nvcc():
