@@ -51,8 +51,76 @@ def parse():
     ap.add_argument("--n-mcmc", type=int, default=20)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=256, help="particles in the oracle's bounded sample")
+    ap.add_argument("--cpu-sample", type=int, default=2048, help="particles in the oracle's bounded sample")
+    ap.add_argument("--workload", default="single", choices=["single", "batch"],
+                    help="single: one L=64 run; batch: 64 independent runs of mixed lattice sizes")
+    ap.add_argument("--batch-runs", type=int, default=64)
     return ap.parse_args()
+
+
+def batch_configs(p, n_runs, n_mcmc):
+    """64 independent runs: L in {8,12,16,24,32} round-robin, N in {1024,2048,4096} by seed,
+    lambda in {4,8,16} by (run // 3), m2 = -4, float fields with bf16 tensor-core GEMMs."""
+    cfgs = []
+    for r in range(n_runs):
+        cfgs.append(p.Config(L=[8, 12, 16, 24, 32][r % 5], N=[1024, 2048, 4096][r % 3], m2=-4.0,
+                             lam=[4.0, 8.0, 16.0][(r // 3) % 3], precision=p.MIXED_BF16, n_mcmc=n_mcmc,
+                             ess_target=0.5, seed=r))
+    return cfgs
+
+
+def run_batch(a):
+    import torch
+    import paper_2511_15196_gb300 as p
+    rank, world, dist = dist_setup(a)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    n_mcmc = a.n_mcmc if a.n_mcmc != 20 else 10
+    cfgs = batch_configs(p, a.batch_runs, n_mcmc)
+    for c in cfgs:
+        c.seed += 100000 * rank
+    stream = torch.cuda.current_stream()
+    units = lambda b: sum(c.N * c.L * c.L * c.n_mcmc for c, m in zip(b.cfgs, b.members) if m.observables()["beta"] < 1.0)
+    b = p.Batch(cfgs)
+    for _ in range(a.warmup):
+        if b.temper_step() == 0:
+            b = p.Batch(cfgs)
+    l0 = sum(m.kernel_launches() for m in b.members)
+    total_units = 0
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    elapsed = 0.0
+    with Clocks(local) as clk:
+        for _ in range(a.steps):
+            u = units(b)
+            if u == 0:
+                b = p.Batch(cfgs)
+                u = units(b)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            b.temper_step()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            elapsed += ev0.elapsed_time(ev1)
+            total_units += u
+    launches = sum(m.kernel_launches() for m in b.members) - l0 + 2 * a.steps
+    elapsed = max_over_ranks(elapsed, dist)
+    value = world * total_units / (elapsed * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": elapsed / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": PREC_DTYPE["mixed"], "data": "synthetic (Philox N(0,I) initial fields)",
+            "config": {"workload": "batched SMC-RW: %d independent runs, L in {8,12,16,24,32} round-robin, "
+                                   "N in {1024,2048,4096} by seed, lambda in {4,8,16}, m2=-4, %d RWM sweeps, "
+                                   "ESS 0.5N, bf16 tensor-core GEMMs" % (a.batch_runs, n_mcmc),
+                       "runs": a.batch_runs, "l2": "per-step working set of all runs (~1.5 GB) larger than L2"},
+            "gpu_launches": launches, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line))
+    b.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
 
 
 def workload(a):
@@ -208,6 +276,8 @@ def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
+    if a.workload == "batch":
+        return run_batch(a)
     import torch
     import paper_2511_15196_gb300 as p
     rank, world, dist = dist_setup(a)
@@ -279,7 +349,8 @@ def main():
     acc = obs["acc_rate"] if obs["acc_rate"] == obs["acc_rate"] else 0.25
     work = {
         "propose": ("tensor", a.N * D * (D + 1), "TFLOP/s"),
-        "accept": ("hbm", a.N * D * 4 * (1 + acc), "GB/s"),
+        "accept": ("hbm", a.N * D * ((4 + 2) if prec == 2 else (8 if prec == 0 else 4)) + a.N * D * acc *
+                   (8 if prec == 0 else 4), "GB/s"),
         "normals": ("hbm", a.N * D * (2 if prec == 2 else 4 * (2 if prec == 0 else 1)), "GB/s"),
         "gather": ("hbm", 2 * a.N * D * (8 if prec == 0 else 4), "GB/s"),
         "cholesky": ("alu", D ** 3 / 3.0, "TFLOP/s"),

@@ -59,9 +59,10 @@ typedef enum { PHI4_SMC_RW = 0, PHI4_NS_SLICE = 1 } phi4_kind;
 
 /* Arithmetic forms of a run.
  * FP64:      fields, proposal GEMM, covariance and everything else in double.
- * FP32:      float fields, SIMT float proposal GEMM and covariance; float
- *            per-site action terms with compensated float partial sums that are
- *            combined in double; double log-weights, Cholesky and log Z.
+ * FP32:      the plain float form: float fields, SIMT float proposal GEMM,
+ *            covariance and Cholesky; float per-site action terms with compensated
+ *            float partial sums; the per-particle sums, log-weights and log Z stay
+ *            double (a few operations per particle).
  * MIXED_BF16: float fields; proposal and covariance GEMMs on the tcgen05 tensor
  *            cores with bf16 operands and fp32 accumulation; double Cholesky,
  *            acceptance test, log-weights and compensated log Z. */
@@ -168,7 +169,8 @@ phi4_status smc_copy_particles(const phi4_run* run, void* dst, size_t bytes);
  * stream (enqueued; returns after the copy is enqueued). */
 phi4_status smc_load_particles(phi4_run* run, const void* src, size_t bytes);
 
-/* Releases the handle (not the workspace). Synchronises the run's stream. */
+/* Releases the handle (not the workspace); for a batch handle, every member.
+ * Synchronises the run's stream. */
 phi4_status smc_free(phi4_run* run);
 
 /* Number of kernels the run has launched since smc_init (host counter). */
@@ -182,6 +184,31 @@ phi4_status phi4_kernel_launches(const phi4_run* run, int64_t* out);
 phi4_status phi4_set_stage_timing(phi4_run* run, int32_t enable);
 phi4_status phi4_stage_times(phi4_run* run, double* ms_out, int64_t* launches_out, int32_t reset);
 const char* phi4_stage_name(int32_t stage);
+
+/* ------------------------------------------------------------------------ */
+/* Batched form: many independent SMC runs advanced together.                */
+/* ------------------------------------------------------------------------ */
+
+/* Workspace bytes for `n_runs` SMC runs with configurations cfgs[0..n_runs-1]
+ * (different L, N, couplings, precisions and seeds allowed; N <= 4096 each). */
+phi4_status phi4_batch_workspace_bytes(const phi4_config* cfgs, int32_t n_runs, size_t* bytes);
+
+/* Creates the runs in one caller workspace (>= phi4_batch_workspace_bytes, 256-byte
+ * aligned) and returns a batch handle. Each member gets its own CUDA stream so the
+ * members' kernels overlap on the GPU; `stream` is the caller's stream, which every
+ * batch call orders itself after and joins before returning. */
+phi4_status smc_init_batch(const phi4_config* cfgs, int32_t n_runs, void* d_workspace, size_t workspace_bytes,
+                           void* stream, phi4_run** out);
+
+/* One temperature for every member still below beta = 1 (the same steps as
+ * smc_temper_step, stage-interleaved across members; the ESS bisection runs in one
+ * CTA per member). *n_active_out = members still below beta = 1 afterwards.
+ * Synchronises. PHI4_ERR_DONE when no member is active. */
+phi4_status smc_temper_step_batch(phi4_run* batch, int32_t* n_active_out);
+
+/* Borrowed handle of member r for smc_log_evidence / smc_observables /
+ * smc_copy_particles (owned by the batch; smc_free on it is rejected). */
+phi4_status phi4_batch_member(phi4_run* batch, int32_t r, phi4_run** member_out);
 
 /* ------------------------------------------------------------------------ */
 /* Kernel-level API: each step of the path on caller buffers.                */
@@ -268,16 +295,28 @@ phi4_status phi4_covariance(const void* phi, int32_t precision, int32_t N, int32
  * row-major D x D double matrix `a` (device) holds Sigma; `*d_ridge` (device
  * double) is added to its diagonal; on exit the lower triangle holds L and the
  * strictly upper triangle is zeroed. A non-positive pivot sets bit 2 of
- * `*d_status` (device uint32) and stops the factorisation. Blocked right-looking,
- * all arithmetic double. */
-phi4_status phi4_cholesky(double* a, int32_t D, const double* d_ridge, uint32_t* d_status, void* stream);
+ * `*d_status` (device uint32) and stops the factorisation. Blocked right-looking
+ * with 64 x 64 blocks, all arithmetic double; the inverses of the diagonal blocks
+ * (used for the panel solves) live in `scratch` (device, phi4_cholesky_scratch_bytes). */
+size_t phi4_cholesky_scratch_bytes(int32_t D);
+phi4_status phi4_cholesky(double* a, int32_t D, const double* d_ridge, uint32_t* d_status, void* scratch,
+                          size_t scratch_bytes, void* stream);
+
+/* The same factorisation in float for the plain FP32 form: `sigma` (device double,
+ * lower triangle read) is rounded to float into `a` (device float[D*D], row-major),
+ * *d_ridge is added to the diagonal and `a` is factorised in place (lower L, zeros
+ * above). Non-positive pivot: bit 2 of *d_status. */
+phi4_status phi4_cholesky_f32(const double* sigma, float* a, int32_t D, const double* d_ridge, uint32_t* d_status,
+                              void* scratch, size_t scratch_bytes, void* stream);
 
 /* Random-walk proposal (App. A): prop = phi + scale * Z L^T with Z the normals of
  * (PHI4_RNG_PROPOSE, step, sweep, particle, block) drawn for this call.
  * precision FP64/FP32: L double/float [D][D] lower (device), SIMT GEMM.
- * MIXED_BF16: L bf16 [D][ldl] (ldl >= D, multiple of 8), tcgen05 GEMM with fp32
- * accumulation. phi, prop: device [N][D] (F64 for FP64, else F32).
- * `scratch` holds Z (phi4_propose_scratch_bytes). */
+ * MIXED_BF16: L bf16 [D][ldl] (ldl >= D, multiple of 8); the tcgen05 GEMM (bf16
+ * operands, fp32 accumulation) writes the increment scale * Z L^T rounded to fp16,
+ * and prop = phi + that increment (the run pipeline instead hands the increment to
+ * phi4_rw_accept_delta). phi, prop: device [N][D] (F64 for FP64, else F32).
+ * `scratch` holds Z (and the fp16 increment) (phi4_propose_scratch_bytes). */
 size_t phi4_propose_scratch_bytes(int32_t N, int32_t D, int32_t precision);
 phi4_status phi4_rw_propose(const void* phi, void* prop, const void* Lfac, int32_t ldl, int32_t precision,
                             int32_t N, int32_t D, double scale, uint64_t seed, uint64_t stream_id,
@@ -295,6 +334,16 @@ phi4_status phi4_rw_accept(void* phi, const void* prop, int32_t dtype, int32_t N
                            double lambda, double c_kin, double c_mass, int32_t keep_reference,
                            double* S, double* sq, double* ell, const double* beta, uint64_t seed,
                            uint64_t stream_id, uint32_t step, uint32_t sweep, uint32_t* acc_count, void* stream);
+
+/* The accept step of the mixed form: as phi4_rw_accept with float fields and the
+ * proposal phi' = phi + delta, delta the fp16 increment (device __half [N][D]) of the
+ * tensor-core proposal; phi' is formed while phi is loaded, so neither phi' nor the
+ * full-precision increment is stored. Requires L % 4 == 0 (float4 site groups within
+ * a lattice row) and D <= 8192. acc_count: device uint32[2] as for phi4_rw_accept. */
+phi4_status phi4_rw_accept_delta(float* phi, const void* delta_f16, int32_t N, int32_t L, double m2, double lambda,
+                                 double c_kin, double c_mass, int32_t keep_reference, double* S, double* sq,
+                                 double* ell, const double* beta, uint64_t seed, uint64_t stream_id, uint32_t step,
+                                 uint32_t sweep, uint32_t* acc_count, void* stream);
 
 #ifdef __cplusplus
 }

@@ -97,6 +97,10 @@ _SIGS = {
     "smc_copy_particles": ([_P, _P, _SZ], _I32),
     "smc_load_particles": ([_P, _P, _SZ], _I32),
     "smc_free": ([_P], _I32),
+    "phi4_batch_workspace_bytes": ([_P, _I32, ctypes.POINTER(_SZ)], _I32),
+    "smc_init_batch": ([_P, _I32, _P, _SZ, _P, ctypes.POINTER(_P)], _I32),
+    "smc_temper_step_batch": ([_P, ctypes.POINTER(_I32)], _I32),
+    "phi4_batch_member": ([_P, _I32, ctypes.POINTER(_P)], _I32),
     "phi4_kernel_launches": ([_P, ctypes.POINTER(ctypes.c_int64)], _I32),
     "phi4_set_stage_timing": ([_P, _I32], _I32),
     "phi4_stage_times": ([_P, ctypes.POINTER(_F64), ctypes.POINTER(ctypes.c_int64), _I32], _I32),
@@ -111,11 +115,15 @@ _SIGS = {
     "phi4_gather_rows": ([_P, _P, _SZ, _I32, _P, _P], _I32),
     "phi4_covariance_scratch_bytes": ([_I32, _I32, _I32], _SZ),
     "phi4_covariance": ([_P, _I32, _I32, _I32, _P, _P, _SZ, _P], _I32),
-    "phi4_cholesky": ([_P, _I32, _P, _P, _P], _I32),
+    "phi4_cholesky_scratch_bytes": ([_I32], _SZ),
+    "phi4_cholesky": ([_P, _I32, _P, _P, _P, _SZ, _P], _I32),
+    "phi4_cholesky_f32": ([_P, _P, _I32, _P, _P, _P, _SZ, _P], _I32),
     "phi4_propose_scratch_bytes": ([_I32, _I32, _I32], _SZ),
     "phi4_rw_propose": ([_P, _P, _P, _I32, _I32, _I32, _I32, _F64, _U64, _U64, _U32, _U32, _P, _SZ, _P], _I32),
     "phi4_rw_accept": ([_P, _P, _I32, _I32, _I32, _F64, _F64, _F64, _F64, _I32, _P, _P, _P, _P, _U64, _U64, _U32,
                         _U32, _P, _P], _I32),
+    "phi4_rw_accept_delta": ([_P, _P, _I32, _I32, _F64, _F64, _F64, _F64, _I32, _P, _P, _P, _P, _U64, _U64, _U32,
+                              _U32, _P, _P], _I32),
 }
 
 
@@ -253,6 +261,72 @@ class Run:
             pass
 
 
+class _Member(Run):
+    """Borrowed view of one member of a Batch (owned by the batch)."""
+
+    def __init__(self, cfg, handle, device):
+        self.cfg = cfg
+        self.handle = handle
+        self._device = device
+
+    @property
+    def workspace(self):
+        import torch
+        return torch.empty(0, device=self._device)
+
+    def close(self):
+        self.handle = None
+
+
+class Batch:
+    """Many independent SMC runs advanced together (smc_init_batch / smc_temper_step_batch)."""
+
+    def __init__(self, cfgs, device="cuda", stream=None):
+        import torch
+        self.cfgs = list(cfgs)
+        arr = (CConfig * len(self.cfgs))(*[c.to_c() for c in self.cfgs])
+        self._arr = arr
+        n = _SZ()
+        _check(lib().phi4_batch_workspace_bytes(ctypes.cast(arr, _P), len(self.cfgs), ctypes.byref(n)))
+        self.workspace = torch.empty(n.value + 256, dtype=torch.uint8, device=device)
+        ptr = (self.workspace.data_ptr() + 255) & ~255
+        h = _P()
+        _check(lib().smc_init_batch(ctypes.cast(arr, _P), len(self.cfgs), ctypes.c_void_p(ptr), n.value,
+                                    _stream(stream), ctypes.byref(h)))
+        self.handle = h
+        self.members = []
+        for r, c in enumerate(self.cfgs):
+            mh = _P()
+            _check(lib().phi4_batch_member(self.handle, r, ctypes.byref(mh)))
+            self.members.append(_Member(c, mh, self.workspace.device))
+
+    def temper_step(self):
+        n = _I32()
+        _check(lib().smc_temper_step_batch(self.handle, ctypes.byref(n)))
+        return n.value
+
+    def run(self, max_steps=100000):
+        steps = 0
+        while steps < max_steps:
+            steps += 1
+            if self.temper_step() == 0:
+                break
+        return [m.observables() for m in self.members]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            for m in self.members:
+                m.handle = None
+            lib().smc_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ---------------------------------------------------------------- kernel level
 
 def philox_normals(out, seed, stream_id, kind, step, sub, row0=0, dtype=None, stream=None):
@@ -334,7 +408,22 @@ def cholesky(a, ridge=0.0, stream=None):
     D = a.shape[0]
     r = torch.tensor([ridge], dtype=torch.float64, device=a.device)
     st = torch.zeros(1, dtype=torch.int32, device=a.device)
-    _check(lib().phi4_cholesky(_ptr(a), D, _ptr(r), _ptr(st), _stream(stream)))
+    nb = lib().phi4_cholesky_scratch_bytes(D)
+    scratch = torch.empty(nb, dtype=torch.uint8, device=a.device)
+    _check(lib().phi4_cholesky(_ptr(a), D, _ptr(r), _ptr(st), _ptr(scratch), nb, _stream(stream)))
+    return a, st
+
+
+def cholesky_f32(sigma, ridge=0.0, stream=None):
+    """Float Cholesky of the lower triangle of a D x D double CUDA tensor; returns (L32, status)."""
+    import torch
+    D = sigma.shape[0]
+    a = torch.empty((D, D), dtype=torch.float32, device=sigma.device)
+    r = torch.tensor([ridge], dtype=torch.float64, device=sigma.device)
+    st = torch.zeros(1, dtype=torch.int32, device=sigma.device)
+    nb = lib().phi4_cholesky_scratch_bytes(D)
+    scratch = torch.empty(nb, dtype=torch.uint8, device=sigma.device)
+    _check(lib().phi4_cholesky_f32(_ptr(sigma), _ptr(a), D, _ptr(r), _ptr(st), _ptr(scratch), nb, _stream(stream)))
     return a, st
 
 
@@ -361,6 +450,19 @@ def rw_accept(phi, prop, L, m2, lam, S, sq, ell, beta, seed, stream_id, step, sw
     _check(lib().phi4_rw_accept(_ptr(phi), _ptr(prop), dt, N, L, m2, lam, c_kin, c_mass, int(keep_reference),
                                 _ptr(S), _ptr(sq), _ptr(ell), _ptr(b), seed, stream_id, step, sweep, _ptr(cnt),
                                 _stream(stream)))
+    return cnt
+
+
+def rw_accept_delta(phi, delta, L, m2, lam, S, sq, ell, beta, seed, stream_id, step, sweep, c_kin=1.0, c_mass=1.0,
+                    keep_reference=False, stream=None):
+    """Accept step of the mixed form with proposal phi + delta (delta: float16 tensor); in place."""
+    import torch
+    N = phi.shape[0]
+    b = torch.tensor([beta], dtype=torch.float64, device=phi.device)
+    cnt = torch.zeros(2, dtype=torch.int32, device=phi.device)
+    _check(lib().phi4_rw_accept_delta(_ptr(phi), _ptr(delta), N, L, m2, lam, c_kin, c_mass, int(keep_reference),
+                                      _ptr(S), _ptr(sq), _ptr(ell), _ptr(b), seed, stream_id, step, sweep, _ptr(cnt),
+                                      _stream(stream)))
     return cnt
 
 

@@ -102,6 +102,7 @@ void lay_out(phi4_run* r, Layout& L) {
   r->anc = (int32_t*)L.take(N * 4);
   r->sigma = (double*)L.take((size_t)D * D * 8);
   r->chol = (double*)L.take((size_t)D * D * 8);
+  r->chol_aux = L.take(cholesky_aux_bytes(D));
   r->scal = (double*)L.take(SC_COUNT * 8);
   r->status = (uint32_t*)L.take(16);
   r->acc_count = r->status + 1;
@@ -150,7 +151,8 @@ phi4_status status_to_error(uint32_t st) {
 // Covariance, regularised FP64 Cholesky and the GEMM copy of the factor. The ridge
 // starts at chol_jitter_rel * 10^level * trace / D with the level that succeeded at
 // the previous outer step, and grows x10 per failed try (up to 6 tries).
-phi4_status refit_factor(phi4_run* r, const void* pts, int n_pts) {
+// refit_enqueue: covariance, ridge and the first factorisation attempt (no host sync).
+phi4_status refit_enqueue(phi4_run* r, const void* pts, int n_pts) {
   const int D = r->D;
   cudaStream_t s = r->stream;
   {
@@ -159,33 +161,65 @@ phi4_status refit_factor(phi4_run* r, const void* pts, int n_pts) {
     CUDA_TRY(launch_ridge(r->sigma, D, r->cfg.chol_jitter_rel * pow(10.0, r->ridge_level), r->scal + SC_RIDGE, s));
     r->kernel_launches += 4;
   }
-  for (int tries = 0; tries < 6; ++tries) {
-    {
-      StageScope sc(r, STG_CHOL);
-      CUDA_TRY(launch_copy_lower(r->sigma, r->chol, D, s));
-      CUDA_TRY(launch_cholesky(r->chol, D, r->scal + SC_RIDGE, r->status, s));
-      r->kernel_launches += 1 + cholesky_launches(D);
-    }
-    uint32_t st = 0;
-    phi4_status ps = read_status(r, &st);
-    if (ps != PHI4_OK) return ps;
+  return factor_attempt(r);
+}
+
+phi4_status factor_attempt(phi4_run* r) {
+  const int D = r->D;
+  cudaStream_t s = r->stream;
+  const bool f32 = r->cfg.precision == PHI4_FP32;  // the plain float form factors in float
+  StageScope sc(r, STG_CHOL);
+  if (f32) {
+    CUDA_TRY(launch_cholesky_f32(r->sigma, (float*)r->chol, D, r->scal + SC_RIDGE, r->status, r->chol_aux, s,
+                                 r->side, r->evA, r->evB));
+  } else {
+    CUDA_TRY(launch_copy_lower(r->sigma, r->chol, D, s));
+    CUDA_TRY(launch_cholesky(r->chol, D, r->scal + SC_RIDGE, r->status, r->chol_aux, s, r->side, r->evA, r->evB));
+  }
+  r->kernel_launches += 1 + cholesky_launches(D);
+  return PHI4_OK;
+}
+
+// refit_check: with the attempt's status word `st` already read, retry with larger
+// ridges until the factorisation succeeds (synchronous), then enqueue the conversion.
+phi4_status refit_check(phi4_run* r, uint32_t st) {
+  const int D = r->D;
+  cudaStream_t s = r->stream;
+  for (int tries = 1;; ++tries) {
     if (st & (ST_TIMEOUT | ST_NONFINITE)) return status_to_error(st);
     if (!(st & ST_NOT_PD)) {
-      r->ridge_level += tries;  // the next outer step starts from the level that worked
-      StageScope sc(r, STG_CHOL);
-      CUDA_TRY(launch_factor_convert(r->chol, D, r->zdtype, r->Lg, r->ldl, s));
+      r->ridge_level += tries - 1;  // the next outer step starts from the level that worked
+      StageScope sc(r, STG_OTHER);
+      if (r->cfg.precision == PHI4_FP32)
+        CUDA_TRY(launch_factor_convert_f32((const float*)r->chol, D, (float*)r->Lg, s));
+      else
+        CUDA_TRY(launch_factor_convert(r->chol, D, r->zdtype, r->Lg, r->ldl, s));
       r->kernel_launches += 1;
       return PHI4_OK;
     }
+    if (tries >= 6) break;
     double ridge = 0.0;
     CUDA_TRY(cudaMemcpy(&ridge, r->scal + SC_RIDGE, 8, cudaMemcpyDeviceToHost));
     ridge = ridge > 0.0 ? ridge * 10.0 : 1e-12;
     const uint32_t clear = st & ~ST_NOT_PD;
     CUDA_TRY(cudaMemcpy(r->scal + SC_RIDGE, &ridge, 8, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(r->status, &clear, 4, cudaMemcpyHostToDevice));
+    phi4_status ps = factor_attempt(r);
+    if (ps != PHI4_OK) return ps;
+    ps = read_status(r, &st);
+    if (ps != PHI4_OK) return ps;
   }
   set_error("covariance not positive definite after 6 ridge increases");
   return PHI4_ERR_NOT_PD;
+}
+
+phi4_status refit_factor(phi4_run* r, const void* pts, int n_pts) {
+  phi4_status ps = refit_enqueue(r, pts, n_pts);
+  if (ps != PHI4_OK) return ps;
+  uint32_t st = 0;
+  ps = read_status(r, &st);
+  if (ps != PHI4_OK) return ps;
+  return refit_check(r, st);
 }
 
 }  // namespace phi4
@@ -201,15 +235,141 @@ phi4_status propose(phi4_run* r, uint32_t step, uint32_t sweep) {
   }
   r->kernel_launches += 2;
   StageScope sc(r, STG_PROPOSE);
-  if (r->cfg.precision == PHI4_MIXED_BF16)
-    CUDA_TRY(launch_propose_tc((const float*)r->phi, (float*)r->prop, r->Z, r->ldz, r->Lg, r->ldl, N, D,
-                               (float)r->scale, r->status, s));
+  if (r->cfg.precision == PHI4_MIXED_BF16)  // fp16 increment into the proposal buffer
+    CUDA_TRY(launch_propose_tc(r->prop, r->Z, r->ldz, r->Lg, r->ldl, N, D, (float)r->scale, r->status, s));
   else
     CUDA_TRY(launch_propose_simt(r->phi, r->prop, r->Z, r->Lg, r->dtype, N, D, r->scale, s));
   return PHI4_OK;
 }
 
 }  // namespace
+
+namespace phi4 {
+
+// Front of a temperature: bisection + reweighting, resampling, gather, covariance and
+// the first factorisation attempt, all enqueued on the run's stream.
+phi4_status step_front(phi4_run* r, bool single_cta_bisect) {
+  const phi4_config& c = r->cfg;
+  const int N = c.N, D = r->D;
+  cudaStream_t s = r->stream;
+  const uint32_t t = (uint32_t)(++r->t);
+  double* out = r->scal + SC_OUT;
+  {
+    StageScope sc(r, STG_BISECT);
+    CUDA_TRY(launch_bisect(r->ell, N, r->scal + SC_BETA, c.ess_target, c.bisect_iters, r->w, out, r->bisect_scratch,
+                           r->status, s, single_cta_bisect));
+    CUDA_TRY(launch_logz_accumulate(out, r->scal + SC_KAHAN, r->scal + SC_BETA, s));
+    r->kernel_launches += 2;
+  }
+  {
+    StageScope sc(r, STG_RESAMPLE);
+    const uint4 wd = philox4x32_10_host(make_uint4(counter_word0(RNG_RESAMPLE, t), 0u, 0u, 0u),
+                                        philox_key(c.seed, c.stream_id));
+    CUDA_TRY(launch_resample(r->w, N, wd.x, nullptr, r->anc, r->resample_scratch, s));
+    r->kernel_launches += 1;
+  }
+  {
+    StageScope sc(r, STG_GATHER);
+    CUDA_TRY(launch_gather(r->phi, r->phi_alt, (size_t)D * r->elem, N, r->anc, s));
+    CUDA_TRY(launch_gather_f64(r->S, r->S_alt, N, r->anc, s));
+    CUDA_TRY(launch_gather_f64(r->sq, r->sq_alt, N, r->anc, s));
+    CUDA_TRY(launch_gather_f64(r->ell, r->ell_alt, N, r->anc, s));
+    r->kernel_launches += 4;
+    std::swap(r->phi, r->phi_alt);
+    std::swap(r->S, r->S_alt);
+    std::swap(r->sq, r->sq_alt);
+    std::swap(r->ell, r->ell_alt);
+  }
+  return refit_enqueue(r, r->phi, N);
+}
+
+// Back of a temperature: the n_mcmc random-walk sweeps (normals, proposal, accept).
+phi4_status step_back(phi4_run* r) {
+  const phi4_config& c = r->cfg;
+  const int N = c.N, D = r->D;
+  cudaStream_t s = r->stream;
+  const uint32_t t = (uint32_t)r->t;
+  CUDA_TRY(cudaMemsetAsync(r->acc_count, 0, 4, s));
+  const ActionParams ap = action_params(r);
+  for (int sweep = 0; sweep < c.n_mcmc; ++sweep) {
+    phi4_status ps = propose(r, t, (uint32_t)sweep);
+    if (ps != PHI4_OK) return ps;
+    StageScope sc(r, STG_ACCEPT);
+    if (c.precision == PHI4_MIXED_BF16) {
+      if (c.L % 4 == 0) {
+        CUDA_TRY(launch_accept_delta((float*)r->phi, r->prop, ap, c.keep_reference, r->S, r->sq, r->ell,
+                                     r->scal + SC_BETA, c.seed, c.stream_id, t, (uint32_t)sweep, r->acc_count,
+                                     r->status, s));
+      } else {  // generic lattices: materialise phi + delta next to it, then the generic accept
+        float* prop = (float*)r->phi_alt;
+        CUDA_TRY(launch_apply_delta((const float*)r->phi, r->prop, prop, (long long)N * D, s));
+        CUDA_TRY(launch_accept(r->phi, prop, r->dtype, ap, c.keep_reference, r->S, r->sq, r->ell,
+                               r->scal + SC_BETA, c.seed, c.stream_id, t, (uint32_t)sweep, r->acc_count, r->status,
+                               s));
+        r->kernel_launches += 1;
+      }
+    } else {
+      CUDA_TRY(launch_accept(r->phi, r->prop, r->dtype, ap, c.keep_reference, r->S, r->sq, r->ell,
+                             r->scal + SC_BETA, c.seed, c.stream_id, t, (uint32_t)sweep, r->acc_count, r->status,
+                             s));
+    }
+    r->kernel_launches += 1;
+  }
+  r->n_evals += (int64_t)N * c.n_mcmc;
+  return PHI4_OK;
+}
+
+// After the stream has drained: bisection results h[0..7] and status words sw[0..1].
+phi4_status step_finish(phi4_run* r, const double* h, const uint32_t* sw, double* beta_out) {
+  if (r->timing) collect_stage_times(r);
+  phi4_status ps = status_to_error(sw[0]);
+  if (ps != PHI4_OK) return ps;
+  r->beta = h[1];
+  r->last_ess = h[2];
+  r->last_acc = r->cfg.n_mcmc > 0 ? (double)sw[1] / ((double)r->cfg.N * r->cfg.n_mcmc) : NAN;
+  if (r->beta >= 1.0) r->done = true;
+  if (beta_out) *beta_out = r->beta;
+  return PHI4_OK;
+}
+
+}  // namespace phi4
+
+namespace phi4 {
+
+// Per-member results of a batch into one array: [0..7] bisection results, [8] log Z,
+// [9] beta, [10] status word, [11] accepted moves of the last sweeps.
+__global__ void batch_gather_kernel(void* const* __restrict__ ptrs, int R, double* __restrict__ out) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
+    const double* scal = (const double*)ptrs[2 * r];
+    const uint32_t* st = (const uint32_t*)ptrs[2 * r + 1];
+    double* o = out + (size_t)r * 12;
+    for (int k = 0; k < 8; ++k) o[k] = scal[SC_OUT + k];
+    o[8] = scal[SC_KAHAN];
+    o[9] = scal[SC_BETA];
+    o[10] = (double)st[0];
+    o[11] = (double)st[1];
+  }
+}
+
+namespace {
+// Caller stream waits for every member stream, then one launch gathers the members'
+// scalars and one copy brings them to the host.
+phi4_status batch_collect(phi4_run* b, const std::vector<phi4_run*>& act, std::vector<double>& host) {
+  const int R = (int)b->members.size();
+  for (phi4_run* m : act) {
+    CUDA_TRY(cudaEventRecord(m->join, m->stream));
+    CUDA_TRY(cudaStreamWaitEvent(b->stream, m->join, 0));
+  }
+  batch_gather_kernel<<<(R + 127) / 128, 128, 0, b->stream>>>(b->batch_ptrs, R, b->batch_scalars);
+  CUDA_TRY(cudaGetLastError());
+  host.resize((size_t)R * 12);
+  CUDA_TRY(cudaMemcpyAsync(host.data(), b->batch_scalars, host.size() * 8, cudaMemcpyDeviceToHost, b->stream));
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  return PHI4_OK;
+}
+}  // namespace
+
+}  // namespace phi4
 
 extern "C" {
 
@@ -266,10 +426,19 @@ phi4_status smc_init(const phi4_config* cfg, void* d_workspace, size_t workspace
   cudaStream_t s = r->stream;
   auto fail = [&](cudaError_t e, const char* what) {
     set_error("%s: %s", what, cudaGetErrorString(e));
+    if (r->evA) cudaEventDestroy(r->evA);
+    if (r->evB) cudaEventDestroy(r->evB);
+    if (r->side) cudaStreamDestroy(r->side);
     delete r;
     return PHI4_ERR_CUDA;
   };
   cudaError_t e;
+  int lo_prio = 0, hi_prio = 0;
+  if ((e = cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio)) != cudaSuccess) return fail(e, "priority range");
+  if ((e = cudaStreamCreateWithPriority(&r->side, cudaStreamNonBlocking, hi_prio)) != cudaSuccess)
+    return fail(e, "look-ahead stream");
+  if ((e = cudaEventCreateWithFlags(&r->evA, cudaEventDisableTiming)) != cudaSuccess) return fail(e, "event");
+  if ((e = cudaEventCreateWithFlags(&r->evB, cudaEventDisableTiming)) != cudaSuccess) return fail(e, "event");
   if ((e = cudaMemsetAsync(r->scal, 0, SC_COUNT * 8, s)) != cudaSuccess) return fail(e, "memset");
   if ((e = cudaMemsetAsync(r->status, 0, 16, s)) != cudaSuccess) return fail(e, "memset");
   if ((e = launch_normals(cfg->seed, cfg->stream_id, RNG_INIT, 0, 0, 0, cfg->N, r->D, r->D, r->dtype, r->phi, s)) !=
@@ -292,72 +461,28 @@ phi4_status smc_init(const phi4_config* cfg, void* d_workspace, size_t workspace
 phi4_status smc_temper_step(phi4_run* r, double* beta_out) {
   ARG_CHECK(r, "run is NULL");
   ARG_CHECK(r->cfg.kind == PHI4_SMC_RW, "smc_temper_step on a nested-sampling run");
+  ARG_CHECK(!r->batch, "smc_temper_step on a batch handle (use smc_temper_step_batch)");
   if (r->done) {
     set_error("beta already 1");
     return PHI4_ERR_DONE;
   }
-  const phi4_config& c = r->cfg;
-  const int N = c.N, D = r->D;
-  cudaStream_t s = r->stream;
-  const uint32_t t = (uint32_t)(++r->t);
-  double* out = r->scal + SC_OUT;
-  {
-    StageScope sc(r, STG_BISECT);
-    CUDA_TRY(launch_bisect(r->ell, N, r->scal + SC_BETA, c.ess_target, c.bisect_iters, r->w, out, r->bisect_scratch,
-                           r->status, s));
-    CUDA_TRY(launch_logz_accumulate(out, r->scal + SC_KAHAN, r->scal + SC_BETA, s));
-    r->kernel_launches += 2;
-  }
-  {
-    StageScope sc(r, STG_RESAMPLE);
-    const uint4 wd = philox4x32_10_host(make_uint4(counter_word0(RNG_RESAMPLE, t), 0u, 0u, 0u),
-                                        philox_key(c.seed, c.stream_id));
-    CUDA_TRY(launch_resample(r->w, N, wd.x, nullptr, r->anc, r->resample_scratch, s));
-    r->kernel_launches += 1;
-  }
-  {
-    StageScope sc(r, STG_GATHER);
-    CUDA_TRY(launch_gather(r->phi, r->phi_alt, (size_t)D * r->elem, N, r->anc, s));
-    CUDA_TRY(launch_gather_f64(r->S, r->S_alt, N, r->anc, s));
-    CUDA_TRY(launch_gather_f64(r->sq, r->sq_alt, N, r->anc, s));
-    CUDA_TRY(launch_gather_f64(r->ell, r->ell_alt, N, r->anc, s));
-    r->kernel_launches += 4;
-    std::swap(r->phi, r->phi_alt);
-    std::swap(r->S, r->S_alt);
-    std::swap(r->sq, r->sq_alt);
-    std::swap(r->ell, r->ell_alt);
-  }
-  phi4_status ps = refit_factor(r, r->phi, N);
+  phi4_status ps = step_front(r, false);
   if (ps != PHI4_OK) return ps;
-  CUDA_TRY(cudaMemsetAsync(r->acc_count, 0, 4, s));
-  const ActionParams ap = action_params(r);
-  for (int sweep = 0; sweep < c.n_mcmc; ++sweep) {
-    ps = propose(r, t, (uint32_t)sweep);
-    if (ps != PHI4_OK) return ps;
-    StageScope sc(r, STG_ACCEPT);
-    CUDA_TRY(launch_accept(r->phi, r->prop, r->dtype, ap, c.keep_reference, r->S, r->sq, r->ell, r->scal + SC_BETA,
-                           c.seed, c.stream_id, t, (uint32_t)sweep, r->acc_count, r->status, s));
-    r->kernel_launches += 1;
-  }
-  r->n_evals += (int64_t)N * c.n_mcmc;
+  uint32_t st = 0;
+  if ((ps = read_status(r, &st)) != PHI4_OK) return ps;
+  if ((ps = refit_check(r, st)) != PHI4_OK) return ps;
+  if ((ps = step_back(r)) != PHI4_OK) return ps;
   double h[8];
-  uint32_t st[2];
-  CUDA_TRY(cudaMemcpyAsync(h, out, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaMemcpyAsync(st, r->status, 8, cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaStreamSynchronize(s));
-  if (r->timing) collect_stage_times(r);
-  ps = status_to_error(st[0]);
-  if (ps != PHI4_OK) return ps;
-  r->beta = h[1];
-  r->last_ess = h[2];
-  r->last_acc = c.n_mcmc > 0 ? (double)st[1] / ((double)N * c.n_mcmc) : NAN;
-  if (r->beta >= 1.0) r->done = true;
-  if (beta_out) *beta_out = r->beta;
-  return PHI4_OK;
+  uint32_t sw[2];
+  CUDA_TRY(cudaMemcpyAsync(h, r->scal + SC_OUT, 8 * sizeof(double), cudaMemcpyDeviceToHost, r->stream));
+  CUDA_TRY(cudaMemcpyAsync(sw, r->status, 8, cudaMemcpyDeviceToHost, r->stream));
+  CUDA_TRY(cudaStreamSynchronize(r->stream));
+  return step_finish(r, h, sw, beta_out);
 }
 
 phi4_status ns_replace_step(phi4_run* r, int32_t* done_out) {
   ARG_CHECK(r, "run is NULL");
+  ARG_CHECK(!r->batch, "ns_replace_step on a batch handle");
   ARG_CHECK(r->cfg.kind == PHI4_NS_SLICE, "ns_replace_step on an SMC run");
   if (r->done) {
     set_error("nested sampling already stopped");
@@ -442,12 +567,31 @@ phi4_status smc_load_particles(phi4_run* r, const void* src, size_t bytes) {
 
 phi4_status smc_free(phi4_run* r) {
   if (!r) return PHI4_OK;
+  ARG_CHECK(!r->owner, "this run belongs to a batch: free the batch handle");
+  if (r->batch) {
+    for (phi4_run* m : r->members) {
+      m->owner = nullptr;
+      cudaStream_t ms = m->stream;
+      if (m->join) cudaEventDestroy(m->join);
+      smc_free(m);
+      if (ms) cudaStreamDestroy(ms);
+    }
+    if (r->join) cudaEventDestroy(r->join);
+    delete r;
+    return PHI4_OK;
+  }
   cudaStreamSynchronize(r->stream);
   for (auto& rec : r->pending) {
     cudaEventDestroy(rec.a);
     cudaEventDestroy(rec.b);
   }
   for (auto e : r->pool) cudaEventDestroy(e);
+  if (r->side) {
+    cudaStreamSynchronize(r->side);
+    cudaStreamDestroy(r->side);
+  }
+  if (r->evA) cudaEventDestroy(r->evA);
+  if (r->evB) cudaEventDestroy(r->evB);
   delete r;
   return PHI4_OK;
 }
@@ -564,17 +708,31 @@ phi4_status phi4_covariance(const void* phi, int32_t precision, int32_t N, int32
   return status_to_error(st);
 }
 
-phi4_status phi4_cholesky(double* a, int32_t D, const double* d_ridge, uint32_t* d_status, void* stream) {
-  ARG_CHECK(a && d_status, "NULL argument");
+size_t phi4_cholesky_scratch_bytes(int32_t D) { return D > 0 ? cholesky_aux_bytes(D) : 0; }
+
+phi4_status phi4_cholesky(double* a, int32_t D, const double* d_ridge, uint32_t* d_status, void* scratch,
+                          size_t scratch_bytes, void* stream) {
+  ARG_CHECK(a && d_status && scratch, "NULL argument");
   ARG_CHECK(D >= 1 && D <= 16384, "D = %d outside [1, 16384]", D);
+  ARG_CHECK(scratch_bytes >= cholesky_aux_bytes(D), "scratch too small");
   cudaStream_t s = (cudaStream_t)stream;
   CUDA_TRY(launch_copy_lower(a, a, D, s));
-  CUDA_TRY(launch_cholesky(a, D, d_ridge, d_status, s));
+  CUDA_TRY(launch_cholesky(a, D, d_ridge, d_status, scratch, s));
+  return PHI4_OK;
+}
+
+phi4_status phi4_cholesky_f32(const double* sigma, float* a, int32_t D, const double* d_ridge, uint32_t* d_status,
+                              void* scratch, size_t scratch_bytes, void* stream) {
+  ARG_CHECK(sigma && a && d_status && scratch, "NULL argument");
+  ARG_CHECK(D >= 1 && D <= 16384, "D = %d outside [1, 16384]", D);
+  ARG_CHECK(scratch_bytes >= cholesky_aux_bytes(D), "scratch too small");
+  CUDA_TRY(launch_cholesky_f32(sigma, a, D, d_ridge, d_status, scratch, (cudaStream_t)stream));
   return PHI4_OK;
 }
 
 size_t phi4_propose_scratch_bytes(int32_t N, int32_t D, int32_t precision) {
-  if (precision == PHI4_MIXED_BF16) return align256((size_t)N * (((size_t)D + 7) & ~(size_t)7) * 2) + 256;
+  if (precision == PHI4_MIXED_BF16)
+    return align256((size_t)N * (((size_t)D + 7) & ~(size_t)7) * 2) + align256((size_t)N * D * 2) + 256;
   return align256((size_t)N * D * (precision == PHI4_FP64 ? 8 : 4)) + 256;
 }
 
@@ -594,11 +752,12 @@ phi4_status phi4_rw_propose(const void* phi, void* prop, const void* Lfac, int32
       return PHI4_ERR_UNSUPPORTED;
     }
     const int ldz = (D + 7) & ~7;
-    uint32_t* status = (uint32_t*)((unsigned char*)scratch + align256((size_t)N * ldz * 2));
+    unsigned char* delta = (unsigned char*)scratch + align256((size_t)N * ldz * 2);
+    uint32_t* status = (uint32_t*)(delta + align256((size_t)N * D * 2));
     CUDA_TRY(cudaMemsetAsync(status, 0, 4, s));
     CUDA_TRY(launch_normals(seed, stream_id, RNG_PROPOSE, step, sweep, 0, N, D, ldz, PHI4_DT_BF16, scratch, s));
-    CUDA_TRY(launch_propose_tc((const float*)phi, (float*)prop, scratch, ldz, Lfac, ldl, N, D, (float)scale, status,
-                               s));
+    CUDA_TRY(launch_propose_tc(delta, scratch, ldz, Lfac, ldl, N, D, (float)scale, status, s));
+    CUDA_TRY(launch_apply_delta((const float*)phi, delta, (float*)prop, (long long)N * D, s));
     uint32_t st = 0;
     CUDA_TRY(cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
@@ -622,6 +781,135 @@ phi4_status phi4_rw_accept(void* phi, const void* prop, int32_t dtype, int32_t N
   // the status word shares the counter's allocation: acc_count[1]
   CUDA_TRY(launch_accept(phi, prop, dtype, p, keep_reference, S, sq, ell, beta, seed, stream_id, step, sweep,
                          acc_count, acc_count + 1, (cudaStream_t)stream));
+  return PHI4_OK;
+}
+
+phi4_status phi4_rw_accept_delta(float* phi, const void* delta_f16, int32_t N, int32_t L, double m2, double lambda,
+                                 double c_kin, double c_mass, int32_t keep_reference, double* S, double* sq,
+                                 double* ell, const double* beta, uint64_t seed, uint64_t stream_id, uint32_t step,
+                                 uint32_t sweep, uint32_t* acc_count, void* stream) {
+  ARG_CHECK(phi && delta_f16 && S && sq && ell && beta && acc_count, "NULL argument");
+  ARG_CHECK(N >= 0 && L >= 4 && L <= 128 && L % 4 == 0 && L * L <= 8192, "L = %d: need L %% 4 == 0, L*L <= 8192", L);
+  ActionParams p{L, L * L, N, m2, lambda, c_kin, c_mass, 0.5 * L * L * log(2.0 * M_PI)};
+  CUDA_TRY(launch_accept_delta(phi, delta_f16, p, keep_reference, S, sq, ell, beta, seed, stream_id, step, sweep,
+                               acc_count, acc_count + 1, (cudaStream_t)stream));
+  return PHI4_OK;
+}
+
+/* ------------------------------ batched form ------------------------------ */
+
+static size_t batch_header_bytes(int32_t n) { return align256((size_t)n * 12 * 8) + align256((size_t)n * 2 * 8); }
+
+phi4_status phi4_batch_workspace_bytes(const phi4_config* cfgs, int32_t n_runs, size_t* bytes) {
+  ARG_CHECK(cfgs && bytes, "NULL argument");
+  ARG_CHECK(n_runs >= 1 && n_runs <= 4096, "n_runs = %d outside [1, 4096]", n_runs);
+  size_t tot = batch_header_bytes(n_runs);
+  for (int r = 0; r < n_runs; ++r) {
+    size_t b = 0;
+    phi4_status st = phi4_workspace_bytes(&cfgs[r], &b);
+    if (st != PHI4_OK) return st;
+    ARG_CHECK(cfgs[r].kind == PHI4_SMC_RW, "batch member %d: only SMC runs are batched", r);
+    ARG_CHECK(cfgs[r].N <= 4096, "batch member %d: N = %d above the 4096 of a one-CTA bisection", r, cfgs[r].N);
+    tot += align256(b);
+  }
+  *bytes = tot;
+  return PHI4_OK;
+}
+
+phi4_status smc_init_batch(const phi4_config* cfgs, int32_t n_runs, void* d_ws, size_t ws_bytes, void* stream,
+                           phi4_run** out) {
+  ARG_CHECK(out, "out is NULL");
+  size_t need = 0;
+  phi4_status ps = phi4_batch_workspace_bytes(cfgs, n_runs, &need);
+  if (ps != PHI4_OK) return ps;
+  ARG_CHECK(d_ws && ((uintptr_t)d_ws & 255) == 0, "workspace must be non-NULL and 256-byte aligned");
+  if (ws_bytes < need) {
+    set_error("workspace of %zu bytes, need %zu", ws_bytes, need);
+    return PHI4_ERR_WORKSPACE;
+  }
+  phi4_run* b = new phi4_run();
+  b->batch = true;
+  b->cfg = cfgs[0];
+  b->stream = (cudaStream_t)stream;
+  unsigned char* base = (unsigned char*)d_ws;
+  b->batch_scalars = (double*)base;
+  b->batch_ptrs = (void**)(base + align256((size_t)n_runs * 12 * 8));
+  size_t off = batch_header_bytes(n_runs);
+  std::vector<void*> ptrs((size_t)n_runs * 2);
+  for (int r = 0; r < n_runs; ++r) {
+    size_t bytes = 0;
+    phi4_workspace_bytes(&cfgs[r], &bytes);
+    cudaStream_t ms = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&ms, cudaStreamNonBlocking);
+    phi4_run* m = nullptr;
+    if (e == cudaSuccess) ps = smc_init(&cfgs[r], base + off, bytes, ms, &m);
+    if (e != cudaSuccess || ps != PHI4_OK) {
+      if (e != cudaSuccess) set_error("member stream: %s", cudaGetErrorString(e));
+      if (ms) cudaStreamDestroy(ms);
+      smc_free(b);
+      return e != cudaSuccess ? PHI4_ERR_CUDA : ps;
+    }
+    m->owner = b;
+    m->owns_stream = true;
+    cudaEventCreateWithFlags(&m->join, cudaEventDisableTiming);
+    b->members.push_back(m);
+    ptrs[2 * r] = m->scal;
+    ptrs[2 * r + 1] = m->status;
+    off += align256(bytes);
+  }
+  CUDA_TRY(cudaMemcpyAsync(b->batch_ptrs, ptrs.data(), ptrs.size() * sizeof(void*), cudaMemcpyHostToDevice,
+                           b->stream));
+  cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
+  for (phi4_run* m : b->members) {
+    CUDA_TRY(cudaEventRecord(m->join, m->stream));
+    CUDA_TRY(cudaStreamWaitEvent(b->stream, m->join, 0));
+  }
+  *out = b;
+  return PHI4_OK;
+}
+
+phi4_status smc_temper_step_batch(phi4_run* b, int32_t* n_active_out) {
+  ARG_CHECK(b && b->batch, "not a batch handle");
+  std::vector<phi4_run*> act;
+  for (phi4_run* m : b->members)
+    if (!m->done) act.push_back(m);
+  if (act.empty()) {
+    if (n_active_out) *n_active_out = 0;
+    set_error("every run of the batch is at beta = 1");
+    return PHI4_ERR_DONE;
+  }
+  // members start after the caller's earlier work
+  CUDA_TRY(cudaEventRecord(b->join, b->stream));
+  for (phi4_run* m : act) CUDA_TRY(cudaStreamWaitEvent(m->stream, b->join, 0));
+  phi4_status ps;
+  for (phi4_run* m : act)
+    if ((ps = step_front(m, true)) != PHI4_OK) return ps;
+  std::vector<double> h;
+  if ((ps = batch_collect(b, act, h)) != PHI4_OK) return ps;
+  for (phi4_run* m : act) {
+    const size_t i = (size_t)(std::find(b->members.begin(), b->members.end(), m) - b->members.begin());
+    if ((ps = refit_check(m, (uint32_t)h[i * 12 + 10])) != PHI4_OK) return ps;
+  }
+  for (phi4_run* m : act)
+    if ((ps = step_back(m)) != PHI4_OK) return ps;
+  if ((ps = batch_collect(b, act, h)) != PHI4_OK) return ps;
+  int n_active = 0;
+  for (size_t i = 0; i < b->members.size(); ++i) {
+    phi4_run* m = b->members[i];
+    if (std::find(act.begin(), act.end(), m) != act.end()) {
+      const uint32_t sw[2] = {(uint32_t)h[i * 12 + 10], (uint32_t)h[i * 12 + 11]};
+      if ((ps = step_finish(m, &h[i * 12], sw, nullptr)) != PHI4_OK) return ps;
+    }
+    if (!m->done) ++n_active;
+  }
+  if (n_active_out) *n_active_out = n_active;
+  return PHI4_OK;
+}
+
+phi4_status phi4_batch_member(phi4_run* b, int32_t r, phi4_run** member_out) {
+  ARG_CHECK(b && b->batch && member_out, "not a batch handle");
+  ARG_CHECK(r >= 0 && r < (int32_t)b->members.size(), "member %d outside [0, %d)", r, (int)b->members.size());
+  *member_out = b->members[r];
   return PHI4_OK;
 }
 

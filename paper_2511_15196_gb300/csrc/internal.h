@@ -26,12 +26,17 @@ cudaError_t launch_accept(void* phi, const void* prop, int dtype, const ActionPa
                           double* S, double* sq, double* ell, const double* beta, uint64_t seed,
                           uint64_t stream_id, uint32_t step, uint32_t sweep, uint32_t* acc_count,
                           uint32_t* status, cudaStream_t s);
+// float fields, proposal = phi + delta (fp16 increment), L % 4 == 0
+cudaError_t launch_accept_delta(float* phi, const void* delta_f16, const ActionParams& p, int keep_reference,
+                                double* S, double* sq, double* ell, const double* beta, uint64_t seed,
+                                uint64_t stream_id, uint32_t step, uint32_t sweep, uint32_t* acc_count,
+                                uint32_t* status, cudaStream_t s);
 cudaError_t launch_magnetisation(const void* phi, int dtype, int N, int D, double* M, cudaStream_t s);
 
 // kernels_temper.cu
 size_t bisect_scratch_bytes(int N);
 cudaError_t launch_bisect(const double* ell, int N, const double* beta_in, double rho, int iters, double* w,
-                          double* out, void* scratch, uint32_t* status, cudaStream_t s);
+                          double* out, void* scratch, uint32_t* status, cudaStream_t s, bool single_cta = false);
 cudaError_t launch_logz_accumulate(const double* out, double* logz_kahan, double* beta, cudaStream_t s);
 
 // kernels_resample.cu
@@ -50,8 +55,17 @@ cudaError_t launch_ridge(const double* sigma, int D, double jitter_rel, double* 
 
 // kernels_chol.cu
 cudaError_t launch_copy_lower(const double* src, double* dst, int D, cudaStream_t s);
-cudaError_t launch_cholesky(double* a, int D, const double* ridge, uint32_t* status, cudaStream_t s);
+// In-place blocked Cholesky; aux: cholesky_aux_bytes(D) device scratch for the diagonal-block
+// inverses. With side != nullptr the look-ahead schedule uses `side` and the two events.
+size_t cholesky_aux_bytes(int D);
+cudaError_t launch_cholesky(double* a, int D, const double* ridge, uint32_t* status, void* aux, cudaStream_t s,
+                            cudaStream_t side = nullptr, cudaEvent_t evA = nullptr, cudaEvent_t evB = nullptr);
 int cholesky_launches(int D);  // kernels one launch_cholesky enqueues
+// float factorisation of the lower triangle of sigma (copied into a) for the plain FP32 form
+cudaError_t launch_cholesky_f32(const double* sigma, float* a, int D, const double* ridge, uint32_t* status,
+                                void* aux, cudaStream_t s, cudaStream_t side = nullptr, cudaEvent_t evA = nullptr,
+                                cudaEvent_t evB = nullptr);
+cudaError_t launch_factor_convert_f32(const float* Lc, int D, float* out, cudaStream_t s);
 cudaError_t launch_factor_convert(const double* Lc, int D, int dtype, void* out, int ld, cudaStream_t s);
 
 // kernels_gemm_simt.cu
@@ -62,8 +76,11 @@ cudaError_t launch_syrk_simt(const void* XcT, int dtype, int D, int N, int ldx, 
 
 // kernels_tc.cu (tcgen05 / TMA)
 bool tc_available();
-cudaError_t launch_propose_tc(const float* phi, float* prop, const void* Zb, int ldz, const void* Lb, int ldl,
-                              int N, int D, float scale, uint32_t* status, cudaStream_t s);
+// increment Delta = scale * Z L^T as fp16 [N][D] (tensor cores, bf16 operands)
+cudaError_t launch_propose_tc(void* delta_f16, const void* Zb, int ldz, const void* Lb, int ldl, int N, int D,
+                              float scale, uint32_t* status, cudaStream_t s);
+// prop = phi + float(delta) elementwise (float fields)
+cudaError_t launch_apply_delta(const float* phi, const void* delta_f16, float* prop, long long n, cudaStream_t s);
 cudaError_t launch_syrk_tc(const void* XcTb, int ldx, int D, int N, double inv_nm1, double* sigma,
                            uint32_t* status, cudaStream_t s);
 

@@ -1,8 +1,9 @@
-// FP64 Cholesky of the particle covariance (App. A), blocked right-looking with
-// 64 x 64 blocks: per block column, (1) factor the diagonal block in one CTA,
-// (2) triangular solve of the panel below it, (3) symmetric update of the
-// trailing lower blocks. All arithmetic is double. A non-positive pivot sets
-// ST_NOT_PD in the status word; later kernels see the bit and return.
+// Cholesky of the particle covariance (App. A), blocked right-looking with 64 x 64
+// blocks: per block column, (1) factor the diagonal block in one CTA, (2) triangular
+// solve of the panel below it, (3) symmetric update of the trailing lower blocks.
+// Templated on the element type: double for the FP64 and mixed forms, float for the
+// plain FP32 form. A non-positive pivot sets ST_NOT_PD in the status word; later
+// kernels see the bit and return.
 #include <math.h>
 #include "internal.h"
 #include "common.cuh"
@@ -14,26 +15,34 @@ constexpr int NB = 64;
 }
 
 // dst = lower triangle of src, zeros strictly above the diagonal (src may equal dst).
-__global__ void copy_lower_kernel(const double* __restrict__ src, double* __restrict__ dst, int D) {
+template <typename T>
+__global__ void copy_lower_kernel(const double* src, T* dst, int D) {
   const long long total = (long long)D * D;
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
        k += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(k / D), j = (int)(k - (long long)i * D);
-    dst[k] = j <= i ? src[k] : 0.0;
+    const double v = j <= i ? src[k] : 0.0;
+    dst[k] = (T)v;
   }
 }
 
-__global__ void __launch_bounds__(256) potrf_diag_kernel(double* __restrict__ a, int D, int k0,
-                                                         const double* __restrict__ ridge,
-                                                         uint32_t* __restrict__ status) {
-  __shared__ double blk[NB][NB + 1];
+// Factor the diagonal block in one CTA and form its inverse W = L_kk^{-1} (lower),
+// which turns the panel's triangular solve into a dependency-free product.
+template <typename T>
+__global__ void __launch_bounds__(256) potrf_inv_kernel(T* __restrict__ a, int D, int k0,
+                                                        const double* __restrict__ ridge, T* __restrict__ W,
+                                                        uint32_t* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char chol_smem[];
+  T(*blk)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(chol_smem);
+  T(*inv)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(chol_smem + sizeof(T) * NB * (NB + 1));
+  __shared__ T rdiag[NB];
   __shared__ int fail;
   if (*status & ST_NOT_PD) return;
   const int n = min(NB, D - k0);
-  const double r = ridge ? *ridge : 0.0;
+  const T r = ridge ? (T)*ridge : (T)0;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int i = e / n, j = e % n;
-    double v = (j <= i) ? a[(size_t)(k0 + i) * D + k0 + j] : 0.0;
+    T v = (j <= i) ? a[(size_t)(k0 + i) * D + k0 + j] : (T)0;
     if (i == j) v += r;
     blk[i][j] = v;
   }
@@ -41,13 +50,13 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* __restrict__ a,
   __syncthreads();
   for (int j = 0; j < n; ++j) {
     if (threadIdx.x == 0) {
-      const double d = blk[j][j];
-      if (!(d > 0.0) || !isfinite(d)) fail = 1;
+      const T d = blk[j][j];
+      if (!(d > (T)0) || !isfinite(d)) fail = 1;
       else blk[j][j] = sqrt(d);
     }
     __syncthreads();
     if (fail) break;
-    const double piv = blk[j][j];
+    const T piv = blk[j][j];
     for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) blk[i][j] /= piv;
     __syncthreads();
     const int m = n - j - 1;  // trailing size
@@ -61,80 +70,112 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* __restrict__ a,
     if (threadIdx.x == 0) atomicOr(status, ST_NOT_PD);
     return;
   }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) rdiag[i] = (T)1 / blk[i][i];
+  __syncthreads();
+  // W column j by forward substitution of L w = e_j, four lanes per column splitting each
+  // dot product. Every lane runs the same trip count (the shuffles and warp barriers need
+  // all 32 lanes); lanes whose column has not started yet contribute zero.
+  const int j = threadIdx.x >> 2, sub = threadIdx.x & 3;
+  const bool col = j < n;
+  if (col && sub == 0) inv[j][j] = rdiag[j];
+  __syncwarp();
+  for (int i = 1; i < n; ++i) {
+    const bool act = col && i > j;
+    T part = (T)0;
+    if (act)
+      for (int m = j + sub; m < i; m += 4) part += blk[i][m] * inv[m][j];
+    part += __shfl_xor_sync(0xffffffffu, part, 1);
+    part += __shfl_xor_sync(0xffffffffu, part, 2);
+    if (act && sub == 0) inv[i][j] = -part * rdiag[i];
+    __syncwarp();
+  }
+  __syncthreads();
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const int i = e / n, j = e % n;
-    a[(size_t)(k0 + i) * D + k0 + j] = (j <= i) ? blk[i][j] : 0.0;
+    const int i = e / n, c = e % n;
+    a[(size_t)(k0 + i) * D + k0 + c] = (c <= i) ? blk[i][c] : (T)0;
+    W[i * NB + c] = (c <= i) ? inv[i][c] : (T)0;
   }
 }
 
-// Rows r0.. of the panel below diagonal block k0: X L_kk^T = A  ->  A := X.
-__global__ void __launch_bounds__(NB) trsm_panel_kernel(double* __restrict__ a, int D, int k0,
+// Panel below diagonal block k0: X = A W^T with W = L_kk^{-1} (solves X L_kk^T = A),
+// 32 rows per CTA, written in place.
+template <typename T>
+__global__ void __launch_bounds__(256) trsm_gemm_kernel(T* __restrict__ a, int D, int k0, const T* __restrict__ W,
                                                         const uint32_t* __restrict__ status) {
-  extern __shared__ double trsm_smem[];
-  double(*Lkk)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(trsm_smem);
-  double(*X)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(trsm_smem + NB * (NB + 1));
+  extern __shared__ __align__(16) unsigned char chol_smem[];
+  T(*Ws)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(chol_smem);
+  T(*As)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(chol_smem + sizeof(T) * NB * (NB + 1));
   if (*status & ST_NOT_PD) return;
   const int n = min(NB, D - k0);
-  const int r0 = k0 + n + blockIdx.x * NB;
-  const int rows = min(NB, D - r0);
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const int i = e / n, j = e % n;
-    Lkk[i][j] = a[(size_t)(k0 + i) * D + k0 + j];
+  const int r0 = k0 + n + blockIdx.x * 32;
+  const int rows = min(32, D - r0);
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int i = e / NB, c = e % NB;
+    Ws[i][c] = (i < n && c < n) ? W[i * NB + c] : (T)0;
   }
-  for (int e = threadIdx.x; e < rows * n; e += blockDim.x) {
-    const int i = e / n, j = e % n;
-    X[i][j] = a[(size_t)(r0 + i) * D + k0 + j];
-  }
-  __syncthreads();
-  const int t = threadIdx.x;
-  if (t < rows) {
-    for (int j = 0; j < n; ++j) {
-      double v = X[t][j];
-      for (int m = 0; m < j; ++m) v -= X[t][m] * Lkk[j][m];
-      X[t][j] = v / Lkk[j][j];
-    }
+  for (int e = threadIdx.x; e < 32 * NB; e += blockDim.x) {
+    const int i = e / NB, c = e % NB;
+    As[i][c] = (i < rows && c < n) ? a[(size_t)(r0 + i) * D + k0 + c] : (T)0;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < rows * n; e += blockDim.x) {
-    const int i = e / n, j = e % n;
-    a[(size_t)(r0 + i) * D + k0 + j] = X[i][j];
+  // thread -> (row = tid / 8, 8 consecutive output columns)
+  const int rr = threadIdx.x >> 3, c0 = (threadIdx.x & 7) * 8;
+  T acc[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) acc[q] = (T)0;
+  for (int m = 0; m < n; ++m) {
+    const T x = As[rr][m];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = fma(x, Ws[c0 + q][m], acc[q]);  // W[c][m] = 0 for m > c
+  }
+  if (rr < rows) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (c0 + q < n) a[(size_t)(r0 + rr) * D + k0 + c0 + q] = acc[q];
   }
 }
 
-// Trailing update of lower block (bi, bj), bj <= bi, both below block column k0:
-// A_ij -= L_ik L_jk^T (K = width of the block column). 256 threads, 4 x 4 outputs each.
-__global__ void __launch_bounds__(256) syrk_update_kernel(double* __restrict__ a, int D, int k0,
+// Trailing update after block column k0: A_ij -= L_ik L_jk^T on 64 x 64 lower tiles.
+// part 0: every tile; part 1: only the next block column (bj = 0); part 2: the rest.
+template <typename T>
+__global__ void __launch_bounds__(256) syrk_update_kernel(T* __restrict__ a, int D, int k0, int part,
                                                           const uint32_t* __restrict__ status) {
-  __shared__ double As[16][NB + 2];
-  __shared__ double Bs[16][NB + 2];
+  __shared__ T As[16][NB + 2];
+  __shared__ T Bs[16][NB + 2];
   if (*status & ST_NOT_PD) return;
   const int n = min(NB, D - k0);
-  // decode the lower-triangular tile index
   const long long t = blockIdx.x;
-  int bi = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-  while ((long long)(bi + 1) * (bi + 2) / 2 <= t) ++bi;
-  while ((long long)bi * (bi + 1) / 2 > t) --bi;
-  const int bj = (int)(t - (long long)bi * (bi + 1) / 2);
+  int bi, bj;
+  if (part == 1) {
+    bi = (int)t;
+    bj = 0;
+  } else {
+    bi = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((long long)(bi + 1) * (bi + 2) / 2 <= t) ++bi;
+    while ((long long)bi * (bi + 1) / 2 > t) --bi;
+    bj = (int)(t - (long long)bi * (bi + 1) / 2);
+    if (part == 2) { ++bi; ++bj; }
+  }
   const int base = k0 + n;
   const int i0 = base + bi * NB, j0 = base + bj * NB;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  double acc[4][4];
+  T acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
   for (int kk = 0; kk < n; kk += 16) {
     for (int e = threadIdx.x; e < NB * 16; e += 256) {
       const int r = e / 16, k = e % 16;
       const int gk = k0 + kk + k;
       const bool kin = (kk + k) < n;
-      As[k][r] = (kin && i0 + r < D) ? a[(size_t)(i0 + r) * D + gk] : 0.0;
-      Bs[k][r] = (kin && j0 + r < D) ? a[(size_t)(j0 + r) * D + gk] : 0.0;
+      As[k][r] = (kin && i0 + r < D) ? a[(size_t)(i0 + r) * D + gk] : (T)0;
+      Bs[k][r] = (kin && j0 + r < D) ? a[(size_t)(j0 + r) * D + gk] : (T)0;
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-      double x[4], y[4];
+      T x[4], y[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) x[i] = As[k][ty + 16 * i];
 #pragma unroll
@@ -159,56 +200,100 @@ __global__ void __launch_bounds__(256) syrk_update_kernel(double* __restrict__ a
   }
 }
 
-template <typename To>
-__global__ void convert_factor_kernel(const double* __restrict__ Lc, int D, To* __restrict__ out, int ld) {
+template <typename Ti, typename To>
+__global__ void convert_factor_kernel(const Ti* __restrict__ Lc, int D, To* __restrict__ out, int ld) {
   const long long total = (long long)D * ld;
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
        k += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(k / ld), j = (int)(k - (long long)i * ld);
-    const double v = (j < D && j <= i) ? Lc[(size_t)i * D + j] : 0.0;
+    const double v = (j < D && j <= i) ? (double)Lc[(size_t)i * D + j] : 0.0;
     if constexpr (sizeof(To) == 2) out[k] = __float2bfloat16_rn((float)v);
     else out[k] = (To)v;
   }
 }
 
 cudaError_t launch_copy_lower(const double* src, double* dst, int D, cudaStream_t s) {
-  copy_lower_kernel<<<sm_count() * 4, 256, 0, s>>>(src, dst, D);
+  copy_lower_kernel<double><<<sm_count() * 4, 256, 0, s>>>(src, dst, D);
   return cudaGetLastError();
 }
 
-cudaError_t launch_cholesky(double* a, int D, const double* ridge, uint32_t* status, cudaStream_t s) {
+// Blocked right-looking factorisation. With a second stream `side` (and two events),
+// the next block column's update and its diagonal/panel factorisation run on `side`
+// while `s` applies the rest of the trailing update (look-ahead); the arithmetic of
+// every tile is the same either way, so both schedules give identical results.
+template <typename T>
+static cudaError_t cholesky_t(T* a, int D, const double* ridge, T* W, uint32_t* status, cudaStream_t s,
+                              cudaStream_t side, cudaEvent_t evA, cudaEvent_t evB) {
   const int nblk = (D + NB - 1) / NB;
-  const size_t trsm_smem = 2 * sizeof(double) * NB * (NB + 1);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(trsm_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  for (int kb = 0; kb < nblk; ++kb) {
+  const bool ahead = side != nullptr && nblk > 2;
+  const size_t sm_potrf = 2 * sizeof(T) * NB * (NB + 1), sm_trsm = sizeof(T) * (NB + 32) * (NB + 1);
+  cudaError_t e0 = cudaFuncSetAttribute(potrf_inv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_potrf);
+  if (e0 != cudaSuccess) return e0;
+  e0 = cudaFuncSetAttribute(trsm_gemm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_trsm);
+  if (e0 != cudaSuccess) return e0;
+  auto panel = [&](int kb, cudaStream_t st) {
     const int k0 = kb * NB;
-    potrf_diag_kernel<<<1, 256, 0, s>>>(a, D, k0, ridge, status);
+    potrf_inv_kernel<T><<<1, 256, sm_potrf, st>>>(a, D, k0, ridge, W + (size_t)kb * NB * NB, status);
+    const int rows = D - k0 - min(NB, D - k0);
+    if (rows > 0)
+      trsm_gemm_kernel<T><<<(rows + 31) / 32, 256, sm_trsm, st>>>(a, D, k0, W + (size_t)kb * NB * NB, status);
+  };
+  panel(0, s);
+  for (int kb = 0; kb < nblk - 1; ++kb) {
+    const int k0 = kb * NB;
     const int below = nblk - kb - 1;
-    if (below > 0) {
-      trsm_panel_kernel<<<below, NB, trsm_smem, s>>>(a, D, k0, status);
-      const long long tiles = (long long)below * (below + 1) / 2;
-      syrk_update_kernel<<<(unsigned)tiles, 256, 0, s>>>(a, D, k0, status);
+    const long long all = (long long)below * (below + 1) / 2;
+    if (!ahead) {
+      syrk_update_kernel<T><<<(unsigned)all, 256, 0, s>>>(a, D, k0, 0, status);
+      panel(kb + 1, s);
+      continue;
     }
+    cudaError_t e;
+    if ((e = cudaEventRecord(evA, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(side, evA, 0)) != cudaSuccess) return e;
+    syrk_update_kernel<T><<<(unsigned)below, 256, 0, side>>>(a, D, k0, 1, status);
+    panel(kb + 1, side);
+    if ((e = cudaEventRecord(evB, side)) != cudaSuccess) return e;
+    const long long rest = all - below;
+    if (rest > 0) syrk_update_kernel<T><<<(unsigned)rest, 256, 0, s>>>(a, D, k0, 2, status);
+    if ((e = cudaStreamWaitEvent(s, evB, 0)) != cudaSuccess) return e;
   }
   return cudaGetLastError();
+}
+
+size_t cholesky_aux_bytes(int D) {
+  const size_t nblk = (size_t)(D + NB - 1) / NB;
+  return nblk * NB * NB * sizeof(double);
+}
+
+cudaError_t launch_cholesky(double* a, int D, const double* ridge, uint32_t* status, void* aux, cudaStream_t s,
+                            cudaStream_t side, cudaEvent_t evA, cudaEvent_t evB) {
+  return cholesky_t<double>(a, D, ridge, (double*)aux, status, s, side, evA, evB);
+}
+
+cudaError_t launch_cholesky_f32(const double* sigma, float* a, int D, const double* ridge, uint32_t* status,
+                                void* aux, cudaStream_t s, cudaStream_t side, cudaEvent_t evA, cudaEvent_t evB) {
+  copy_lower_kernel<float><<<sm_count() * 4, 256, 0, s>>>(sigma, a, D);
+  return cholesky_t<float>(a, D, ridge, (float*)aux, status, s, side, evA, evB);
 }
 
 int cholesky_launches(int D) {
   const int nblk = (D + NB - 1) / NB;
-  return nblk + 2 * (nblk - 1);
+  return nblk + 2 * (nblk - 1) + (nblk - 1);
 }
 
 cudaError_t launch_factor_convert(const double* Lc, int D, int dtype, void* out, int ld, cudaStream_t s) {
   const int grid = sm_count() * 4;
-  if (dtype == 0) convert_factor_kernel<double><<<grid, 256, 0, s>>>(Lc, D, (double*)out, ld);
-  else if (dtype == 1) convert_factor_kernel<float><<<grid, 256, 0, s>>>(Lc, D, (float*)out, ld);
-  else if (dtype == 2) convert_factor_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(Lc, D, (__nv_bfloat16*)out, ld);
+  if (dtype == 0) convert_factor_kernel<double, double><<<grid, 256, 0, s>>>(Lc, D, (double*)out, ld);
+  else if (dtype == 1) convert_factor_kernel<double, float><<<grid, 256, 0, s>>>(Lc, D, (float*)out, ld);
+  else if (dtype == 2)
+    convert_factor_kernel<double, __nv_bfloat16><<<grid, 256, 0, s>>>(Lc, D, (__nv_bfloat16*)out, ld);
   else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_factor_convert_f32(const float* Lc, int D, float* out, cudaStream_t s) {
+  convert_factor_kernel<float, float><<<sm_count() * 4, 256, 0, s>>>(Lc, D, out, D);
   return cudaGetLastError();
 }
 

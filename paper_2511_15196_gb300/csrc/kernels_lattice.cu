@@ -5,6 +5,7 @@
 //   D >= 1024: one particle per 256-thread CTA;  D < 1024: one particle per warp.
 #include <math.h>
 #include "internal.h"
+#include <cuda_fp16.h>
 #include "philox.cuh"
 
 namespace phi4 {
@@ -136,6 +137,118 @@ __global__ void __launch_bounds__(PPB* TPP) accept_kernel(T* __restrict__ phi, c
     for (int x = t; x < p.D; x += TPP) phi[(size_t)i * p.D + x] = row[x];
 }
 
+// Float fields with L % 4 == 0: each thread owns float4 groups of four sites of one
+// lattice row (kept in registers), reads the up/down neighbour groups and the two
+// horizontal end neighbours from the staged row, and keeps plain float partial sums
+// over at most a few groups; partials are combined in double with one fused
+// two-value reduction. The proposal is either a float row `prop` or phi + delta with
+// delta an fp16 increment (the tensor-core proposal's epilogue output).
+template <int PPB, int TPP, bool kDelta>
+__global__ void __launch_bounds__(PPB* TPP) accept_vec_kernel(float* __restrict__ phi, const float* __restrict__ prop,
+                                                              const __half* __restrict__ delta, ActionParams p,
+                                                              int keep_ref, double* __restrict__ S,
+                                                              double* __restrict__ sq, double* __restrict__ ell,
+                                                              const double* __restrict__ beta_ptr, PhiloxKey key,
+                                                              uint32_t w0, uint32_t sweep,
+                                                              uint32_t* __restrict__ acc_count,
+                                                              uint32_t* __restrict__ status) {
+  constexpr int kMaxG = 8;  // float4 groups per thread (D <= 8 * 4 * TPP)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[PPB][TPP / 32][2];
+  __shared__ int accept_flag[PPB];
+  const int g = threadIdx.x / TPP, t = threadIdx.x % TPP;
+  const int i = blockIdx.x * PPB + g;
+  const int L = p.L, D = p.D, ng = D >> 2;
+  float* row = reinterpret_cast<float*>(smem_raw) + (size_t)g * D;
+  float4 v[kMaxG];
+  if (i < p.N) {
+#pragma unroll
+    for (int k = 0; k < kMaxG; ++k) {
+      const int q = t + k * TPP;
+      if (q < ng) {
+        float4 f;
+        if constexpr (kDelta) {
+          f = reinterpret_cast<const float4*>(phi + (size_t)i * D)[q];
+          const uint2 hv = reinterpret_cast<const uint2*>(delta + (size_t)i * D)[q];
+          const float2 d01 = __half22float2(*reinterpret_cast<const __half2*>(&hv.x));
+          const float2 d23 = __half22float2(*reinterpret_cast<const __half2*>(&hv.y));
+          f.x += d01.x; f.y += d01.y; f.z += d23.x; f.w += d23.y;
+        } else {
+          f = reinterpret_cast<const float4*>(prop + (size_t)i * D)[q];
+        }
+        v[k] = f;
+        reinterpret_cast<float4*>(row)[q] = f;
+      }
+    }
+  }
+  __syncthreads();
+  const float ck = (float)p.c_kin, cm = (float)(p.c_mass * p.m2), lm = (float)p.lam;
+  float s = 0.f, qq = 0.f;
+  if (i < p.N) {
+#pragma unroll
+    for (int k = 0; k < kMaxG; ++k) {
+      const int q = t + k * TPP;
+      if (q < ng) {
+        const int x0 = q << 2;
+        const int r = x0 / L, c0 = x0 - r * L;
+        const int ru = r == 0 ? L - 1 : r - 1, rd = r == L - 1 ? 0 : r + 1;
+        const float4 up = reinterpret_cast<const float4*>(row + ru * L)[c0 >> 2];
+        const float4 dn = reinterpret_cast<const float4*>(row + rd * L)[c0 >> 2];
+        const float lf = row[r * L + (c0 == 0 ? L - 1 : c0 - 1)];
+        const float rt = row[r * L + (c0 + 4 == L ? 0 : c0 + 4)];
+        const float4 f = v[k];
+        const float n0 = lf + f.y + up.x + dn.x, n1 = f.x + f.z + up.y + dn.y;
+        const float n2 = f.y + f.w + up.z + dn.z, n3 = f.z + rt + up.w + dn.w;
+        const float a0 = f.x * f.x, a1 = f.y * f.y, a2 = f.z * f.z, a3 = f.w * f.w;
+        s += ck * (f.x * (4.f * f.x - n0)) + cm * a0 + lm * (a0 * a0);
+        s += ck * (f.y * (4.f * f.y - n1)) + cm * a1 + lm * (a1 * a1);
+        s += ck * (f.z * (4.f * f.z - n2)) + cm * a2 + lm * (a2 * a2);
+        s += ck * (f.w * (4.f * f.w - n3)) + cm * a3 + lm * (a3 * a3);
+        qq += (a0 + a1) + (a2 + a3);
+      }
+    }
+  }
+  double ds = warp_sum((double)s), dq = warp_sum((double)qq);
+  const int lane = t & 31, wg = t >> 5;
+  if (lane == 0) {
+    red[g][wg][0] = ds;
+    red[g][wg][1] = dq;
+  }
+  __syncthreads();
+  if (i < p.N && t == 0) {
+    double Sp = 0.0, Qp = 0.0;
+#pragma unroll
+    for (int w = 0; w < TPP / 32; ++w) {
+      Sp += red[g][w][0];
+      Qp += red[g][w][1];
+    }
+    const double beta = *beta_ptr;
+    const double dS = Sp - S[i], dq2 = Qp - sq[i];
+    const double log_alpha = keep_ref ? (-beta * dS - 0.5 * dq2) : (-beta * dS - (1.0 - beta) * 0.5 * dq2);
+    const uint4 w = philox4x32_10(make_uint4(w0, sweep, (uint32_t)i, 0u), key);
+    int acc = log(uniform53(w.x, w.y)) < log_alpha;
+    if (!isfinite(Sp) || !isfinite(Qp)) {
+      atomicOr(status, ST_NONFINITE);
+      acc = 0;
+    }
+    accept_flag[g] = acc;
+    if (acc) {
+      S[i] = Sp;
+      sq[i] = Qp;
+      ell[i] = keep_ref ? -Sp : (-Sp + 0.5 * Qp + p.half_d_log2pi);
+      atomicAdd(acc_count, 1u);
+    }
+  }
+  __syncthreads();
+  if (i < p.N && accept_flag[g]) {
+#pragma unroll
+    for (int k = 0; k < kMaxG; ++k) {
+      const int q = t + k * TPP;
+      if (q < ng) reinterpret_cast<float4*>(phi + (size_t)i * D)[q] = v[k];
+    }
+  }
+}
+
 template <typename T>
 __global__ void magnetisation_kernel(const T* __restrict__ phi, int N, int D, double* __restrict__ M) {
   const int lane = threadIdx.x & 31;
@@ -201,12 +314,47 @@ static cudaError_t accept_t(T* phi, const T* prop, const ActionParams& p, int ke
   return cudaGetLastError();
 }
 
+template <bool kDelta>
+static cudaError_t accept_vec(float* phi, const float* prop, const __half* delta, const ActionParams& p, int keep_ref,
+                              double* S, double* sq, double* ell, const double* beta, PhiloxKey key, uint32_t w0,
+                              uint32_t sweep, uint32_t* acc, uint32_t* status, cudaStream_t s) {
+  if (p.D >= kBigD) {
+    const size_t sm = (size_t)p.D * sizeof(float);
+    cudaError_t e = set_smem(accept_vec_kernel<1, 256, kDelta>, sm);
+    if (e != cudaSuccess) return e;
+    accept_vec_kernel<1, 256, kDelta><<<p.N, 256, sm, s>>>(phi, prop, delta, p, keep_ref, S, sq, ell, beta, key, w0,
+                                                           sweep, acc, status);
+  } else {
+    const size_t sm = (size_t)8 * p.D * sizeof(float);
+    cudaError_t e = set_smem(accept_vec_kernel<8, 32, kDelta>, sm);
+    if (e != cudaSuccess) return e;
+    accept_vec_kernel<8, 32, kDelta><<<(p.N + 7) / 8, 256, sm, s>>>(phi, prop, delta, p, keep_ref, S, sq, ell, beta,
+                                                                    key, w0, sweep, acc, status);
+  }
+  return cudaGetLastError();
+}
+
+static bool vec_ok(const ActionParams& p) { return p.L % 4 == 0 && p.D <= 8 * 4 * 256; }
+
+cudaError_t launch_accept_delta(float* phi, const void* delta_f16, const ActionParams& p, int keep_reference,
+                                double* S, double* sq, double* ell, const double* beta, uint64_t seed,
+                                uint64_t stream_id, uint32_t step, uint32_t sweep, uint32_t* acc_count,
+                                uint32_t* status, cudaStream_t s) {
+  if (p.N <= 0) return cudaSuccess;
+  if (!vec_ok(p)) return cudaErrorInvalidValue;
+  return accept_vec<true>(phi, nullptr, (const __half*)delta_f16, p, keep_reference, S, sq, ell, beta,
+                          philox_key(seed, stream_id), counter_word0(RNG_ACCEPT, step), sweep, acc_count, status, s);
+}
+
 cudaError_t launch_accept(void* phi, const void* prop, int dtype, const ActionParams& p, int keep_reference,
                           double* S, double* sq, double* ell, const double* beta, uint64_t seed, uint64_t stream_id,
                           uint32_t step, uint32_t sweep, uint32_t* acc_count, uint32_t* status, cudaStream_t s) {
   if (p.N <= 0) return cudaSuccess;
   const PhiloxKey key = philox_key(seed, stream_id);
   const uint32_t w0 = counter_word0(RNG_ACCEPT, step);
+  if (dtype == 1 && vec_ok(p))
+    return accept_vec<false>((float*)phi, (const float*)prop, nullptr, p, keep_reference, S, sq, ell, beta, key, w0,
+                             sweep, acc_count, status, s);
   if (dtype == 0)
     return accept_t<double>((double*)phi, (const double*)prop, p, keep_reference, S, sq, ell, beta, key, w0, sweep,
                             acc_count, status, s);
@@ -214,6 +362,17 @@ cudaError_t launch_accept(void* phi, const void* prop, int dtype, const ActionPa
     return accept_t<float>((float*)phi, (const float*)prop, p, keep_reference, S, sq, ell, beta, key, w0, sweep,
                            acc_count, status, s);
   return cudaErrorInvalidValue;
+}
+
+__global__ void apply_delta_kernel(const float* __restrict__ phi, const __half* __restrict__ delta,
+                                   float* __restrict__ prop, long long n) {
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+    prop[k] = phi[k] + __half2float(delta[k]);
+}
+
+cudaError_t launch_apply_delta(const float* phi, const void* delta_f16, float* prop, long long n, cudaStream_t s) {
+  apply_delta_kernel<<<sm_count() * 8, 256, 0, s>>>(phi, (const __half*)delta_f16, prop, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_magnetisation(const void* phi, int dtype, int N, int D, double* M, cudaStream_t s) {

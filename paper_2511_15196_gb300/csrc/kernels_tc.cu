@@ -1,7 +1,8 @@
 // tcgen05 tensor-core GEMM with TMA operand staging (sm_103a), for the one
 // dense contraction of the sampler:
-//   proposal   Phi' = Phi + s Z L^T  (Z: N x D normals, L: D x D lower Cholesky
-//              factor; a 256-column tile [n0, n0+256) only needs k < n0+256), and
+//   proposal   increment Delta = s Z L^T stored as fp16 (Z: N x D normals, L: D x D
+//              lower Cholesky factor; a 256-column tile [n0, n0+256) only needs
+//              k < n0+256); the accept kernel forms Phi + Delta while it loads Phi, and
 //   covariance Sigma = Xc^T Xc / (N-1) on the lower triangle (Xc^T: D x N).
 // Both operands are bf16, K-contiguous, loaded by TMA into 128B-swizzled shared
 // tiles; one elected thread issues tcgen05.mma (M=128, N=256, K=16, fp32
@@ -12,6 +13,7 @@
 // Every mbarrier wait is bounded (about one second); a wait that gives up sets
 // ST_TIMEOUT and an abort flag that stops the other roles.
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <algorithm>
 #include "internal.h"
 #include "common.cuh"
@@ -35,8 +37,7 @@ constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >
 struct Params {
   int M, Nn, K;
   int tiles_m, tiles_n, num_tiles;
-  const float* phi;
-  float* prop;
+  __half* delta;
   float scale;
   double* sigma;
   double inv;
@@ -246,22 +247,25 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         if (gm < p.M && gn0 < p.Nn) {
           if (MODE == 0) {
             const size_t o = (size_t)gm * p.Nn + gn0;
-            if (gn0 + 32 <= p.Nn && (p.Nn & 3) == 0) {
-              const float4* src = reinterpret_cast<const float4*>(p.phi + o);
-              float4* dst = reinterpret_cast<float4*>(p.prop + o);
+            if (gn0 + 32 <= p.Nn && (p.Nn & 7) == 0) {
+              uint4* dst = reinterpret_cast<uint4*>(p.delta + o);
 #pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                float4 f = src[j];
-                f.x += p.scale * v[4 * j];
-                f.y += p.scale * v[4 * j + 1];
-                f.z += p.scale * v[4 * j + 2];
-                f.w += p.scale * v[4 * j + 3];
-                dst[j] = f;
+              for (int j = 0; j < 4; ++j) {
+                uint4 pk;
+                __half2 h0 = __floats2half2_rn(p.scale * v[8 * j], p.scale * v[8 * j + 1]);
+                __half2 h1 = __floats2half2_rn(p.scale * v[8 * j + 2], p.scale * v[8 * j + 3]);
+                __half2 h2 = __floats2half2_rn(p.scale * v[8 * j + 4], p.scale * v[8 * j + 5]);
+                __half2 h3 = __floats2half2_rn(p.scale * v[8 * j + 6], p.scale * v[8 * j + 7]);
+                pk.x = *reinterpret_cast<uint32_t*>(&h0);
+                pk.y = *reinterpret_cast<uint32_t*>(&h1);
+                pk.z = *reinterpret_cast<uint32_t*>(&h2);
+                pk.w = *reinterpret_cast<uint32_t*>(&h3);
+                dst[j] = pk;
               }
             } else {
 #pragma unroll
               for (int j = 0; j < 32; ++j)
-                if (gn0 + j < p.Nn) p.prop[o + j] = p.phi[o + j] + p.scale * v[j];
+                if (gn0 + j < p.Nn) p.delta[o + j] = __float2half_rn(p.scale * v[j]);
             }
           } else {
             double* row = p.sigma + (size_t)gm * p.Nn;
@@ -334,8 +338,8 @@ static cudaError_t launch(const CUtensorMap& a, const CUtensorMap& b, const Para
 
 bool tc_available() { return tc::encode_fn() != nullptr; }
 
-cudaError_t launch_propose_tc(const float* phi, float* prop, const void* Zb, int ldz, const void* Lb, int ldl, int N,
-                              int D, float scale, uint32_t* status, cudaStream_t s) {
+cudaError_t launch_propose_tc(void* delta_f16, const void* Zb, int ldz, const void* Lb, int ldl, int N, int D,
+                              float scale, uint32_t* status, cudaStream_t s) {
   CUtensorMap ma, mb;
   if (!tc::make_map(&ma, Zb, D, N, ldz, tc::BM) || !tc::make_map(&mb, Lb, D, D, ldl, tc::BN))
     return cudaErrorInvalidValue;
@@ -346,8 +350,7 @@ cudaError_t launch_propose_tc(const float* phi, float* prop, const void* Zb, int
   p.tiles_m = (N + tc::BM - 1) / tc::BM;
   p.tiles_n = (D + tc::BN - 1) / tc::BN;
   p.num_tiles = p.tiles_m * p.tiles_n;
-  p.phi = phi;
-  p.prop = prop;
+  p.delta = (__half*)delta_f16;
   p.scale = scale;
   p.status = status;
   return tc::launch<0>(ma, mb, p, s);

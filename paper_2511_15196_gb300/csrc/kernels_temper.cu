@@ -190,19 +190,35 @@ static cudaError_t launch_bisect_t(int G, const double* ell, int N, const double
   return cudaLaunchCooperativeKernel((const void*)bisect_kernel<EPT>, dim3(G), dim3(kThreads), args, 0, s);
 }
 
+// One CTA: the grid barrier degenerates to the CTA's own arrival (nothing waits on
+// another CTA), so an ordinary launch is safe next to other streams' work.
+template <int EPT>
+static cudaError_t launch_bisect_one(const double* ell, int N, const double* beta_in, double rho, int iters,
+                                     double* w, double* out, GridSync gs, cudaStream_t s) {
+  bisect_kernel<EPT><<<1, kThreads, 0, s>>>(ell, N, beta_in, rho, iters, w, out, gs);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bisect(const double* ell, int N, const double* beta_in, double rho, int iters, double* w,
-                          double* out, void* scratch, uint32_t* status, cudaStream_t s) {
+                          double* out, void* scratch, uint32_t* status, cudaStream_t s, bool single_cta) {
   if (N <= 0) return cudaErrorInvalidValue;
+  unsigned char* base = (unsigned char*)scratch;
+  GridSync gs{(unsigned*)base, (unsigned*)(base + 4), (double*)(base + 256), status};
+  cudaError_t e = cudaMemsetAsync(base, 0, 8, s);
+  if (e != cudaSuccess) return e;
+  if (single_cta) {
+    const int ept = (N + kThreads - 1) / kThreads;
+    if (ept <= 8) return launch_bisect_one<8>(ell, N, beta_in, rho, iters, w, out, gs, s);
+    if (ept <= 16) return launch_bisect_one<16>(ell, N, beta_in, rho, iters, w, out, gs, s);
+    if (ept <= 32) return launch_bisect_one<32>(ell, N, beta_in, rho, iters, w, out, gs, s);
+    return cudaErrorInvalidValue;
+  }
   int G = (N + kThreads - 1) / kThreads;
   const int sms = sm_count();
   if (G > sms) G = sms;
   if (G > kMaxGrid) G = kMaxGrid;
   if (G < 1) G = 1;
   const int ept = (N + G * kThreads - 1) / (G * kThreads);
-  unsigned char* base = (unsigned char*)scratch;
-  GridSync gs{(unsigned*)base, (unsigned*)(base + 4), (double*)(base + 256), status};
-  cudaError_t e = cudaMemsetAsync(base, 0, 8, s);
-  if (e != cudaSuccess) return e;
   if (ept <= 1) return launch_bisect_t<1>(G, ell, N, beta_in, rho, iters, w, out, gs, s);
   if (ept <= 2) return launch_bisect_t<2>(G, ell, N, beta_in, rho, iters, w, out, gs, s);
   if (ept <= 4) return launch_bisect_t<4>(G, ell, N, beta_in, rho, iters, w, out, gs, s);

@@ -46,6 +46,18 @@ struct phi4_run {
   double stage_ms[PHI4_N_STAGES] = {0};
   int64_t kernel_launches = 0;  // kernels this run has launched
   int ridge_level = 0;          // decades above chol_jitter_rel that made the last Cholesky succeed
+  void* chol_aux = nullptr;     // diagonal-block inverses of the blocked Cholesky
+  cudaStream_t side = nullptr;  // high-priority look-ahead stream of the Cholesky
+  cudaEvent_t evA = nullptr, evB = nullptr;
+  // batched form: a batch handle owns its member runs (each with its own stream);
+  // a member's `owner` points back to the batch
+  bool batch = false;
+  phi4_run* owner = nullptr;
+  std::vector<phi4_run*> members;
+  bool owns_stream = false;
+  double* batch_scalars = nullptr;    // device [R][12] gathered per-run results
+  void** batch_ptrs = nullptr;        // device [R][2]: each member's scal and status
+  cudaEvent_t join = nullptr;
   int64_t stage_launches[PHI4_N_STAGES] = {0};
 };
 
@@ -96,6 +108,12 @@ ActionParams action_params(const phi4_run* r);
 phi4_status read_status(phi4_run* r, uint32_t* st);
 phi4_status status_to_error(uint32_t st);
 phi4_status refit_factor(phi4_run* r, const void* pts, int n_pts);
+phi4_status refit_enqueue(phi4_run* r, const void* pts, int n_pts);
+phi4_status factor_attempt(phi4_run* r);
+phi4_status refit_check(phi4_run* r, uint32_t st);
+phi4_status step_front(phi4_run* r, bool single_cta_bisect);
+phi4_status step_back(phi4_run* r);
+phi4_status step_finish(phi4_run* r, const double* h, const uint32_t* sw, double* beta_out);
 phi4_status ns_replace(phi4_run* r, int32_t* done_out);
 phi4_status ns_evidence(phi4_run* r, double* logz, double* logz_err);
 

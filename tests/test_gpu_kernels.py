@@ -4,7 +4,7 @@ identical seeded inputs. Tolerances:
   * FP32 kernels: action relative 1e-5; GEMMs within the worst-case float
     dot-product bound gamma_K = K u / (1 - K u), u = 2^-24, on sum |a||b|;
   * bf16 tensor-core GEMMs: operand rounding 2 u_b + u_b^2 (u_b = 2^-8) plus gamma_K,
-    both on sum |a||b|;
+    both on sum |a||b|, plus the fp16 rounding u_h = 2^-11 of the stored increment;
   * integer and index results (resampling, gather): bit-exact.
 """
 import math
@@ -27,6 +27,7 @@ import paper_2511_15196_gb300 as p  # noqa: E402
 
 U32 = 2.0 ** -24
 UB = 2.0 ** -8
+UH = 2.0 ** -11  # fp16 unit roundoff (the mixed proposal stores its increment in fp16)
 
 
 def cuda(x, dtype=None):
@@ -194,6 +195,19 @@ def test_cholesky_fp64(D):
     assert (np.triu(Lg, 1) == 0).all()
 
 
+@pytest.mark.parametrize("D", [1, 63, 64, 130, 1024])
+def test_cholesky_fp32(D):
+    A = inputs.spd_matrix(D, seed=D + 7, cond=1e2)
+    ridge = 1e-3
+    Lg, st = p.cholesky_f32(cuda(A), ridge)
+    assert int(st.cpu()[0]) == 0
+    Lg = Lg.cpu().numpy().astype(np.float64)
+    ref = np.linalg.cholesky(A.astype(np.float32).astype(np.float64) + ridge * np.eye(D))
+    # backward-stable float Cholesky: |L - L_ref| bounded by a modest multiple of D u kappa-free scale
+    np.testing.assert_allclose(Lg, ref, rtol=0, atol=64 * D ** 0.5 * U32 * 1e2 * np.abs(ref).max())
+    assert (np.triu(Lg, 1) == 0).all()
+
+
 def test_cholesky_flags_indefinite():
     D = 100
     A = inputs.spd_matrix(D, seed=1)
@@ -239,7 +253,7 @@ def test_propose_single(N, L, precision):
         Lt[:, :D] = cuda(Lc, torch.bfloat16)
         Lt = Lt  # row pitch ld (multiple of 8)
         Lr = Lc
-        op_err = 2 * UB + UB * UB
+        op_err = 2 * UB + UB * UB + UH * (1 + 2 * UB)
     got = p.rw_propose(cuda(phi), Lt, precision, s, 11, 3, 4, 2).cpu().numpy().astype(np.float64)
     ref, Z = _propose_ref(phi.astype(np.float64), Lr, s, N, D, 24, 4, 2)
     absprod = np.abs(Z) @ np.abs(Lr).T
@@ -265,7 +279,8 @@ def test_propose_bf16_full_size_sampled_rows():
     Z = np.stack([oph.normals(21, 0, oph.KIND_PROPOSE, 1, 0, 1, D, bits=24, row0=int(r))[0] for r in rows])
     ref = phi[rows].astype(np.float64) + s * (Z @ Lc.T)
     absprod = np.abs(Z) @ np.abs(Lc).T
-    bound = s * ((2 * UB + UB * UB + gamma(D)) * absprod + 8 * U32 * 6 * np.abs(Lc).sum(1)[None, :]) \
+    bound = s * ((2 * UB + UB * UB + UH * (1 + 2 * UB) + gamma(D)) * absprod
+                 + 8 * U32 * 6 * np.abs(Lc).sum(1)[None, :]) \
         + 2 * U32 * (np.abs(ref) + np.abs(phi[rows]))
     err = np.abs(got - ref)
     assert (err <= bound).all(), (err / bound).max()
@@ -299,6 +314,36 @@ def test_accept_fp64(L, N, keep_reference):
     np.testing.assert_allclose(tsq.cpu().numpy()[~near], rsq[~near], rtol=1e-12)
     rell = olat.tempering_loglik(rS, rsq, D, keep_reference)
     np.testing.assert_allclose(tell.cpu().numpy()[~near], rell[~near], rtol=1e-12)
+
+
+@pytest.mark.parametrize("L,N", [(64, 300), (32, 1000), (8, 777), (12, 64)])
+def test_accept_delta_matches_oracle(L, N):
+    # mixed-form accept: proposal = phi + fp16 increment, formed in float while loading
+    D = L * L
+    phi = inputs.broken_phase_fields(N, D, seed=L + 40).astype(np.float32)
+    delta = (0.02 * inputs.fields(N, D, seed=L + 41)).astype(np.float16)
+    prop = (phi + delta.astype(np.float32)).astype(np.float32)  # the float sum the kernel forms
+    m2, lam, beta = -4.0, 8.0, 0.6
+    phi64, prop64 = phi.astype(np.float64), prop.astype(np.float64)
+    S = olat.action(phi64, L, m2, lam)
+    sq = olat.sq_norm(phi64)
+    ell = olat.tempering_loglik(S, sq, D)
+    tphi, tS, tsq, tell = cuda(phi), cuda(S), cuda(sq), cuda(ell)
+    cnt = p.rw_accept_delta(tphi, torch.as_tensor(delta).cuda(), L, m2, lam, tS, tsq, tell, beta, 9, 1, 5, 3)
+    u = oph.uniform53(9, 1, oph.KIND_ACCEPT, 5, 3, np.arange(N))
+    _, _, _, acc, S2, sq2, la = omut.accept(phi64, S, sq, prop64, np.log(u), beta, L, m2, lam, 1.0, 1.0)
+    site_scale = np.abs(S2) + np.abs(S) + 1.0
+    near = np.abs(np.log(u) - la) < beta * 2e-5 * site_scale
+    gphi = tphi.cpu().numpy()
+    gacc = np.all(gphi == prop, axis=1)
+    assert (gacc[~near] == acc[~near]).all()
+    assert (gacc | np.all(gphi == phi, axis=1)).all()
+    assert int(cnt.cpu()[0]) == gacc.sum()
+    ok = gacc & ~near
+    site = olat.kinetic_site_terms(prop64, L).reshape(N, -1) + m2 * prop64 ** 2 + lam * prop64 ** 4
+    scale = np.abs(site).sum(axis=1)
+    assert (np.abs(tS.cpu().numpy() - S2)[ok] <= 1e-5 * scale[ok]).all()
+    np.testing.assert_allclose(tsq.cpu().numpy()[ok], sq2[ok], rtol=1e-6)
 
 
 def test_accept_fp32_decisions():
