@@ -96,6 +96,9 @@ typedef struct {
   int32_t bisect_iters;      /* maximum bisection steps for the next beta (64) */
   int32_t slice_max_shrink;  /* slice shrinkage tries before a step is abandoned (64) */
   uint64_t seed, stream_id;  /* Philox key material */
+  int32_t chol_mode;         /* double Cholesky trailing update: 0 automatic (tensor cores for D >= 256),
+                                1 FP64 SIMT, 2 FP64-accurate exact-digit emulation on the tensor cores */
+  int32_t reserved;          /* zero */
 } phi4_config;
 
 typedef struct {
@@ -296,11 +299,17 @@ phi4_status phi4_covariance(const void* phi, int32_t precision, int32_t N, int32
  * double) is added to its diagonal; on exit the lower triangle holds L and the
  * strictly upper triangle is zeroed. A non-positive pivot sets bit 2 of
  * `*d_status` (device uint32) and stops the factorisation. Blocked right-looking
- * with 64 x 64 blocks, all arithmetic double; the inverses of the diagonal blocks
- * (used for the panel solves) live in `scratch` (device, phi4_cholesky_scratch_bytes). */
+ * with 64 x 64 blocks; the inverses of the diagonal blocks (used for the panel
+ * solves) and the digit planes of the tensor-core update live in `scratch` (device,
+ * phi4_cholesky_scratch_bytes). `mode` as phi4_config.chol_mode: the trailing update
+ * A22 -= P P^T either in FP64 on the SIMT pipes, or exactly emulated on the tcgen05
+ * tensor cores (each panel row split into eight 7-bit integer digits under a per-row
+ * power of two, digit products summed exactly in fp32 by weight, recombined in
+ * double-float and subtracted in FP64; error comparable to a length-64 FP64 dot
+ * product). Diagonal blocks and panel solves are always FP64. */
 size_t phi4_cholesky_scratch_bytes(int32_t D);
 phi4_status phi4_cholesky(double* a, int32_t D, const double* d_ridge, uint32_t* d_status, void* scratch,
-                          size_t scratch_bytes, void* stream);
+                          size_t scratch_bytes, int32_t mode, void* stream);
 
 /* The same factorisation in float for the plain FP32 form: `sigma` (device double,
  * lower triangle read) is rounded to float into `a` (device float[D*D], row-major),

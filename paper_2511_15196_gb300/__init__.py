@@ -40,7 +40,8 @@ class CConfig(ctypes.Structure):
                 ("ns_n_delete", ctypes.c_int32), ("ns_slice_steps", ctypes.c_int32),
                 ("ns_stop_frac", ctypes.c_double), ("chol_jitter_rel", ctypes.c_double),
                 ("bisect_iters", ctypes.c_int32), ("slice_max_shrink", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint64), ("chol_mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class CObs(ctypes.Structure):
@@ -74,12 +75,13 @@ class Config:
     slice_max_shrink: int = 64
     seed: int = 0
     stream_id: int = 0
+    chol_mode: int = 0
 
     def to_c(self):
         return CConfig(self.L, self.N, self.kind, self.precision, self.m2, self.lam, self.c_kin, self.c_mass,
                        int(bool(self.keep_reference)), self.n_mcmc, self.ess_target, self.rw_scale,
                        self.ns_n_delete, self.ns_slice_steps, self.ns_stop_frac, self.chol_jitter_rel,
-                       self.bisect_iters, self.slice_max_shrink, self.seed, self.stream_id)
+                       self.bisect_iters, self.slice_max_shrink, self.seed, self.stream_id, self.chol_mode, 0)
 
 
 _lib = None
@@ -116,7 +118,7 @@ _SIGS = {
     "phi4_covariance_scratch_bytes": ([_I32, _I32, _I32], _SZ),
     "phi4_covariance": ([_P, _I32, _I32, _I32, _P, _P, _SZ, _P], _I32),
     "phi4_cholesky_scratch_bytes": ([_I32], _SZ),
-    "phi4_cholesky": ([_P, _I32, _P, _P, _P, _SZ, _P], _I32),
+    "phi4_cholesky": ([_P, _I32, _P, _P, _P, _SZ, _I32, _P], _I32),
     "phi4_cholesky_f32": ([_P, _P, _I32, _P, _P, _P, _SZ, _P], _I32),
     "phi4_propose_scratch_bytes": ([_I32, _I32, _I32], _SZ),
     "phi4_rw_propose": ([_P, _P, _P, _I32, _I32, _I32, _I32, _F64, _U64, _U64, _U32, _U32, _P, _SZ, _P], _I32),
@@ -402,15 +404,16 @@ def covariance(phi, precision, stream=None):
     return sigma
 
 
-def cholesky(a, ridge=0.0, stream=None):
-    """In-place FP64 Cholesky of a (D x D double CUDA tensor); returns (a, status)."""
+def cholesky(a, ridge=0.0, mode=0, stream=None):
+    """In-place FP64 Cholesky of a (D x D double CUDA tensor); returns (a, status).
+    mode: 0 automatic, 1 FP64 SIMT trailing update, 2 tensor-core emulated trailing update."""
     import torch
     D = a.shape[0]
     r = torch.tensor([ridge], dtype=torch.float64, device=a.device)
     st = torch.zeros(1, dtype=torch.int32, device=a.device)
     nb = lib().phi4_cholesky_scratch_bytes(D)
     scratch = torch.empty(nb, dtype=torch.uint8, device=a.device)
-    _check(lib().phi4_cholesky(_ptr(a), D, _ptr(r), _ptr(st), _ptr(scratch), nb, _stream(stream)))
+    _check(lib().phi4_cholesky(_ptr(a), D, _ptr(r), _ptr(st), _ptr(scratch), nb, mode, _stream(stream)))
     return a, st
 
 

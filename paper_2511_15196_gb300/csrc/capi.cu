@@ -57,6 +57,7 @@ phi4_status check_config(const phi4_config* c) {
     ARG_CHECK(c->N <= 8192, "nested sampling supports N <= 8192 live points (N = %d)", c->N);
   }
   ARG_CHECK(c->chol_jitter_rel >= 0.0 && isfinite(c->chol_jitter_rel), "chol_jitter_rel invalid");
+  ARG_CHECK(c->chol_mode >= 0 && c->chol_mode <= 2, "chol_mode = %d unknown", c->chol_mode);
   return PHI4_OK;
 }
 
@@ -174,7 +175,8 @@ phi4_status factor_attempt(phi4_run* r) {
                                  r->side, r->evA, r->evB));
   } else {
     CUDA_TRY(launch_copy_lower(r->sigma, r->chol, D, s));
-    CUDA_TRY(launch_cholesky(r->chol, D, r->scal + SC_RIDGE, r->status, r->chol_aux, s, r->side, r->evA, r->evB));
+    CUDA_TRY(launch_cholesky(r->chol, D, r->scal + SC_RIDGE, r->status, r->chol_aux, s, r->side, r->evA, r->evB,
+                             r->cfg.chol_mode));
   }
   r->kernel_launches += 1 + cholesky_launches(D);
   return PHI4_OK;
@@ -711,13 +713,15 @@ phi4_status phi4_covariance(const void* phi, int32_t precision, int32_t N, int32
 size_t phi4_cholesky_scratch_bytes(int32_t D) { return D > 0 ? cholesky_aux_bytes(D) : 0; }
 
 phi4_status phi4_cholesky(double* a, int32_t D, const double* d_ridge, uint32_t* d_status, void* scratch,
-                          size_t scratch_bytes, void* stream) {
+                          size_t scratch_bytes, int32_t mode, void* stream) {
   ARG_CHECK(a && d_status && scratch, "NULL argument");
   ARG_CHECK(D >= 1 && D <= 16384, "D = %d outside [1, 16384]", D);
+  ARG_CHECK(mode >= 0 && mode <= 2, "mode %d unknown", mode);
   ARG_CHECK(scratch_bytes >= cholesky_aux_bytes(D), "scratch too small");
+  ARG_CHECK(((uintptr_t)scratch & 255) == 0, "scratch must be 256-byte aligned");
   cudaStream_t s = (cudaStream_t)stream;
   CUDA_TRY(launch_copy_lower(a, a, D, s));
-  CUDA_TRY(launch_cholesky(a, D, d_ridge, d_status, scratch, s));
+  CUDA_TRY(launch_cholesky(a, D, d_ridge, d_status, scratch, s, nullptr, nullptr, nullptr, mode));
   return PHI4_OK;
 }
 

@@ -58,8 +58,13 @@ cudaError_t launch_copy_lower(const double* src, double* dst, int D, cudaStream_
 // In-place blocked Cholesky; aux: cholesky_aux_bytes(D) device scratch for the diagonal-block
 // inverses. With side != nullptr the look-ahead schedule uses `side` and the two events.
 size_t cholesky_aux_bytes(int D);
+// mode: 0 automatic (tensor-core trailing update for D >= 256), 1 FP64 SIMT update, 2 tensor-core update
 cudaError_t launch_cholesky(double* a, int D, const double* ridge, uint32_t* status, void* aux, cudaStream_t s,
-                            cudaStream_t side = nullptr, cudaEvent_t evA = nullptr, cudaEvent_t evB = nullptr);
+                            cudaStream_t side = nullptr, cudaEvent_t evA = nullptr, cudaEvent_t evB = nullptr,
+                            int mode = 0);
+// A22 -= P P^T from the digit planes of the panel P (kernels_tc.cu)
+cudaError_t launch_chol_update_tc(double* a, int D, int b0, int m, const void* planes, int m_pad, const int* rexp,
+                                  int part, uint32_t* status, cudaStream_t s);
 int cholesky_launches(int D);  // kernels one launch_cholesky enqueues
 // float factorisation of the lower triangle of sigma (copied into a) for the plain FP32 form
 cudaError_t launch_cholesky_f32(const double* sigma, float* a, int D, const double* ridge, uint32_t* status,

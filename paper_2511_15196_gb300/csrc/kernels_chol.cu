@@ -12,7 +12,9 @@ namespace phi4 {
 
 namespace {
 constexpr int NB = 64;
-}
+size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
+int mpad_of(int D) { return ((D + 127) / 128) * 128; }
+}  // namespace
 
 // dst = lower triangle of src, zeros strictly above the diagonal (src may equal dst).
 template <typename T>
@@ -200,6 +202,39 @@ __global__ void __launch_bounds__(256) syrk_update_kernel(T* __restrict__ a, int
   }
 }
 
+// Exact digit splitting of a Cholesky panel for the tensor-core trailing update.
+// Row i of the panel (64 doubles below the diagonal block) gets the exponent
+// e_i = ilogb(max |x|) + 1 (so |x| < 2^e_i) and every element the integer
+// N = floor(|x| 2^(56 - e_i)) < 2^56, cut into eight base-128 digits
+// d_k = (N >> (56 - 7k)) & 127 carrying x's sign: x = sum_k d_k 2^(e_i - 7k) up to
+// 2^(e_i - 56). Digits are integers below 128 in magnitude, exact in bf16.
+// Planes: plane k (0..7) holds rows [k m_pad, (k+1) m_pad) of a [8 m_pad][64] array.
+__global__ void digit_split_kernel(const double* __restrict__ a, int D, int row0, int col0, int m, int m_pad,
+                                   __nv_bfloat16* __restrict__ planes, int* __restrict__ rexp) {
+  const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (row >= m_pad) return;
+  double x0 = 0.0, x1 = 0.0;
+  if (row < m) {
+    const double* src = a + (size_t)(row0 + row) * D + col0;
+    x0 = src[lane];
+    x1 = src[lane + 32];
+  }
+  const double amax = warp_max(fmax(fabs(x0), fabs(x1)));
+  const int e = amax > 0.0 ? ilogb(amax) + 1 : 0;
+  if (lane == 0) rexp[row] = e;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const double x = h ? x1 : x0;
+    const unsigned long long N = (unsigned long long)ldexp(fabs(x), 56 - e);
+    const bool neg = x < 0.0;
+#pragma unroll
+    for (int k = 1; k <= 8; ++k) {
+      const int d = (int)((N >> (56 - 7 * k)) & 127ull);
+      planes[((size_t)(k - 1) * m_pad + row) * 64 + lane + 32 * h] = __float2bfloat16_rn((float)(neg ? -d : d));
+    }
+  }
+}
+
 template <typename Ti, typename To>
 __global__ void convert_factor_kernel(const Ti* __restrict__ Lc, int D, To* __restrict__ out, int ld) {
   const long long total = (long long)D * ld;
@@ -222,10 +257,27 @@ cudaError_t launch_copy_lower(const double* src, double* dst, int D, cudaStream_
 // while `s` applies the rest of the trailing update (look-ahead); the arithmetic of
 // every tile is the same either way, so both schedules give identical results.
 template <typename T>
-static cudaError_t cholesky_t(T* a, int D, const double* ridge, T* W, uint32_t* status, cudaStream_t s,
-                              cudaStream_t side, cudaEvent_t evA, cudaEvent_t evB) {
+static cudaError_t cholesky_t(T* a, int D, const double* ridge, void* aux, uint32_t* status, cudaStream_t s,
+                              cudaStream_t side, cudaEvent_t evA, cudaEvent_t evB, bool tensor_update) {
   const int nblk = (D + NB - 1) / NB;
   const bool ahead = side != nullptr && nblk > 2;
+  T* W = (T*)aux;
+  const int m_pad = mpad_of(D);
+  unsigned char* dig0 = (unsigned char*)aux + round256((size_t)nblk * NB * NB * sizeof(double));
+  __nv_bfloat16* planes[2] = {(__nv_bfloat16*)dig0, (__nv_bfloat16*)(dig0 + round256(8 * (size_t)m_pad * 64 * 2))};
+  int* rexp0 = (int*)(dig0 + 2 * round256(8 * (size_t)m_pad * 64 * 2));
+  int* rexp[2] = {rexp0, (int*)((unsigned char*)rexp0 + round256((size_t)m_pad * sizeof(int)))};
+  const bool tcu = tensor_update && sizeof(T) == 8;
+  // trailing update after block column kb (part: 0 all, 1 next block column, 2 the rest)
+  auto update = [&](int kb, int part, unsigned grid_all, unsigned grid_col, unsigned grid_rest,
+                    cudaStream_t st) -> cudaError_t {
+    const int k0 = kb * NB, b0 = k0 + NB;
+    if (tcu)
+      return launch_chol_update_tc((double*)a, D, b0, D - b0, planes[kb & 1], m_pad, rexp[kb & 1], part, status, st);
+    const unsigned g = part == 0 ? grid_all : (part == 1 ? grid_col : grid_rest);
+    if (g > 0) syrk_update_kernel<T><<<g, 256, 0, st>>>(a, D, k0, part, status);
+    return cudaGetLastError();
+  };
   const size_t sm_potrf = 2 * sizeof(T) * NB * (NB + 1), sm_trsm = sizeof(T) * (NB + 32) * (NB + 1);
   cudaError_t e0 = cudaFuncSetAttribute(potrf_inv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_potrf);
   if (e0 != cudaSuccess) return e0;
@@ -235,27 +287,31 @@ static cudaError_t cholesky_t(T* a, int D, const double* ridge, T* W, uint32_t* 
     const int k0 = kb * NB;
     potrf_inv_kernel<T><<<1, 256, sm_potrf, st>>>(a, D, k0, ridge, W + (size_t)kb * NB * NB, status);
     const int rows = D - k0 - min(NB, D - k0);
-    if (rows > 0)
+    if (rows > 0) {
       trsm_gemm_kernel<T><<<(rows + 31) / 32, 256, sm_trsm, st>>>(a, D, k0, W + (size_t)kb * NB * NB, status);
+      if (tcu)  // planes use the stride m_pad of the update kernel's tensor maps; rows >= `rows` get zeros
+        digit_split_kernel<<<(m_pad * 32 + 255) / 256, 256, 0, st>>>((const double*)a, D, k0 + NB, k0, rows, m_pad,
+                                                                     planes[kb & 1], rexp[kb & 1]);
+    }
   };
   panel(0, s);
   for (int kb = 0; kb < nblk - 1; ++kb) {
     const int k0 = kb * NB;
     const int below = nblk - kb - 1;
     const long long all = (long long)below * (below + 1) / 2;
+    const long long rest = all - below;
+    cudaError_t e;
     if (!ahead) {
-      syrk_update_kernel<T><<<(unsigned)all, 256, 0, s>>>(a, D, k0, 0, status);
+      if ((e = update(kb, 0, (unsigned)all, (unsigned)below, (unsigned)rest, s)) != cudaSuccess) return e;
       panel(kb + 1, s);
       continue;
     }
-    cudaError_t e;
     if ((e = cudaEventRecord(evA, s)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(side, evA, 0)) != cudaSuccess) return e;
-    syrk_update_kernel<T><<<(unsigned)below, 256, 0, side>>>(a, D, k0, 1, status);
+    if ((e = update(kb, 1, (unsigned)all, (unsigned)below, (unsigned)rest, side)) != cudaSuccess) return e;
     panel(kb + 1, side);
     if ((e = cudaEventRecord(evB, side)) != cudaSuccess) return e;
-    const long long rest = all - below;
-    if (rest > 0) syrk_update_kernel<T><<<(unsigned)rest, 256, 0, s>>>(a, D, k0, 2, status);
+    if ((e = update(kb, 2, (unsigned)all, (unsigned)below, (unsigned)rest, s)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(s, evB, 0)) != cudaSuccess) return e;
   }
   return cudaGetLastError();
@@ -263,18 +319,26 @@ static cudaError_t cholesky_t(T* a, int D, const double* ridge, T* W, uint32_t* 
 
 size_t cholesky_aux_bytes(int D) {
   const size_t nblk = (size_t)(D + NB - 1) / NB;
-  return nblk * NB * NB * sizeof(double);
+  const size_t mp = (size_t)mpad_of(D);
+  return round256(nblk * NB * NB * sizeof(double)) + 2 * round256(8 * mp * 64 * 2) + 2 * round256(mp * sizeof(int));
+}
+
+// Which trailing update the double factorisation uses (mode 0 = automatic).
+static bool use_tensor_update(int D, int mode) {
+  if (mode == 1) return false;
+  if (mode == 2) return tc_available();
+  return D >= 256 && tc_available();
 }
 
 cudaError_t launch_cholesky(double* a, int D, const double* ridge, uint32_t* status, void* aux, cudaStream_t s,
-                            cudaStream_t side, cudaEvent_t evA, cudaEvent_t evB) {
-  return cholesky_t<double>(a, D, ridge, (double*)aux, status, s, side, evA, evB);
+                            cudaStream_t side, cudaEvent_t evA, cudaEvent_t evB, int mode) {
+  return cholesky_t<double>(a, D, ridge, aux, status, s, side, evA, evB, use_tensor_update(D, mode));
 }
 
 cudaError_t launch_cholesky_f32(const double* sigma, float* a, int D, const double* ridge, uint32_t* status,
                                 void* aux, cudaStream_t s, cudaStream_t side, cudaEvent_t evA, cudaEvent_t evB) {
   copy_lower_kernel<float><<<sm_count() * 4, 256, 0, s>>>(sigma, a, D);
-  return cholesky_t<float>(a, D, ridge, (float*)aux, status, s, side, evA, evB);
+  return cholesky_t<float>(a, D, ridge, aux, status, s, side, evA, evB, false);
 }
 
 int cholesky_launches(int D) {

@@ -99,6 +99,13 @@ PHI4_DEV void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumu
       "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
       : "memory");
 }
+PHI4_DEV void umma_idesc(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
 PHI4_DEV void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
@@ -336,6 +343,213 @@ static cudaError_t launch(const CUtensorMap& a, const CUtensorMap& b, const Para
 
 }  // namespace tc
 
+// ---------------------------------------------------------------------------
+// FP64 Cholesky trailing update on the tensor cores (exact digit emulation).
+// A22 -= P P^T with P the 64-wide panel below the diagonal block, given as eight
+// bf16 digit planes d_k (|d| < 128, exact) and row exponents e (see digit_split_kernel):
+//   (P P^T)_ij = 2^(e_i + e_j) sum_{k,l} 2^(-7(k+l)) T_kl,  T_kl = sum_n d_ik,n d_jl,n.
+// Products are exact in fp32 and, grouped by c = k + l, each group sum is an integer
+// below 2^23 in magnitude (at most 8 pairs x 64 terms x 2^14), so tcgen05 accumulates
+// every U_c = sum_{k+l=c} T_kl exactly in TMEM. Groups c = 2..9 are kept (dropped
+// groups weigh < 2^-47 of sum |x||y|, like the rounding of a length-64 FP64 dot
+// product); U_9 .. U_2 are combined by a Horner pass in double-float (two fp32)
+// and the result, scaled by 2^(e_i + e_j - 14), is subtracted in FP64.
+// Tiles of 128 rows x 64 columns of the lower trailing matrix; part 1 = the next
+// block column only, part 2 = the rest, part 0 = all.
+namespace emu {
+constexpr int BM = 128, BN = 64, KD = 64, ND = 8, NC = 8;
+constexpr int A_PLANE = BM * KD * 2;
+constexpr int B_PLANE = BN * KD * 2;
+constexpr int SMEM_DATA = ND * (A_PLANE + B_PLANE);
+constexpr int SMEM_BYTES = SMEM_DATA + 1024 + 256;
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+struct Params {
+  double* a;
+  int D, b0, m, m_pad, tiles_m, tiles_n, num_tiles, part;
+  const int* rexp;
+  uint32_t* status;
+};
+
+PHI4_DEV void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+PHI4_DEV void get_tile(const Params& p, int u, int& mb, int& bj) {
+  if (p.part == 1) {
+    mb = u;
+    bj = 0;
+    return;
+  }
+  const int first = p.part == 2 ? 1 : 0;
+  int m = 0, base = 0;
+  for (;;) {
+    const int cnt = max(0, min(p.tiles_n, (m * BM + BM - 1) / BN + 1) - first);
+    if (u < base + cnt) break;
+    base += cnt;
+    ++m;
+  }
+  mb = m;
+  bj = u - base + first;
+}
+
+PHI4_DEV double pow2(int n) {
+  if (n < -1022 || n > 1023) return ldexp(1.0, n);
+  return __longlong_as_double((long long)(n + 1023) << 52);
+}
+
+__global__ void __launch_bounds__(tc::NUM_THREADS, 1)
+    chol_update_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Params p) {
+  using namespace tc;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + ND * A_PLANE;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + SMEM_DATA);
+  uint64_t* empty = full + 1;
+  uint64_t* tfull = full + 2;
+  uint64_t* tempty = full + 3;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(full + 4);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    mbar_init(full, 1);
+    mbar_init(empty, 1);
+    mbar_init(tfull, 1);
+    mbar_init(tempty, 4);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  auto give_up = [&]() {
+    *abort_flag = 1;
+    atomicOr(p.status, ST_TIMEOUT);
+  };
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t phase = 0;
+      for (int u = blockIdx.x; u < p.num_tiles && !*abort_flag; u += gridDim.x) {
+        int mb, bj;
+        get_tile(p, u, mb, bj);
+        if (!mbar_wait(empty, phase ^ 1u, abort_flag)) { give_up(); break; }
+        mbar_expect_tx(full, SMEM_DATA);
+        for (int k = 0; k < ND; ++k) {
+          tma_load_2d(&tmA, full, sA + k * A_PLANE, 0, k * p.m_pad + mb * BM);
+          tma_load_2d(&tmB, full, sB + k * B_PLANE, 0, k * p.m_pad + bj * BN);
+        }
+        phase ^= 1u;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      uint32_t phase = 0, tphase = 0;
+      for (int u = blockIdx.x; u < p.num_tiles && !*abort_flag; u += gridDim.x) {
+        if (!mbar_wait(tempty, tphase ^ 1u, abort_flag)) { give_up(); break; }
+        tc_fence_after();
+        if (!mbar_wait(full, phase, abort_flag)) { give_up(); break; }
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+        for (int c = 2; c <= NC + 1; ++c) {
+          const uint32_t acc = tmem_base + (uint32_t)((c - 2) * BN);
+          uint32_t accumulate = 0;
+          for (int k = max(1, c - ND); k <= min(ND, c - 1); ++k) {
+            const int l = c - k;
+#pragma unroll
+            for (int kk = 0; kk < KD / 16; ++kk) {
+              umma_idesc(acc, sdesc(a0 + (k - 1) * A_PLANE + kk * 32), sdesc(b0 + (l - 1) * B_PLANE + kk * 32),
+                         IDESC, accumulate);
+              accumulate = 1;
+            }
+          }
+        }
+        umma_commit(empty);
+        umma_commit(tfull);
+        phase ^= 1u;
+        tphase ^= 1u;
+      }
+    }
+  } else {
+    const int q = warp & 3;
+    const int r = q * 32 + lane;
+    uint32_t tphase = 0;
+    for (int u = blockIdx.x; u < p.num_tiles; u += gridDim.x) {
+      int mb, bj;
+      get_tile(p, u, mb, bj);
+      if (!mbar_wait(tfull, tphase, abort_flag)) { give_up(); break; }
+      tc_fence_after();
+      const int ir = mb * BM + r;  // row inside the trailing matrix
+      const bool row_ok = ir < p.m;
+      const int ei = row_ok ? p.rexp[ir] : 0;
+      const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16);
+#pragma unroll 1
+      for (int ch = 0; ch < BN / 16; ++ch) {
+        float hi[16], lo[16];
+        tmem_ld16(trow + (uint32_t)((NC - 1) * BN + ch * 16), hi);
+#pragma unroll
+        for (int t = 0; t < 16; ++t) lo[t] = 0.f;
+#pragma unroll 1
+        for (int c = NC; c >= 2; --c) {
+          float uu[16];
+          tmem_ld16(trow + (uint32_t)((c - 2) * BN + ch * 16), uu);
+#pragma unroll
+          for (int t = 0; t < 16; ++t) {
+            // (hi, lo) <- (hi, lo) 2^-7 + U_c  in double-float (TwoSum, then renormalise)
+            const float h = hi[t] * 0.0078125f, l = lo[t] * 0.0078125f;
+            const float s = h + uu[t];
+            const float bb = s - h;
+            const float err = (h - (s - bb)) + (uu[t] - bb);
+            const float l2 = l + err;
+            const float hs = s + l2;
+            lo[t] = l2 - (hs - s);
+            hi[t] = hs;
+          }
+        }
+        if (row_ok) {
+          const int i = p.b0 + ir;
+          double* arow = p.a + (size_t)i * p.D;
+#pragma unroll
+          for (int t = 0; t < 16; ++t) {
+            const int jc = bj * BN + ch * 16 + t;
+            if (jc < p.m && jc <= ir) {
+              const double v = ((double)hi[t] + (double)lo[t]) * pow2(ei + p.rexp[jc] - 14);
+              arow[p.b0 + jc] -= v;
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty);
+      tphase ^= 1u;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512) : "memory");
+  }
+}
+}  // namespace emu
+
 bool tc_available() { return tc::encode_fn() != nullptr; }
 
 cudaError_t launch_propose_tc(void* delta_f16, const void* Zb, int ldz, const void* Lb, int ldl, int N, int D,
@@ -374,6 +588,40 @@ cudaError_t launch_syrk_tc(const void* XcTb, int ldx, int D, int N, double inv_n
   p.inv = inv_nm1;
   p.status = status;
   return tc::launch<1>(ma, mb, p, s);
+}
+
+cudaError_t launch_chol_update_tc(double* a, int D, int b0, int m, const void* planes, int m_pad, const int* rexp,
+                                  int part, uint32_t* status, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  CUtensorMap ma, mb;
+  if (!tc::make_map(&ma, planes, 64, 8 * m_pad, 64, emu::BM) || !tc::make_map(&mb, planes, 64, 8 * m_pad, 64, emu::BN))
+    return cudaErrorInvalidValue;
+  emu::Params p{};
+  p.a = a;
+  p.D = D;
+  p.b0 = b0;
+  p.m = m;
+  p.m_pad = m_pad;
+  p.tiles_m = (m + emu::BM - 1) / emu::BM;
+  p.tiles_n = (m + emu::BN - 1) / emu::BN;
+  p.part = part;
+  p.rexp = rexp;
+  p.status = status;
+  if (part == 1) {
+    p.num_tiles = p.tiles_m;
+  } else {
+    int count = 0;
+    for (int mm = 0; mm < p.tiles_m; ++mm)
+      count += std::max(0, std::min(p.tiles_n, (mm * emu::BM + emu::BM - 1) / emu::BN + 1) - (part == 2 ? 1 : 0));
+    p.num_tiles = count;
+  }
+  if (p.num_tiles == 0) return cudaSuccess;
+  cudaError_t e =
+      cudaFuncSetAttribute(emu::chol_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, emu::SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  const int grid = std::min(sm_count(), p.num_tiles);
+  emu::chol_update_kernel<<<grid, tc::NUM_THREADS, emu::SMEM_BYTES, s>>>(ma, mb, p);
+  return cudaGetLastError();
 }
 
 }  // namespace phi4

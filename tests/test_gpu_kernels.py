@@ -182,17 +182,38 @@ def test_covariance(N, L, precision):
 
 # ------------------------------------------------------------------ Cholesky
 
-@pytest.mark.parametrize("D", [1, 5, 63, 64, 65, 130, 1024])
-def test_cholesky_fp64(D):
+@pytest.mark.parametrize("mode", [1, 2], ids=["simt", "tc_emulated"])
+@pytest.mark.parametrize("D", [1, 5, 63, 64, 65, 130, 257, 1024])
+def test_cholesky_fp64(D, mode):
     A = inputs.spd_matrix(D, seed=D, cond=1e3)
     ridge = 1e-3
     a = cuda(A)
-    a, st = p.cholesky(a, ridge)
+    a, st = p.cholesky(a, ridge, mode=mode)
     assert int(st.cpu()[0]) == 0
     Lg = a.cpu().numpy()
     ref = np.linalg.cholesky(A + ridge * np.eye(D))
     np.testing.assert_allclose(Lg, ref, rtol=0, atol=1e-11 * np.abs(ref).max())
     assert (np.triu(Lg, 1) == 0).all()
+
+
+@pytest.mark.parametrize("D", [384, 2048, 4096])
+def test_cholesky_tensor_update_matches_fp64(D):
+    # the exact-digit tensor-core trailing update against the FP64 SIMT update and LAPACK
+    g = inputs.rng(D)
+    X = g.standard_normal((D + 64, D)) * np.exp(g.uniform(-3, 3, D))[None, :]   # columns of mixed scale
+    A = X.T @ X / (D + 63)
+    ridge = 1e-6 * np.trace(A) / D
+    a1, s1 = p.cholesky(cuda(A), ridge, mode=1)
+    a2, s2 = p.cholesky(cuda(A), ridge, mode=2)
+    assert int(s1.cpu()[0]) == 0 and int(s2.cpu()[0]) == 0
+    L1, L2 = a1.cpu().numpy(), a2.cpu().numpy()
+    ref = np.linalg.cholesky(A + ridge * np.eye(D))
+    scale = np.abs(ref).max(axis=1, keepdims=True)
+    assert (np.abs(L2 - ref) <= 1e-10 * scale).all(), (np.abs(L2 - ref) / scale).max()
+    assert (np.abs(L2 - L1) <= 1e-10 * scale).all(), (np.abs(L2 - L1) / scale).max()
+    # backward error of the emulated factor at FP64 level
+    R = L2 @ L2.T - (A + ridge * np.eye(D))
+    assert np.abs(R).max() <= 1e-13 * np.abs(A).max() * D ** 0.5
 
 
 @pytest.mark.parametrize("D", [1, 63, 64, 130, 1024])
@@ -212,8 +233,9 @@ def test_cholesky_flags_indefinite():
     D = 100
     A = inputs.spd_matrix(D, seed=1)
     A[70, 70] = -1.0
-    _, st = p.cholesky(cuda(A), 0.0)
-    assert int(st.cpu()[0]) & 2
+    for mode in (1, 2):
+        _, st = p.cholesky(cuda(A), 0.0, mode=mode)
+        assert int(st.cpu()[0]) & 2
 
 
 # ------------------------------------------------------------------ proposal GEMM
