@@ -30,6 +30,9 @@ __global__ void copy_lower_kernel(const double* src, T* dst, int D) {
 
 // Factor the diagonal block in one CTA and form its inverse W = L_kk^{-1} (lower),
 // which turns the panel's triangular solve into a dependency-free product.
+// Per column: one thread forms the pivot with a single rsqrt (FP64 square roots and
+// divisions are long sequences on the FP64 pipe, so they are done once per column),
+// the column is scaled by multiplication, then the trailing block gets a rank-1 update.
 template <typename T>
 __global__ void __launch_bounds__(256) potrf_inv_kernel(T* __restrict__ a, int D, int k0,
                                                         const double* __restrict__ ridge, T* __restrict__ W,
@@ -49,22 +52,37 @@ __global__ void __launch_bounds__(256) potrf_inv_kernel(T* __restrict__ a, int D
     blk[i][j] = v;
   }
   if (threadIdx.x == 0) fail = 0;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   __syncthreads();
   for (int j = 0; j < n; ++j) {
     if (threadIdx.x == 0) {
       const T d = blk[j][j];
-      if (!(d > (T)0) || !isfinite(d)) fail = 1;
-      else blk[j][j] = sqrt(d);
+      if (!(d > (T)0) || !isfinite(d)) {
+        fail = 1;
+      } else {
+        const T ip = rsqrt(d);
+        rdiag[j] = ip;
+        blk[j][j] = d * ip;
+      }
     }
     __syncthreads();
     if (fail) break;
-    const T piv = blk[j][j];
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) blk[i][j] /= piv;
+    const T ip = rdiag[j];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) blk[i][j] *= ip;
     __syncthreads();
-    const int m = n - j - 1;  // trailing size
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      const int i = j + 1 + e / m, l = j + 1 + e % m;
-      if (l <= i) blk[i][l] -= blk[i][j] * blk[l][j];
+    // rank-1 update of the trailing block: thread (ty, tx) of a 16 x 16 layout owns
+    // rows ty + 16a and columns tx + 16b
+#pragma unroll
+    for (int a4 = 0; a4 < 4; ++a4) {
+      const int i = ty + 16 * a4;
+      if (i > j && i < n) {
+        const T lij = blk[i][j];
+#pragma unroll
+        for (int b4 = 0; b4 < 4; ++b4) {
+          const int l = tx + 16 * b4;
+          if (l > j && l <= i) blk[i][l] -= lij * blk[l][j];
+        }
+      }
     }
     __syncthreads();
   }
@@ -72,8 +90,7 @@ __global__ void __launch_bounds__(256) potrf_inv_kernel(T* __restrict__ a, int D
     if (threadIdx.x == 0) atomicOr(status, ST_NOT_PD);
     return;
   }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) rdiag[i] = (T)1 / blk[i][i];
-  __syncthreads();
+  T(*Lo)[NB + 1] = blk;
   // W column j by forward substitution of L w = e_j, four lanes per column splitting each
   // dot product. Every lane runs the same trip count (the shuffles and warp barriers need
   // all 32 lanes); lanes whose column has not started yet contribute zero.
@@ -85,7 +102,7 @@ __global__ void __launch_bounds__(256) potrf_inv_kernel(T* __restrict__ a, int D
     const bool act = col && i > j;
     T part = (T)0;
     if (act)
-      for (int m = j + sub; m < i; m += 4) part += blk[i][m] * inv[m][j];
+      for (int m = j + sub; m < i; m += 4) part += Lo[i][m] * inv[m][j];
     part += __shfl_xor_sync(0xffffffffu, part, 1);
     part += __shfl_xor_sync(0xffffffffu, part, 2);
     if (act && sub == 0) inv[i][j] = -part * rdiag[i];
@@ -94,13 +111,15 @@ __global__ void __launch_bounds__(256) potrf_inv_kernel(T* __restrict__ a, int D
   __syncthreads();
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int i = e / n, c = e % n;
-    a[(size_t)(k0 + i) * D + k0 + c] = (c <= i) ? blk[i][c] : (T)0;
+    a[(size_t)(k0 + i) * D + k0 + c] = (c <= i) ? Lo[i][c] : (T)0;
     W[i * NB + c] = (c <= i) ? inv[i][c] : (T)0;
   }
 }
 
 // Panel below diagonal block k0: X = A W^T with W = L_kk^{-1} (solves X L_kk^T = A),
-// 32 rows per CTA, written in place.
+// kTrsmRows rows per CTA (many small CTAs keep the panel solve short on the critical
+// path of the factorisation), written in place.
+constexpr int kTrsmRows = 8;
 template <typename T>
 __global__ void __launch_bounds__(256) trsm_gemm_kernel(T* __restrict__ a, int D, int k0, const T* __restrict__ W,
                                                         const uint32_t* __restrict__ status) {
@@ -109,31 +128,28 @@ __global__ void __launch_bounds__(256) trsm_gemm_kernel(T* __restrict__ a, int D
   T(*As)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(chol_smem + sizeof(T) * NB * (NB + 1));
   if (*status & ST_NOT_PD) return;
   const int n = min(NB, D - k0);
-  const int r0 = k0 + n + blockIdx.x * 32;
-  const int rows = min(32, D - r0);
+  const int r0 = k0 + n + blockIdx.x * kTrsmRows;
+  const int rows = min(kTrsmRows, D - r0);
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int i = e / NB, c = e % NB;
+    const int i = e >> 6, c = e & 63;
     Ws[i][c] = (i < n && c < n) ? W[i * NB + c] : (T)0;
   }
-  for (int e = threadIdx.x; e < 32 * NB; e += blockDim.x) {
-    const int i = e / NB, c = e % NB;
+  for (int e = threadIdx.x; e < kTrsmRows * NB; e += blockDim.x) {
+    const int i = e >> 6, c = e & 63;
     As[i][c] = (i < rows && c < n) ? a[(size_t)(r0 + i) * D + k0 + c] : (T)0;
   }
   __syncthreads();
-  // thread -> (row = tid / 8, 8 consecutive output columns)
-  const int rr = threadIdx.x >> 3, c0 = (threadIdx.x & 7) * 8;
-  T acc[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) acc[q] = (T)0;
+  // thread -> (row = tid / 32, output columns lane and lane + 32); W[c][m] = 0 for m > c
+  const int rr = threadIdx.x >> 5, c0 = threadIdx.x & 31;
+  T acc0 = (T)0, acc1 = (T)0;
   for (int m = 0; m < n; ++m) {
     const T x = As[rr][m];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = fma(x, Ws[c0 + q][m], acc[q]);  // W[c][m] = 0 for m > c
+    acc0 = fma(x, Ws[c0][m], acc0);
+    acc1 = fma(x, Ws[c0 + 32][m], acc1);
   }
   if (rr < rows) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-      if (c0 + q < n) a[(size_t)(r0 + rr) * D + k0 + c0 + q] = acc[q];
+    if (c0 < n) a[(size_t)(r0 + rr) * D + k0 + c0] = acc0;
+    if (c0 + 32 < n) a[(size_t)(r0 + rr) * D + k0 + c0 + 32] = acc1;
   }
 }
 
@@ -278,7 +294,7 @@ static cudaError_t cholesky_t(T* a, int D, const double* ridge, void* aux, uint3
     if (g > 0) syrk_update_kernel<T><<<g, 256, 0, st>>>(a, D, k0, part, status);
     return cudaGetLastError();
   };
-  const size_t sm_potrf = 2 * sizeof(T) * NB * (NB + 1), sm_trsm = sizeof(T) * (NB + 32) * (NB + 1);
+  const size_t sm_potrf = 2 * sizeof(T) * NB * (NB + 1), sm_trsm = sizeof(T) * (NB + kTrsmRows) * (NB + 1);
   cudaError_t e0 = cudaFuncSetAttribute(potrf_inv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_potrf);
   if (e0 != cudaSuccess) return e0;
   e0 = cudaFuncSetAttribute(trsm_gemm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_trsm);
@@ -288,7 +304,7 @@ static cudaError_t cholesky_t(T* a, int D, const double* ridge, void* aux, uint3
     potrf_inv_kernel<T><<<1, 256, sm_potrf, st>>>(a, D, k0, ridge, W + (size_t)kb * NB * NB, status);
     const int rows = D - k0 - min(NB, D - k0);
     if (rows > 0) {
-      trsm_gemm_kernel<T><<<(rows + 31) / 32, 256, sm_trsm, st>>>(a, D, k0, W + (size_t)kb * NB * NB, status);
+      trsm_gemm_kernel<T><<<(rows + kTrsmRows - 1) / kTrsmRows, 256, sm_trsm, st>>>(a, D, k0, W + (size_t)kb * NB * NB, status);
       if (tcu)  // planes use the stride m_pad of the update kernel's tensor maps; rows >= `rows` get zeros
         digit_split_kernel<<<(m_pad * 32 + 255) / 256, 256, 0, st>>>((const double*)a, D, k0 + NB, k0, rows, m_pad,
                                                                      planes[kb & 1], rexp[kb & 1]);

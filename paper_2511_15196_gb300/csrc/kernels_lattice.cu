@@ -137,13 +137,29 @@ __global__ void __launch_bounds__(PPB* TPP) accept_kernel(T* __restrict__ phi, c
     for (int x = t; x < p.D; x += TPP) phi[(size_t)i * p.D + x] = row[x];
 }
 
+// Metropolis decision log u < log alpha for u in (0, 1] (53-bit), taken exactly as in
+// double precision but mostly without the double log: log u lies in [log 2^-53, 0],
+// so log alpha > 0 accepts and log alpha < -40 rejects; otherwise logf of the
+// float-rounded u is within 1e-5 of log u (float rounding of u and logf's error
+// bound), so only draws inside that margin need the double log.
+PHI4_DEV int accept_decision(double u, double log_alpha) {
+  if (!(log_alpha == log_alpha)) return 0;
+  if (log_alpha > 0.0) return 1;
+  if (log_alpha == 0.0) return u < 1.0;
+  if (log_alpha < -40.0) return 0;
+  const double lf = (double)logf((float)u);
+  if (lf < log_alpha - 2e-5) return 1;
+  if (lf > log_alpha + 2e-5) return 0;
+  return log(u) < log_alpha;
+}
+
 // Float fields with L % 4 == 0: each thread owns float4 groups of four sites of one
 // lattice row (kept in registers), reads the up/down neighbour groups and the two
 // horizontal end neighbours from the staged row, and keeps plain float partial sums
 // over at most a few groups; partials are combined in double with one fused
 // two-value reduction. The proposal is either a float row `prop` or phi + delta with
 // delta an fp16 increment (the tensor-core proposal's epilogue output).
-template <int PPB, int TPP, bool kDelta>
+template <int PPB, int TPP, bool kDelta, int kMaxG>
 __global__ void __launch_bounds__(PPB* TPP) accept_vec_kernel(float* __restrict__ phi, const float* __restrict__ prop,
                                                               const __half* __restrict__ delta, ActionParams p,
                                                               int keep_ref, double* __restrict__ S,
@@ -152,10 +168,10 @@ __global__ void __launch_bounds__(PPB* TPP) accept_vec_kernel(float* __restrict_
                                                               uint32_t w0, uint32_t sweep,
                                                               uint32_t* __restrict__ acc_count,
                                                               uint32_t* __restrict__ status) {
-  constexpr int kMaxG = 8;  // float4 groups per thread (D <= 8 * 4 * TPP)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[PPB][TPP / 32][2];
   __shared__ int accept_flag[PPB];
+  __shared__ double uni[PPB];
   const int g = threadIdx.x / TPP, t = threadIdx.x % TPP;
   const int i = blockIdx.x * PPB + g;
   const int L = p.L, D = p.D, ng = D >> 2;
@@ -180,6 +196,11 @@ __global__ void __launch_bounds__(PPB* TPP) accept_vec_kernel(float* __restrict_
         reinterpret_cast<float4*>(row)[q] = f;
       }
     }
+  }
+  // the accept uniform, drawn by the group's last lane-0 while the others start the stencil
+  if (i < p.N && t == TPP - 32) {
+    const uint4 w = philox4x32_10(make_uint4(w0, sweep, (uint32_t)i, 0u), key);
+    uni[g] = uniform53(w.x, w.y);
   }
   __syncthreads();
   const float ck = (float)p.c_kin, cm = (float)(p.c_mass * p.m2), lm = (float)p.lam;
@@ -225,8 +246,7 @@ __global__ void __launch_bounds__(PPB* TPP) accept_vec_kernel(float* __restrict_
     const double beta = *beta_ptr;
     const double dS = Sp - S[i], dq2 = Qp - sq[i];
     const double log_alpha = keep_ref ? (-beta * dS - 0.5 * dq2) : (-beta * dS - (1.0 - beta) * 0.5 * dq2);
-    const uint4 w = philox4x32_10(make_uint4(w0, sweep, (uint32_t)i, 0u), key);
-    int acc = log(uniform53(w.x, w.y)) < log_alpha;
+    int acc = accept_decision(uni[g], log_alpha);
     if (!isfinite(Sp) || !isfinite(Qp)) {
       atomicOr(status, ST_NONFINITE);
       acc = 0;
@@ -314,24 +334,34 @@ static cudaError_t accept_t(T* phi, const T* prop, const ActionParams& p, int ke
   return cudaGetLastError();
 }
 
+template <int PPB, int TPP, bool kDelta, int G>
+static cudaError_t accept_vec_g(float* phi, const float* prop, const __half* delta, const ActionParams& p, int keep_ref,
+                                double* S, double* sq, double* ell, const double* beta, PhiloxKey key, uint32_t w0,
+                                uint32_t sweep, uint32_t* acc, uint32_t* status, cudaStream_t s) {
+  const size_t sm = (size_t)PPB * p.D * sizeof(float);
+  cudaError_t e = set_smem(accept_vec_kernel<PPB, TPP, kDelta, G>, sm);
+  if (e != cudaSuccess) return e;
+  accept_vec_kernel<PPB, TPP, kDelta, G><<<(p.N + PPB - 1) / PPB, PPB * TPP, sm, s>>>(
+      phi, prop, delta, p, keep_ref, S, sq, ell, beta, key, w0, sweep, acc, status);
+  return cudaGetLastError();
+}
+
 template <bool kDelta>
 static cudaError_t accept_vec(float* phi, const float* prop, const __half* delta, const ActionParams& p, int keep_ref,
                               double* S, double* sq, double* ell, const double* beta, PhiloxKey key, uint32_t w0,
                               uint32_t sweep, uint32_t* acc, uint32_t* status, cudaStream_t s) {
+  // float4 groups per thread: D / 4 / threads-per-particle
   if (p.D >= kBigD) {
-    const size_t sm = (size_t)p.D * sizeof(float);
-    cudaError_t e = set_smem(accept_vec_kernel<1, 256, kDelta>, sm);
-    if (e != cudaSuccess) return e;
-    accept_vec_kernel<1, 256, kDelta><<<p.N, 256, sm, s>>>(phi, prop, delta, p, keep_ref, S, sq, ell, beta, key, w0,
-                                                           sweep, acc, status);
-  } else {
-    const size_t sm = (size_t)8 * p.D * sizeof(float);
-    cudaError_t e = set_smem(accept_vec_kernel<8, 32, kDelta>, sm);
-    if (e != cudaSuccess) return e;
-    accept_vec_kernel<8, 32, kDelta><<<(p.N + 7) / 8, 256, sm, s>>>(phi, prop, delta, p, keep_ref, S, sq, ell, beta,
-                                                                    key, w0, sweep, acc, status);
+    const int g = (p.D / 4 + 255) / 256;
+    if (g <= 1) return accept_vec_g<1, 256, kDelta, 1>(phi, prop, delta, p, keep_ref, S, sq, ell, beta, key, w0, sweep, acc, status, s);
+    if (g <= 2) return accept_vec_g<1, 256, kDelta, 2>(phi, prop, delta, p, keep_ref, S, sq, ell, beta, key, w0, sweep, acc, status, s);
+    if (g <= 4) return accept_vec_g<1, 256, kDelta, 4>(phi, prop, delta, p, keep_ref, S, sq, ell, beta, key, w0, sweep, acc, status, s);
+    return accept_vec_g<1, 256, kDelta, 8>(phi, prop, delta, p, keep_ref, S, sq, ell, beta, key, w0, sweep, acc, status, s);
   }
-  return cudaGetLastError();
+  const int g = (p.D / 4 + 31) / 32;
+  if (g <= 2) return accept_vec_g<8, 32, kDelta, 2>(phi, prop, delta, p, keep_ref, S, sq, ell, beta, key, w0, sweep, acc, status, s);
+  if (g <= 4) return accept_vec_g<8, 32, kDelta, 4>(phi, prop, delta, p, keep_ref, S, sq, ell, beta, key, w0, sweep, acc, status, s);
+  return accept_vec_g<8, 32, kDelta, 8>(phi, prop, delta, p, keep_ref, S, sq, ell, beta, key, w0, sweep, acc, status, s);
 }
 
 static bool vec_ok(const ActionParams& p) { return p.L % 4 == 0 && p.D <= 8 * 4 * 256; }
