@@ -156,8 +156,8 @@ PHI4_DEV int accept_decision(double u, double log_alpha) {
 // Float fields with L % 4 == 0: each thread owns float4 groups of four sites of one
 // lattice row (kept in registers), reads the up/down neighbour groups and the two
 // horizontal end neighbours from the staged row, and keeps plain float partial sums
-// over at most a few groups; partials are combined in double with one fused
-// two-value reduction. The proposal is either a float row `prop` or phi + delta with
+// over at most a few groups; each warp sums its lanes in float (a tree over at most
+// 512 sites) and the warps' sums are combined in double. The proposal is either a float row `prop` or phi + delta with
 // delta an fp16 increment (the tensor-core proposal's epilogue output).
 template <int PPB, int TPP, bool kDelta, int kMaxG>
 __global__ void __launch_bounds__(PPB* TPP) accept_vec_kernel(float* __restrict__ phi, const float* __restrict__ prop,
@@ -229,11 +229,14 @@ __global__ void __launch_bounds__(PPB* TPP) accept_vec_kernel(float* __restrict_
       }
     }
   }
-  double ds = warp_sum((double)s), dq = warp_sum((double)qq);
+  // float warp trees (<= 32 partials of <= 4 groups each); the warps' results are
+  // combined in double. Double shuffles would keep GB300's slow FP64 pipe busy.
+  s = warp_sum(s);
+  qq = warp_sum(qq);
   const int lane = t & 31, wg = t >> 5;
   if (lane == 0) {
-    red[g][wg][0] = ds;
-    red[g][wg][1] = dq;
+    red[g][wg][0] = (double)s;
+    red[g][wg][1] = (double)qq;
   }
   __syncthreads();
   if (i < p.N && t == 0) {

@@ -405,7 +405,9 @@ PHI4_DEV double pow2(int n) {
   return __longlong_as_double((long long)(n + 1023) << 52);
 }
 
-__global__ void __launch_bounds__(tc::NUM_THREADS, 1)
+constexpr int NUM_THREADS = 320;  // TMA warp, MMA warp, two epilogue warpgroups
+
+__global__ void __launch_bounds__(NUM_THREADS, 1)
     chol_update_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Params p) {
   using namespace tc;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -423,7 +425,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
     mbar_init(full, 1);
     mbar_init(empty, 1);
     mbar_init(tfull, 1);
-    mbar_init(tempty, 4);
+    mbar_init(tempty, 8);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
@@ -487,7 +489,8 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
       }
     }
   } else {
-    const int q = warp & 3;
+    // two epilogue warpgroups: warps 2..5 take columns 0..31 of the tile, warps 6..9 columns 32..63
+    const int q = warp & 3, grp = (warp - 2) >> 2;
     const int r = q * 32 + lane;
     uint32_t tphase = 0;
     for (int u = blockIdx.x; u < p.num_tiles; u += gridDim.x) {
@@ -499,8 +502,17 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
       const bool row_ok = ir < p.m;
       const int ei = row_ok ? p.rexp[ir] : 0;
       const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16);
+      double* arow = p.a + (size_t)(p.b0 + (row_ok ? ir : 0)) * p.D + p.b0;
 #pragma unroll 1
-      for (int ch = 0; ch < BN / 16; ++ch) {
+      for (int ch = 2 * grp; ch < 2 * grp + 2; ++ch) {
+        const int jc0 = bj * BN + ch * 16;
+        // prefetch the FP64 targets while the accumulators are combined
+        double av[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          const int jc = jc0 + t;
+          av[t] = (row_ok && jc < p.m && jc <= ir) ? arow[jc] : 0.0;
+        }
         float hi[16], lo[16];
         tmem_ld16(trow + (uint32_t)((NC - 1) * BN + ch * 16), hi);
 #pragma unroll
@@ -523,14 +535,21 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
           }
         }
         if (row_ok) {
-          const int i = p.b0 + ir;
-          double* arow = p.a + (size_t)i * p.D;
 #pragma unroll
           for (int t = 0; t < 16; ++t) {
-            const int jc = bj * BN + ch * 16 + t;
+            const int jc = jc0 + t;
             if (jc < p.m && jc <= ir) {
-              const double v = ((double)hi[t] + (double)lo[t]) * pow2(ei + p.rexp[jc] - 14);
-              arow[p.b0 + jc] -= v;
+              const int n = ei + p.rexp[jc] - 14;
+              double v;
+              // every partial is a multiple of 2^-42 below 2^24, so for n in (-80, 100) the float
+              // products stay normal and the scaling is exact
+              if (n > -80 && n < 100) {
+                const float pw = __int_as_float((n + 127) << 23);
+                v = (double)(hi[t] * pw) + (double)(lo[t] * pw);
+              } else {
+                v = ((double)hi[t] + (double)lo[t]) * pow2(n);
+              }
+              arow[jc] = av[t] - v;
             }
           }
         }
@@ -620,7 +639,7 @@ cudaError_t launch_chol_update_tc(double* a, int D, int b0, int m, const void* p
       cudaFuncSetAttribute(emu::chol_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, emu::SMEM_BYTES);
   if (e != cudaSuccess) return e;
   const int grid = std::min(sm_count(), p.num_tiles);
-  emu::chol_update_kernel<<<grid, tc::NUM_THREADS, emu::SMEM_BYTES, s>>>(ma, mb, p);
+  emu::chol_update_kernel<<<grid, emu::NUM_THREADS, emu::SMEM_BYTES, s>>>(ma, mb, p);
   return cudaGetLastError();
 }
 
