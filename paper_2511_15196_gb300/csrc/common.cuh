@@ -19,6 +19,35 @@ enum : uint32_t {
 // About one second of SM clock: every spin-wait in this library gives up after it.
 constexpr long long kSpinLimitCycles = 2000000000LL;
 
+// CTA-scope mbarrier helpers (shared-memory barrier objects, phase parity waits).
+PHI4_DEV uint32_t cta_smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+PHI4_DEV void cta_mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(cta_smem_addr(bar)), "r"(count) : "memory");
+}
+PHI4_DEV void cta_mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(cta_smem_addr(bar)) : "memory");
+}
+PHI4_DEV bool cta_mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(cta_smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of the given parity; false after kSpinLimitCycles or
+// once another warp has raised *abort_flag.
+PHI4_DEV bool cta_mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  if (cta_mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  for (;;) {
+    if (cta_mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kSpinLimitCycles) return false;
+  }
+}
+
 PHI4_DEV double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -28,91 +28,234 @@ __global__ void copy_lower_kernel(const double* src, T* dst, int D) {
   }
 }
 
-// Factor the diagonal block in one CTA and form its inverse W = L_kk^{-1} (lower),
-// which turns the panel's triangular solve into a dependency-free product.
-// Per column: one thread forms the pivot with a single rsqrt (FP64 square roots and
-// divisions are long sequences on the FP64 pipe, so they are done once per column),
-// the column is scaled by multiplication, then the trailing block gets a rank-1 update.
+// x > 0 and finite (not NaN), from the bit pattern (keeps the test off the FP64 pipe)
+__device__ __forceinline__ bool positive_finite(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 && b < 0x7FF0000000000000LL;
+}
+__device__ __forceinline__ bool positive_finite(float x) {
+  const int b = __float_as_int(x);
+  return b > 0 && b < 0x7F800000;
+}
+
+// Factor the diagonal block A_kk = L_kk L_kk^T (+ ridge) in one CTA, right-looking by
+// columns with one column of look-ahead. On this part an FP64 instruction occupies
+// its SM sub-partition's FP64 unit for 64 cycles whatever its lane mask (rsqrt is
+// about six of them), so the layout is chosen by FP64 instruction count:
+//   warp 0 (alone on its sub-partition) runs the pivot chain: column j receives the
+//     update from column j-1, then rsqrt of its pivot and the scaling; it publishes
+//     L_:j in a ring of four shared vectors;
+//   warps 1-3 and 5-7 (warp 4 idles, sharing warp 0's sub-partition) hold the
+//     trailing elements packed column by column from the last column down, so the
+//     live set (columns >= j+2 at step j) is a prefix and every FP64 instruction has
+//     full lanes; at step j they update column j+2 first, signal, then the rest.
+// Two pairs of mbarriers carry the hand-offs: A[j & 1] (six update warps -> pivot
+// warp: column j+2 is ready) and B[j & 1] (pivot -> update warps: L_:j is published);
+// a barrier's next phase needs every waiter past the current one, so parity waits
+// cannot skip a phase. Waits are bounded (ST_TIMEOUT). rsqrt(pivot_j) goes to `rdiag`
+// for the inverse.
+constexpr int kPotrfThreads = 256;
+constexpr int kUpdWarps = 6;
+constexpr int kUpdThreads = 32 * kUpdWarps;
+constexpr int kUpdSlots = ((NB - 2) * (NB - 1) / 2 + kUpdThreads - 1) / kUpdThreads;  // 11
 template <typename T>
-__global__ void __launch_bounds__(256) potrf_inv_kernel(T* __restrict__ a, int D, int k0,
-                                                        const double* __restrict__ ridge, T* __restrict__ W,
-                                                        uint32_t* __restrict__ status) {
-  extern __shared__ __align__(16) unsigned char chol_smem[];
-  T(*blk)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(chol_smem);
-  T(*inv)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(chol_smem + sizeof(T) * NB * (NB + 1));
-  __shared__ T rdiag[NB];
+__global__ void __launch_bounds__(kPotrfThreads) potrf_kernel(T* __restrict__ a, int D, int k0,
+                                                              const double* __restrict__ ridge,
+                                                              T* __restrict__ rdiag, uint32_t* __restrict__ status) {
+  __shared__ T S[NB][NB + 1];
+  __shared__ T lcol[4][NB];
+  __shared__ T rds[NB];
+  // update element e = slot * kUpdThreads + t of update thread t, packed (row << 8) | column:
+  // columns from n-1 down to 2, rows >= column (column c = n-1-r for the triangular
+  // root r of e, row = c + e - r(r+1)/2), so the live set of every step is a prefix
+  __shared__ uint32_t eidx[kUpdSlots][kUpdThreads];
+  __shared__ __align__(8) uint64_t barA[2], barB[2];
   __shared__ int fail;
+  __shared__ volatile int abort_flag;
   if (*status & ST_NOT_PD) return;
   const int n = min(NB, D - k0);
   const T r = ridge ? (T)*ridge : (T)0;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const int i = e / n, j = e % n;
-    T v = (j <= i) ? a[(size_t)(k0 + i) * D + k0 + j] : (T)0;
-    if (i == j) v += r;
-    blk[i][j] = v;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int e = tid; e < n * n; e += kPotrfThreads) {
+    const int i = e / n, c = e - (e / n) * n;
+    if (c <= i) S[i][c] = a[(size_t)(k0 + i) * D + k0 + c] + (c == i ? r : (T)0);
   }
-  if (threadIdx.x == 0) fail = 0;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  __syncthreads();
-  for (int j = 0; j < n; ++j) {
-    if (threadIdx.x == 0) {
-      const T d = blk[j][j];
-      if (!(d > (T)0) || !isfinite(d)) {
-        fail = 1;
-      } else {
-        const T ip = rsqrt(d);
-        rdiag[j] = ip;
-        blk[j][j] = d * ip;
-      }
+  const int Eb = (n - 2) * (n - 1) / 2;
+  for (int e = tid; e < kUpdSlots * kUpdThreads; e += kPotrfThreads) {
+    uint32_t v = 0;
+    if (e < Eb) {
+      int t = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+      while (t * (t + 1) / 2 > e) --t;
+      while ((t + 1) * (t + 2) / 2 <= e) ++t;
+      const int c = n - 1 - t;
+      v = ((uint32_t)(c + e - t * (t + 1) / 2) << 8) | (uint32_t)c;
     }
-    __syncthreads();
-    if (fail) break;
-    const T ip = rdiag[j];
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) blk[i][j] *= ip;
-    __syncthreads();
-    // rank-1 update of the trailing block: thread (ty, tx) of a 16 x 16 layout owns
-    // rows ty + 16a and columns tx + 16b
-#pragma unroll
-    for (int a4 = 0; a4 < 4; ++a4) {
-      const int i = ty + 16 * a4;
-      if (i > j && i < n) {
-        const T lij = blk[i][j];
-#pragma unroll
-        for (int b4 = 0; b4 < 4; ++b4) {
-          const int l = tx + 16 * b4;
-          if (l > j && l <= i) blk[i][l] -= lij * blk[l][j];
+    eidx[e / kUpdThreads][e % kUpdThreads] = v;
+  }
+  if (tid == 0) {
+    fail = 0;
+    abort_flag = 0;
+    for (int q = 0; q < 2; ++q) {
+      cta_mbar_init(&barA[q], kUpdWarps);
+      cta_mbar_init(&barB[q], 1);
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    bool ok = true;
+    const int i0 = lane, i1 = lane + 32;
+    for (int j = 0; j < n; ++j) {
+      // column j has the updates of columns <= j-2
+      if (j >= 2 && !cta_mbar_wait(&barA[j & 1], ((j - 2) >> 1) & 1, &abort_flag)) {
+        abort_flag = 1;
+        break;
+      }
+      const T* lp = lcol[(j - 1) & 3];
+      const T lj = j >= 1 ? lp[j] : (T)0;
+      // the pivot, in every lane: the rsqrt chain starts without a shuffle
+      const T d = fma(-lj, lj, S[j][j]);
+      const bool good = positive_finite(d);
+      ok = ok && good;
+      const T rd = good ? rsqrt(d) : (T)0;
+      T* lo = lcol[j & 3];
+      if (j < 32 && i0 >= j) {
+        const T l0 = (i0 == j ? d : fma(-lp[i0], lj, S[i0][j])) * rd;
+        lo[i0] = l0;
+        S[i0][j] = l0;
+      }
+      if (i1 >= j && i1 < n) {
+        const T l1 = (i1 == j ? d : fma(-lp[i1], lj, S[i1][j])) * rd;
+        lo[i1] = l1;
+        S[i1][j] = l1;
+      }
+      if (lane == 0) rds[j] = rd;
+      __syncwarp();
+      if (j + 2 < n && lane == 0) cta_mbar_arrive(&barB[j & 1]);
+    }
+    if (!ok && lane == 0) fail = 1;
+  } else if (warp != 4) {
+    const int bt = (warp < 4 ? warp - 1 : warp - 2) * 32 + lane;
+    const int wbase = bt - lane;
+    // The passes loop over live slots only, with warp-uniform bounds: a predicated-off
+    // FP64 instruction would still hold the FP64 unit for its full 64 cycles.
+    for (int k = 0; k + 2 < n; ++k) {
+      if (!cta_mbar_wait(&barB[k & 1], (k >> 1) & 1, &abort_flag)) {  // L_:k is published
+        abort_flag = 1;
+        break;
+      }
+      const T* lp = lcol[k & 3];
+      const int live = (n - k - 2) * (n - k - 1) / 2;  // elements of columns >= k+2
+      const int rest = (n - k - 3) * (n - k - 2) / 2;  // elements of columns >= k+3
+      // column k+2 (elements rest .. live-1) first
+#pragma unroll 1
+      const int first = rest - wbase - 31;  // first slot whose warp range reaches e >= rest
+      for (int sl = first > 0 ? (first + kUpdThreads - 1) / kUpdThreads : 0; sl * kUpdThreads + wbase < live; ++sl) {
+        const int e = sl * kUpdThreads + bt;
+        if (e >= rest && e < live) {
+          const uint32_t v = eidx[sl][bt];
+          const int i = (int)(v >> 8), c = (int)(v & 255u);
+          S[i][c] = fma(-lp[i], lp[c], S[i][c]);
         }
       }
+      __syncwarp();
+      if (lane == 0) cta_mbar_arrive(&barA[k & 1]);
+      // slots whose warp range starts below `rest`; all but the last are fully live.
+      // Pairs: both loads, then both FMAs, then both stores (independent chains).
+      const int nsl = rest > wbase ? (rest - wbase + kUpdThreads - 1) / kUpdThreads : 0;
+      int sl = 0;
+#pragma unroll 1
+      for (; sl + 1 < nsl; sl += 2) {
+        const uint32_t v0 = eidx[sl][bt], v1 = eidx[sl + 1][bt];
+        const int i0 = (int)(v0 >> 8), c0 = (int)(v0 & 255u), i1 = (int)(v1 >> 8), c1 = (int)(v1 & 255u);
+        const bool on1 = (sl + 1) * kUpdThreads + bt < rest;
+        const T s0 = S[i0][c0], s1 = S[i1][c1];
+        const T x0 = fma(-lp[i0], lp[c0], s0), x1 = fma(-lp[i1], lp[c1], s1);
+        S[i0][c0] = x0;
+        if (on1) S[i1][c1] = x1;
+      }
+      if (sl < nsl && sl * kUpdThreads + bt < rest) {
+        const uint32_t v = eidx[sl][bt];
+        const int i = (int)(v >> 8), c = (int)(v & 255u);
+        S[i][c] = fma(-lp[i], lp[c], S[i][c]);
+      }
     }
-    __syncthreads();
-  }
-  if (fail) {
-    if (threadIdx.x == 0) atomicOr(status, ST_NOT_PD);
-    return;
-  }
-  T(*Lo)[NB + 1] = blk;
-  // W column j by forward substitution of L w = e_j, four lanes per column splitting each
-  // dot product. Every lane runs the same trip count (the shuffles and warp barriers need
-  // all 32 lanes); lanes whose column has not started yet contribute zero.
-  const int j = threadIdx.x >> 2, sub = threadIdx.x & 3;
-  const bool col = j < n;
-  if (col && sub == 0) inv[j][j] = rdiag[j];
-  __syncwarp();
-  for (int i = 1; i < n; ++i) {
-    const bool act = col && i > j;
-    T part = (T)0;
-    if (act)
-      for (int m = j + sub; m < i; m += 4) part += Lo[i][m] * inv[m][j];
-    part += __shfl_xor_sync(0xffffffffu, part, 1);
-    part += __shfl_xor_sync(0xffffffffu, part, 2);
-    if (act && sub == 0) inv[i][j] = -part * rdiag[i];
-    __syncwarp();
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const int i = e / n, c = e % n;
-    a[(size_t)(k0 + i) * D + k0 + c] = (c <= i) ? Lo[i][c] : (T)0;
-    W[i * NB + c] = (c <= i) ? inv[i][c] : (T)0;
+  if (abort_flag) {
+    if (tid == 0) atomicOr(status, ST_TIMEOUT);
+    return;
+  }
+  if (fail) {
+    if (tid == 0) atomicOr(status, ST_NOT_PD);
+    return;
+  }
+  for (int e = tid; e < n * n; e += kPotrfThreads) {
+    const int i = e / n, c = e - (e / n) * n;
+    a[(size_t)(k0 + i) * D + k0 + c] = (c <= i) ? S[i][c] : (T)0;
+  }
+  if (tid < n) rdiag[tid] = rds[tid];
+}
+
+// W = L_kk^{-1} (lower) for the panel solve: column c of W per CTA, by right-looking
+// forward substitution of L w = e_c in warp 0 with rows lane and lane + 32 in
+// registers; w_m = (accumulated value) * rdiag_m, then rows below subtract L_im w_m.
+// All four warps stage the needed part of L in shared memory first (independent
+// loads, so their latencies overlap). One CTA per column spreads the FP64 work over
+// many SMs.
+constexpr int kInvThreads = 128;
+template <typename T>
+__global__ void __launch_bounds__(kInvThreads) tri_inv_kernel(const T* __restrict__ a, int D, int k0,
+                                                              const T* __restrict__ rdiag, T* __restrict__ W,
+                                                              const uint32_t* __restrict__ status) {
+  __shared__ T Ls[NB][NB + 1];
+  __shared__ T rds[NB];
+  if (*status & ST_NOT_PD) return;
+  const int n = min(NB, D - k0);
+  const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
+  if (c >= n) return;
+  // the part of L this column needs: rows i > c, columns c <= m < i
+#pragma unroll 4
+  for (int e = tid; e < NB * NB; e += kInvThreads) {
+    const int i = e >> 6, m = e & 63;
+    if (i < n && m >= c && m < i) Ls[i][m] = a[(size_t)(k0 + i) * D + k0 + m];
+  }
+  if (tid < n) rds[tid] = rdiag[tid];
+  for (int i = tid; i < c; i += kInvThreads) W[i * NB + c] = (T)0;
+  __syncthreads();
+  if (tid >= 32) return;
+  const int i0 = lane, i1 = lane + 32;
+  T acc0 = (i0 == c) ? (T)1 : (T)0, acc1 = (i1 == c) ? (T)1 : (T)0;
+  for (int m = c; m < n; ++m) {
+    const T w = __shfl_sync(0xffffffffu, m < 32 ? acc0 : acc1, m & 31) * rds[m];
+    if (lane == (m & 31)) W[m * NB + c] = w;
+    if (m < 31) acc0 = fma(-Ls[i0][m], w, acc0);
+    acc1 = fma(-Ls[i1][m], w, acc1);
+  }
+}
+
+// Exact digit split of one panel row for the tensor-core trailing update. The warp
+// holds the row's 64 values (x0 in column lane, x1 in column lane + 32). The row gets
+// the exponent e = ilogb(max |x|) + 1 (so |x| < 2^e) and every element the integer
+// N = floor(|x| 2^(56 - e)) < 2^56, cut into eight base-128 digits
+// d_k = (N >> (56 - 7k)) & 127 carrying x's sign: x = sum_k d_k 2^(e - 7k) up to
+// 2^(e - 56). The digits are integers below 128 in magnitude, exact in bf16; plane k
+// (0..7) holds rows [k m_pad, (k+1) m_pad) of a [8 m_pad][64] array.
+__device__ __forceinline__ void split_row_digits(double x0, double x1, int row, int m_pad,
+                                                 __nv_bfloat16* __restrict__ planes, int* __restrict__ rexp) {
+  const int lane = threadIdx.x & 31;
+  const double amax = warp_max(fmax(fabs(x0), fabs(x1)));
+  const int e = amax > 0.0 ? ilogb(amax) + 1 : 0;
+  if (lane == 0) rexp[row] = e;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const double x = h ? x1 : x0;
+    const unsigned long long N = (unsigned long long)ldexp(fabs(x), 56 - e);
+    const bool neg = x < 0.0;
+#pragma unroll
+    for (int k = 1; k <= 8; ++k) {
+      const int d = (int)((N >> (56 - 7 * k)) & 127ull);
+      planes[((size_t)(k - 1) * m_pad + row) * 64 + lane + 32 * h] = __float2bfloat16_rn((float)(neg ? -d : d));
+    }
   }
 }
 
@@ -122,7 +265,9 @@ __global__ void __launch_bounds__(256) potrf_inv_kernel(T* __restrict__ a, int D
 constexpr int kTrsmRows = 8;
 template <typename T>
 __global__ void __launch_bounds__(256) trsm_gemm_kernel(T* __restrict__ a, int D, int k0, const T* __restrict__ W,
-                                                        const uint32_t* __restrict__ status) {
+                                                        const uint32_t* __restrict__ status,
+                                                        __nv_bfloat16* __restrict__ planes, int* __restrict__ rexp,
+                                                        int m_pad) {
   extern __shared__ __align__(16) unsigned char chol_smem[];
   T(*Ws)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(chol_smem);
   T(*As)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(chol_smem + sizeof(T) * NB * (NB + 1));
@@ -141,15 +286,24 @@ __global__ void __launch_bounds__(256) trsm_gemm_kernel(T* __restrict__ a, int D
   __syncthreads();
   // thread -> (row = tid / 32, output columns lane and lane + 32); W[c][m] = 0 for m > c
   const int rr = threadIdx.x >> 5, c0 = threadIdx.x & 31;
+  // W is lower triangular: column c0 < 32 only needs m < 32
   T acc0 = (T)0, acc1 = (T)0;
-  for (int m = 0; m < n; ++m) {
+#pragma unroll 8
+  for (int m = 0; m < 32; ++m) {
     const T x = As[rr][m];
     acc0 = fma(x, Ws[c0][m], acc0);
     acc1 = fma(x, Ws[c0 + 32][m], acc1);
   }
+#pragma unroll 8
+  for (int m = 32; m < NB; ++m) acc1 = fma(As[rr][m], Ws[c0 + 32][m], acc1);
   if (rr < rows) {
     if (c0 < n) a[(size_t)(r0 + rr) * D + k0 + c0] = acc0;
     if (c0 + 32 < n) a[(size_t)(r0 + rr) * D + k0 + c0 + 32] = acc1;
+  }
+  if constexpr (sizeof(T) == 8) {
+    // the warp holds one whole panel row: split it into the digit planes of the
+    // tensor-core trailing update (rows past the panel get zero digits)
+    if (planes != nullptr) split_row_digits(acc0, acc1, blockIdx.x * kTrsmRows + rr, m_pad, planes, rexp);
   }
 }
 
@@ -218,39 +372,6 @@ __global__ void __launch_bounds__(256) syrk_update_kernel(T* __restrict__ a, int
   }
 }
 
-// Exact digit splitting of a Cholesky panel for the tensor-core trailing update.
-// Row i of the panel (64 doubles below the diagonal block) gets the exponent
-// e_i = ilogb(max |x|) + 1 (so |x| < 2^e_i) and every element the integer
-// N = floor(|x| 2^(56 - e_i)) < 2^56, cut into eight base-128 digits
-// d_k = (N >> (56 - 7k)) & 127 carrying x's sign: x = sum_k d_k 2^(e_i - 7k) up to
-// 2^(e_i - 56). Digits are integers below 128 in magnitude, exact in bf16.
-// Planes: plane k (0..7) holds rows [k m_pad, (k+1) m_pad) of a [8 m_pad][64] array.
-__global__ void digit_split_kernel(const double* __restrict__ a, int D, int row0, int col0, int m, int m_pad,
-                                   __nv_bfloat16* __restrict__ planes, int* __restrict__ rexp) {
-  const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-  if (row >= m_pad) return;
-  double x0 = 0.0, x1 = 0.0;
-  if (row < m) {
-    const double* src = a + (size_t)(row0 + row) * D + col0;
-    x0 = src[lane];
-    x1 = src[lane + 32];
-  }
-  const double amax = warp_max(fmax(fabs(x0), fabs(x1)));
-  const int e = amax > 0.0 ? ilogb(amax) + 1 : 0;
-  if (lane == 0) rexp[row] = e;
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const double x = h ? x1 : x0;
-    const unsigned long long N = (unsigned long long)ldexp(fabs(x), 56 - e);
-    const bool neg = x < 0.0;
-#pragma unroll
-    for (int k = 1; k <= 8; ++k) {
-      const int d = (int)((N >> (56 - 7 * k)) & 127ull);
-      planes[((size_t)(k - 1) * m_pad + row) * 64 + lane + 32 * h] = __float2bfloat16_rn((float)(neg ? -d : d));
-    }
-  }
-}
-
 template <typename Ti, typename To>
 __global__ void convert_factor_kernel(const Ti* __restrict__ Lc, int D, To* __restrict__ out, int ld) {
   const long long total = (long long)D * ld;
@@ -278,8 +399,9 @@ static cudaError_t cholesky_t(T* a, int D, const double* ridge, void* aux, uint3
   const int nblk = (D + NB - 1) / NB;
   const bool ahead = side != nullptr && nblk > 2;
   T* W = (T*)aux;
+  T* rdiag = (T*)((unsigned char*)aux + round256((size_t)nblk * NB * NB * sizeof(double)));
   const int m_pad = mpad_of(D);
-  unsigned char* dig0 = (unsigned char*)aux + round256((size_t)nblk * NB * NB * sizeof(double));
+  unsigned char* dig0 = (unsigned char*)rdiag + round256((size_t)nblk * NB * sizeof(double));
   __nv_bfloat16* planes[2] = {(__nv_bfloat16*)dig0, (__nv_bfloat16*)(dig0 + round256(8 * (size_t)m_pad * 64 * 2))};
   int* rexp0 = (int*)(dig0 + 2 * round256(8 * (size_t)m_pad * 64 * 2));
   int* rexp[2] = {rexp0, (int*)((unsigned char*)rexp0 + round256((size_t)m_pad * sizeof(int)))};
@@ -294,20 +416,22 @@ static cudaError_t cholesky_t(T* a, int D, const double* ridge, void* aux, uint3
     if (g > 0) syrk_update_kernel<T><<<g, 256, 0, st>>>(a, D, k0, part, status);
     return cudaGetLastError();
   };
-  const size_t sm_potrf = 2 * sizeof(T) * NB * (NB + 1), sm_trsm = sizeof(T) * (NB + kTrsmRows) * (NB + 1);
-  cudaError_t e0 = cudaFuncSetAttribute(potrf_inv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_potrf);
-  if (e0 != cudaSuccess) return e0;
-  e0 = cudaFuncSetAttribute(trsm_gemm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_trsm);
+  const size_t sm_trsm = sizeof(T) * (NB + kTrsmRows) * (NB + 1);
+  cudaError_t e0 = cudaFuncSetAttribute(trsm_gemm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_trsm);
   if (e0 != cudaSuccess) return e0;
   auto panel = [&](int kb, cudaStream_t st) {
     const int k0 = kb * NB;
-    potrf_inv_kernel<T><<<1, 256, sm_potrf, st>>>(a, D, k0, ridge, W + (size_t)kb * NB * NB, status);
+    potrf_kernel<T><<<1, kPotrfThreads, 0, st>>>(a, D, k0, ridge, rdiag + (size_t)kb * NB, status);
     const int rows = D - k0 - min(NB, D - k0);
     if (rows > 0) {
-      trsm_gemm_kernel<T><<<(rows + kTrsmRows - 1) / kTrsmRows, 256, sm_trsm, st>>>(a, D, k0, W + (size_t)kb * NB * NB, status);
-      if (tcu)  // planes use the stride m_pad of the update kernel's tensor maps; rows >= `rows` get zeros
-        digit_split_kernel<<<(m_pad * 32 + 255) / 256, 256, 0, st>>>((const double*)a, D, k0 + NB, k0, rows, m_pad,
-                                                                     planes[kb & 1], rexp[kb & 1]);
+      // the inverse only feeds the panel solve
+      tri_inv_kernel<T><<<min(NB, D - k0), kInvThreads, 0, st>>>(a, D, k0, rdiag + (size_t)kb * NB, W + (size_t)kb * NB * NB,
+                                                        status);
+      // with the tensor-core update the solve also writes the digit planes, for every
+      // row of the update's 128-row tiles (rows >= `rows` get zeros)
+      const int grid_rows = tcu ? (rows + 127) / 128 * 128 : rows;
+      trsm_gemm_kernel<T><<<(grid_rows + kTrsmRows - 1) / kTrsmRows, 256, sm_trsm, st>>>(
+          a, D, k0, W + (size_t)kb * NB * NB, status, tcu ? planes[kb & 1] : nullptr, rexp[kb & 1], m_pad);
     }
   };
   panel(0, s);
@@ -336,7 +460,8 @@ static cudaError_t cholesky_t(T* a, int D, const double* ridge, void* aux, uint3
 size_t cholesky_aux_bytes(int D) {
   const size_t nblk = (size_t)(D + NB - 1) / NB;
   const size_t mp = (size_t)mpad_of(D);
-  return round256(nblk * NB * NB * sizeof(double)) + 2 * round256(8 * mp * 64 * 2) + 2 * round256(mp * sizeof(int));
+  return round256(nblk * NB * NB * sizeof(double)) + round256(nblk * NB * sizeof(double)) +
+         2 * round256(8 * mp * 64 * 2) + 2 * round256(mp * sizeof(int));
 }
 
 // Which trailing update the double factorisation uses (mode 0 = automatic).
@@ -359,7 +484,7 @@ cudaError_t launch_cholesky_f32(const double* sigma, float* a, int D, const doub
 
 int cholesky_launches(int D) {
   const int nblk = (D + NB - 1) / NB;
-  return nblk + 2 * (nblk - 1) + (nblk - 1);
+  return nblk + 4 * (nblk - 1);  // diagonal blocks; per panel: inverse, solve, two update parts
 }
 
 cudaError_t launch_factor_convert(const double* Lc, int D, int dtype, void* out, int ld, cudaStream_t s) {

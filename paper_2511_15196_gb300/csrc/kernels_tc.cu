@@ -15,6 +15,7 @@
 #include <cuda.h>
 #include <cuda_fp16.h>
 #include <algorithm>
+#include <cstdlib>
 #include "internal.h"
 #include "common.cuh"
 
@@ -346,7 +347,7 @@ static cudaError_t launch(const CUtensorMap& a, const CUtensorMap& b, const Para
 // ---------------------------------------------------------------------------
 // FP64 Cholesky trailing update on the tensor cores (exact digit emulation).
 // A22 -= P P^T with P the 64-wide panel below the diagonal block, given as eight
-// bf16 digit planes d_k (|d| < 128, exact) and row exponents e (see digit_split_kernel):
+// bf16 digit planes d_k (|d| < 128, exact) and row exponents e (written by the panel solve, split_row_digits):
 //   (P P^T)_ij = 2^(e_i + e_j) sum_{k,l} 2^(-7(k+l)) T_kl,  T_kl = sum_n d_ik,n d_jl,n.
 // Products are exact in fp32 and, grouped by c = k + l, each group sum is an integer
 // below 2^23 in magnitude (at most 8 pairs x 64 terms x 2^14), so tcgen05 accumulates
@@ -354,14 +355,17 @@ static cudaError_t launch(const CUtensorMap& a, const CUtensorMap& b, const Para
 // groups weigh < 2^-47 of sum |x||y|, like the rounding of a length-64 FP64 dot
 // product); U_9 .. U_2 are combined by a Horner pass in double-float (two fp32)
 // and the result, scaled by 2^(e_i + e_j - 14), is subtracted in FP64.
-// Tiles of 128 rows x 64 columns of the lower trailing matrix; part 1 = the next
-// block column only, part 2 = the rest, part 0 = all.
+// Tiles of 128 rows x 32 columns of the lower trailing matrix (two tiles' group
+// accumulators fit in TMEM, so the MMAs of one tile overlap the epilogue of the
+// previous one); part 1 = the next block column only, part 2 = the rest, part 0 = all.
 namespace emu {
-constexpr int BM = 128, BN = 64, KD = 64, ND = 8, NC = 8;
+constexpr int BM = 128, BN = 32, KD = 64, ND = 8, NC = 8;
 constexpr int A_PLANE = BM * KD * 2;
 constexpr int B_PLANE = BN * KD * 2;
-constexpr int SMEM_DATA = ND * (A_PLANE + B_PLANE);
+constexpr int SMEM_DATA = ND * (A_PLANE + B_PLANE);  // 160 KB: leaves room on the SM for the panel kernels
 constexpr int SMEM_BYTES = SMEM_DATA + 1024 + 256;
+constexpr int ACC_COLS = NC * BN;  // one tile's eight group accumulators; two tiles fit in TMEM
+constexpr int P1_COLS = KD / BN;   // tile columns of the next block column (part 1)
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
 
@@ -382,13 +386,16 @@ PHI4_DEV void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Tile u of the part's list: part 1 walks the next block column (P1_COLS tile
+// columns of every 128-row band), parts 0 and 2 the lower tiles band by band.
 PHI4_DEV void get_tile(const Params& p, int u, int& mb, int& bj) {
+  const int p1 = min(P1_COLS, p.tiles_n);
   if (p.part == 1) {
-    mb = u;
-    bj = 0;
+    mb = u / p1;
+    bj = u - mb * p1;
     return;
   }
-  const int first = p.part == 2 ? 1 : 0;
+  const int first = p.part == 2 ? p1 : 0;
   int m = 0, base = 0;
   for (;;) {
     const int cnt = max(0, min(p.tiles_n, (m * BM + BM - 1) / BN + 1) - first);
@@ -405,6 +412,17 @@ PHI4_DEV double pow2(int n) {
   return __longlong_as_double((long long)(n + 1023) << 52);
 }
 
+// x 2^n as a double, built with integer operations (exact): x is zero or a normal
+// float and the result a normal double. Keeps the conversions off the FP64 pipe.
+PHI4_DEV double f2d_pow2(float x, int n) {
+  const uint32_t b = __float_as_uint(x);
+  if ((b << 1) == 0u) return 0.0;
+  const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+  const unsigned long long ex = (unsigned long long)(((int)(b >> 23) & 0xff) + (1023 - 127) + n) << 52;
+  const unsigned long long man = (unsigned long long)(b & 0x7fffffu) << 29;
+  return __longlong_as_double((long long)(sign | ex | man));
+}
+
 constexpr int NUM_THREADS = 320;  // TMA warp, MMA warp, two epilogue warpgroups
 
 __global__ void __launch_bounds__(NUM_THREADS, 1)
@@ -416,16 +434,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   uint8_t* sB = smem + ND * A_PLANE;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + SMEM_DATA);
   uint64_t* empty = full + 1;
-  uint64_t* tfull = full + 2;
-  uint64_t* tempty = full + 3;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(full + 4);
+  uint64_t* tfull = full + 2;   // [2]
+  uint64_t* tempty = full + 4;  // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(full + 6);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     mbar_init(full, 1);
     mbar_init(empty, 1);
-    mbar_init(tfull, 1);
-    mbar_init(tempty, 8);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull + b, 1);
+      mbar_init(tempty + b, 8);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
@@ -462,15 +482,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      uint32_t phase = 0, tphase = 0;
-      for (int u = blockIdx.x; u < p.num_tiles && !*abort_flag; u += gridDim.x) {
-        if (!mbar_wait(tempty, tphase ^ 1u, abort_flag)) { give_up(); break; }
+      uint32_t phase = 0, tph = 0;  // tph bit b: phase parity of accumulator set b
+      int it = 0;
+      for (int u = blockIdx.x; u < p.num_tiles && !*abort_flag; u += gridDim.x, ++it) {
+        const int buf = it & 1;
+        // the epilogue must have drained this accumulator set (two tiles back)
+        if (!mbar_wait(tempty + buf, ((tph >> buf) & 1u) ^ 1u, abort_flag)) { give_up(); break; }
         tc_fence_after();
         if (!mbar_wait(full, phase, abort_flag)) { give_up(); break; }
         tc_fence_after();
         const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
         for (int c = 2; c <= NC + 1; ++c) {
-          const uint32_t acc = tmem_base + (uint32_t)((c - 2) * BN);
+          const uint32_t acc = tmem_base + (uint32_t)(buf * ACC_COLS + (c - 2) * BN);
           uint32_t accumulate = 0;
           for (int k = max(1, c - ND); k <= min(ND, c - 1); ++k) {
             const int l = c - k;
@@ -483,81 +506,79 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           }
         }
         umma_commit(empty);
-        umma_commit(tfull);
+        umma_commit(tfull + buf);
         phase ^= 1u;
-        tphase ^= 1u;
+        tph ^= 1u << buf;
       }
     }
   } else {
-    // two epilogue warpgroups: warps 2..5 take columns 0..31 of the tile, warps 6..9 columns 32..63
+    // two epilogue warpgroups: warps 2..5 take columns 0..15 of the tile, warps 6..9 columns 16..31
     const int q = warp & 3, grp = (warp - 2) >> 2;
     const int r = q * 32 + lane;
-    uint32_t tphase = 0;
-    for (int u = blockIdx.x; u < p.num_tiles; u += gridDim.x) {
+    uint32_t tph = 0;
+    int it = 0;
+    for (int u = blockIdx.x; u < p.num_tiles; u += gridDim.x, ++it) {
+      const int buf = it & 1;
       int mb, bj;
       get_tile(p, u, mb, bj);
-      if (!mbar_wait(tfull, tphase, abort_flag)) { give_up(); break; }
+      if (!mbar_wait(tfull + buf, (tph >> buf) & 1u, abort_flag)) { give_up(); break; }
       tc_fence_after();
       const int ir = mb * BM + r;  // row inside the trailing matrix
       const bool row_ok = ir < p.m;
       const int ei = row_ok ? p.rexp[ir] : 0;
-      const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16);
+      const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * ACC_COLS + grp * 16);
       double* arow = p.a + (size_t)(p.b0 + (row_ok ? ir : 0)) * p.D + p.b0;
+      const int jc0 = bj * BN + grp * 16;
+      // prefetch the FP64 targets while the accumulators are combined
+      double av[16];
+#pragma unroll
+      for (int t = 0; t < 16; ++t) {
+        const int jc = jc0 + t;
+        av[t] = (row_ok && jc < p.m && jc <= ir) ? arow[jc] : 0.0;
+      }
+      float hi[16], lo[16];
+      tmem_ld16(trow + (uint32_t)((NC - 1) * BN), hi);
+#pragma unroll
+      for (int t = 0; t < 16; ++t) lo[t] = 0.f;
 #pragma unroll 1
-      for (int ch = 2 * grp; ch < 2 * grp + 2; ++ch) {
-        const int jc0 = bj * BN + ch * 16;
-        // prefetch the FP64 targets while the accumulators are combined
-        double av[16];
+      for (int c = NC; c >= 2; --c) {
+        float uu[16];
+        tmem_ld16(trow + (uint32_t)((c - 2) * BN), uu);
 #pragma unroll
         for (int t = 0; t < 16; ++t) {
-          const int jc = jc0 + t;
-          av[t] = (row_ok && jc < p.m && jc <= ir) ? arow[jc] : 0.0;
-        }
-        float hi[16], lo[16];
-        tmem_ld16(trow + (uint32_t)((NC - 1) * BN + ch * 16), hi);
-#pragma unroll
-        for (int t = 0; t < 16; ++t) lo[t] = 0.f;
-#pragma unroll 1
-        for (int c = NC; c >= 2; --c) {
-          float uu[16];
-          tmem_ld16(trow + (uint32_t)((c - 2) * BN + ch * 16), uu);
-#pragma unroll
-          for (int t = 0; t < 16; ++t) {
-            // (hi, lo) <- (hi, lo) 2^-7 + U_c  in double-float (TwoSum, then renormalise)
-            const float h = hi[t] * 0.0078125f, l = lo[t] * 0.0078125f;
-            const float s = h + uu[t];
-            const float bb = s - h;
-            const float err = (h - (s - bb)) + (uu[t] - bb);
-            const float l2 = l + err;
-            const float hs = s + l2;
-            lo[t] = l2 - (hs - s);
-            hi[t] = hs;
-          }
-        }
-        if (row_ok) {
-#pragma unroll
-          for (int t = 0; t < 16; ++t) {
-            const int jc = jc0 + t;
-            if (jc < p.m && jc <= ir) {
-              const int n = ei + p.rexp[jc] - 14;
-              double v;
-              // every partial is a multiple of 2^-42 below 2^24, so for n in (-80, 100) the float
-              // products stay normal and the scaling is exact
-              if (n > -80 && n < 100) {
-                const float pw = __int_as_float((n + 127) << 23);
-                v = (double)(hi[t] * pw) + (double)(lo[t] * pw);
-              } else {
-                v = ((double)hi[t] + (double)lo[t]) * pow2(n);
-              }
-              arow[jc] = av[t] - v;
-            }
-          }
+          // (hi, lo) <- (hi, lo) 2^-7 + U_c  in double-float (TwoSum, then renormalise)
+          const float h = hi[t] * 0.0078125f, l = lo[t] * 0.0078125f;
+          const float s = h + uu[t];
+          const float bb = s - h;
+          const float err = (h - (s - bb)) + (uu[t] - bb);
+          const float l2 = l + err;
+          const float hs = s + l2;
+          lo[t] = l2 - (hs - s);
+          hi[t] = hs;
         }
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(tempty);
-      tphase ^= 1u;
+      if (lane == 0) mbar_arrive(tempty + buf);  // the accumulators are in registers now
+      tph ^= 1u << buf;
+      if (row_ok) {
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          const int jc = jc0 + t;
+          if (jc < p.m && jc <= ir) {
+            const int n = ei + p.rexp[jc] - 14;
+            double v;
+            // every partial is a multiple of 2^-42 below 2^24: for |n| < 900 both
+            // halves scale to normal doubles exactly
+            if (n > -900 && n < 900) {
+              v = f2d_pow2(hi[t], n) + f2d_pow2(lo[t], n);
+            } else {
+              v = ((double)hi[t] + (double)lo[t]) * pow2(n);
+            }
+            arow[jc] = av[t] - v;
+          }
+        }
+      }
     }
   }
   tc_fence_before();
@@ -626,19 +647,28 @@ cudaError_t launch_chol_update_tc(double* a, int D, int b0, int m, const void* p
   p.part = part;
   p.rexp = rexp;
   p.status = status;
+  const int p1 = std::min(emu::P1_COLS, p.tiles_n);
   if (part == 1) {
-    p.num_tiles = p.tiles_m;
+    p.num_tiles = p.tiles_m * p1;
   } else {
     int count = 0;
     for (int mm = 0; mm < p.tiles_m; ++mm)
-      count += std::max(0, std::min(p.tiles_n, (mm * emu::BM + emu::BM - 1) / emu::BN + 1) - (part == 2 ? 1 : 0));
+      count += std::max(0, std::min(p.tiles_n, (mm * emu::BM + emu::BM - 1) / emu::BN + 1) - (part == 2 ? p1 : 0));
     p.num_tiles = count;
   }
   if (p.num_tiles == 0) return cudaSuccess;
   cudaError_t e =
       cudaFuncSetAttribute(emu::chol_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, emu::SMEM_BYTES);
   if (e != cudaSuccess) return e;
-  const int grid = std::min(sm_count(), p.num_tiles);
+  // the bulk of the update (part 2) may leave a few SMs to the look-ahead chain
+  // (next block column, diagonal block, panel solve), which would otherwise wait for
+  // whole update CTAs to retire
+  static const int reserve = [] {
+    const char* v = getenv("PHI4_CHOL_UPDATE_RESERVE");
+    return v ? std::max(0, atoi(v)) : 32;
+  }();
+  const int avail = part == 2 ? std::max(1, sm_count() - reserve) : sm_count();
+  const int grid = std::min(avail, p.num_tiles);
   emu::chol_update_kernel<<<grid, emu::NUM_THREADS, emu::SMEM_BYTES, s>>>(ma, mb, p);
   return cudaGetLastError();
 }
