@@ -182,8 +182,11 @@ phi4_status phi4_kernel_launches(const phi4_run* run, int64_t* out);
 /* Per-stage device timing of a run. When enabled, CUDA events bracket each
  * stage on the run's stream; phi4_stage_times returns accumulated milliseconds
  * and launch counts since the last reset, for stage ids 0..PHI4_N_STAGES-1
- * (names from phi4_stage_name). Synchronises the run's stream. */
-#define PHI4_N_STAGES 12
+ * (names from phi4_stage_name). Synchronises the run's stream. Stage 12
+ * ("chol_update") is kernel-level: event pairs around each tensor-core trailing
+ * update launch of the Cholesky, on the stream it runs on; its time is part of
+ * stage 4 ("cholesky"). */
+#define PHI4_N_STAGES 13
 phi4_status phi4_set_stage_timing(phi4_run* run, int32_t enable);
 phi4_status phi4_stage_times(phi4_run* run, double* ms_out, int64_t* launches_out, int32_t reset);
 const char* phi4_stage_name(int32_t stage);

@@ -176,7 +176,7 @@ phi4_status factor_attempt(phi4_run* r) {
   } else {
     CUDA_TRY(launch_copy_lower(r->sigma, r->chol, D, s));
     CUDA_TRY(launch_cholesky(r->chol, D, r->scal + SC_RIDGE, r->status, r->chol_aux, s, r->side, r->evA, r->evB,
-                             r->cfg.chol_mode));
+                             r->cfg.chol_mode, r->timing ? &r->upd_timer : nullptr));
   }
   r->kernel_launches += 1 + cholesky_launches(D);
   return PHI4_OK;
@@ -588,6 +588,7 @@ phi4_status smc_free(phi4_run* r) {
     cudaEventDestroy(rec.b);
   }
   for (auto e : r->pool) cudaEventDestroy(e);
+  r->upd_timer.release();
   if (r->side) {
     cudaStreamSynchronize(r->side);
     cudaStreamDestroy(r->side);

@@ -1,5 +1,7 @@
 // Host-side launchers shared by the translation units of libphi4smc (not part of the ABI).
 #pragma once
+#include <utility>
+#include <vector>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -53,15 +55,67 @@ cudaError_t launch_covariance(const void* phi, int precision, int N, int D, doub
                               uint32_t* status, cudaStream_t s);
 cudaError_t launch_ridge(const double* sigma, int D, double jitter_rel, double* ridge, cudaStream_t s);
 
+// CUDA-event pairs around selected kernel launches, each pair on the launch's own
+// stream (kernel-level timing inside a stage that spans two streams).
+struct LaunchTimer {
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+  std::vector<cudaEvent_t> pool;
+  double ms = 0.0;
+  int64_t launches = 0;
+  cudaEvent_t take() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  cudaEvent_t begin(cudaStream_t s) {
+    cudaEvent_t a = take();
+    cudaEventRecord(a, s);
+    return a;
+  }
+  void end(cudaStream_t s, cudaEvent_t a) {
+    cudaEvent_t b = take();
+    cudaEventRecord(b, s);
+    pending.push_back({a, b});
+  }
+  // after the streams are synchronised
+  void collect() {
+    for (auto& pr : pending) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, pr.first, pr.second) == cudaSuccess) {
+        ms += t;
+        launches += 1;
+      }
+      pool.push_back(pr.first);
+      pool.push_back(pr.second);
+    }
+    pending.clear();
+  }
+  void release() {
+    for (auto& pr : pending) {
+      pool.push_back(pr.first);
+      pool.push_back(pr.second);
+    }
+    pending.clear();
+    for (auto e : pool) cudaEventDestroy(e);
+    pool.clear();
+  }
+};
+
 // kernels_chol.cu
 cudaError_t launch_copy_lower(const double* src, double* dst, int D, cudaStream_t s);
 // In-place blocked Cholesky; aux: cholesky_aux_bytes(D) device scratch for the diagonal-block
 // inverses. With side != nullptr the look-ahead schedule uses `side` and the two events.
 size_t cholesky_aux_bytes(int D);
 // mode: 0 automatic (tensor-core trailing update for D >= 256), 1 FP64 SIMT update, 2 tensor-core update
+// `timer` (optional) brackets every tensor-core trailing-update launch.
 cudaError_t launch_cholesky(double* a, int D, const double* ridge, uint32_t* status, void* aux, cudaStream_t s,
                             cudaStream_t side = nullptr, cudaEvent_t evA = nullptr, cudaEvent_t evB = nullptr,
-                            int mode = 0);
+                            int mode = 0, LaunchTimer* timer = nullptr);
 // A22 -= P P^T from the digit planes of the panel P (kernels_tc.cu)
 cudaError_t launch_chol_update_tc(double* a, int D, int b0, int m, const void* planes, int m_pad, const int* rexp,
                                   int part, uint32_t* status, cudaStream_t s);

@@ -395,7 +395,8 @@ cudaError_t launch_copy_lower(const double* src, double* dst, int D, cudaStream_
 // every tile is the same either way, so both schedules give identical results.
 template <typename T>
 static cudaError_t cholesky_t(T* a, int D, const double* ridge, void* aux, uint32_t* status, cudaStream_t s,
-                              cudaStream_t side, cudaEvent_t evA, cudaEvent_t evB, bool tensor_update) {
+                              cudaStream_t side, cudaEvent_t evA, cudaEvent_t evB, bool tensor_update,
+                              LaunchTimer* timer = nullptr) {
   const int nblk = (D + NB - 1) / NB;
   const bool ahead = side != nullptr && nblk > 2;
   T* W = (T*)aux;
@@ -410,8 +411,13 @@ static cudaError_t cholesky_t(T* a, int D, const double* ridge, void* aux, uint3
   auto update = [&](int kb, int part, unsigned grid_all, unsigned grid_col, unsigned grid_rest,
                     cudaStream_t st) -> cudaError_t {
     const int k0 = kb * NB, b0 = k0 + NB;
-    if (tcu)
-      return launch_chol_update_tc((double*)a, D, b0, D - b0, planes[kb & 1], m_pad, rexp[kb & 1], part, status, st);
+    if (tcu) {
+      cudaEvent_t t0 = timer ? timer->begin(st) : nullptr;
+      const cudaError_t e =
+          launch_chol_update_tc((double*)a, D, b0, D - b0, planes[kb & 1], m_pad, rexp[kb & 1], part, status, st);
+      if (timer) timer->end(st, t0);
+      return e;
+    }
     const unsigned g = part == 0 ? grid_all : (part == 1 ? grid_col : grid_rest);
     if (g > 0) syrk_update_kernel<T><<<g, 256, 0, st>>>(a, D, k0, part, status);
     return cudaGetLastError();
@@ -472,8 +478,8 @@ static bool use_tensor_update(int D, int mode) {
 }
 
 cudaError_t launch_cholesky(double* a, int D, const double* ridge, uint32_t* status, void* aux, cudaStream_t s,
-                            cudaStream_t side, cudaEvent_t evA, cudaEvent_t evB, int mode) {
-  return cholesky_t<double>(a, D, ridge, aux, status, s, side, evA, evB, use_tensor_update(D, mode));
+                            cudaStream_t side, cudaEvent_t evA, cudaEvent_t evB, int mode, LaunchTimer* timer) {
+  return cholesky_t<double>(a, D, ridge, aux, status, s, side, evA, evB, use_tensor_update(D, mode), timer);
 }
 
 cudaError_t launch_cholesky_f32(const double* sigma, float* a, int D, const double* ridge, uint32_t* status,

@@ -7,9 +7,10 @@
 
 static const char* const kStageNames[PHI4_N_STAGES] = {"bisect_reweight", "resample", "gather", "covariance",
                                                  "cholesky",        "normals",  "propose", "accept",
-                                                 "observables",     "ns_select", "ns_slice", "other"};
+                                                 "observables",     "ns_select", "ns_slice", "other",
+                                                 "chol_update"};
 enum { STG_BISECT, STG_RESAMPLE, STG_GATHER, STG_COV, STG_CHOL, STG_NORMALS, STG_PROPOSE, STG_ACCEPT, STG_OBS,
-       STG_NS_SELECT, STG_NS_SLICE, STG_OTHER };
+       STG_NS_SELECT, STG_NS_SLICE, STG_OTHER, STG_CHOL_UPDATE /* kernel-level, inside STG_CHOL */ };
 
 // Device scalars of a run (one 256-byte block).
 enum { SC_OUT = 0 /* 8 doubles: bisection results */, SC_KAHAN = 8 /* 2 */, SC_BETA = 10, SC_RIDGE = 11,
@@ -44,6 +45,7 @@ struct phi4_run {
   std::vector<Rec> pending;
   std::vector<cudaEvent_t> pool;
   double stage_ms[PHI4_N_STAGES] = {0};
+  phi4::LaunchTimer upd_timer;  // the tensor-core trailing-update launches (STG_CHOL_UPDATE)
   int64_t kernel_launches = 0;  // kernels this run has launched
   int ridge_level = 0;          // decades above chol_jitter_rel that made the last Cholesky succeed
   void* chol_aux = nullptr;     // diagonal-block inverses of the blocked Cholesky
@@ -101,6 +103,11 @@ inline void collect_stage_times(phi4_run* r) {
     r->pool.push_back(rec.b);
   }
   r->pending.clear();
+  const double before = r->upd_timer.ms;
+  const int64_t nb = r->upd_timer.launches;
+  r->upd_timer.collect();
+  r->stage_ms[STG_CHOL_UPDATE] += r->upd_timer.ms - before;
+  r->stage_launches[STG_CHOL_UPDATE] += r->upd_timer.launches - nb;
 }
 
 
