@@ -5,6 +5,7 @@
 // plain FP32 form. A non-positive pivot sets ST_NOT_PD in the status word; later
 // kernels see the bit and return.
 #include <math.h>
+#include <algorithm>
 #include "internal.h"
 #include "common.cuh"
 
@@ -110,21 +111,24 @@ __global__ void __launch_bounds__(kPotrfThreads) potrf_kernel(T* __restrict__ a,
         abort_flag = 1;
         break;
       }
+      // column j-1's contribution (none for column 0: its ring slot was never written)
       const T* lp = lcol[(j - 1) & 3];
       const T lj = j >= 1 ? lp[j] : (T)0;
       // the pivot, in every lane: the rsqrt chain starts without a shuffle
-      const T d = fma(-lj, lj, S[j][j]);
+      const T d = j >= 1 ? fma(-lj, lj, S[j][j]) : S[j][j];
       const bool good = positive_finite(d);
       ok = ok && good;
       const T rd = good ? rsqrt(d) : (T)0;
       T* lo = lcol[j & 3];
       if (j < 32 && i0 >= j) {
-        const T l0 = (i0 == j ? d : fma(-lp[i0], lj, S[i0][j])) * rd;
+        const T c0 = j >= 1 ? fma(-lp[i0], lj, S[i0][j]) : S[i0][j];
+        const T l0 = (i0 == j ? d : c0) * rd;
         lo[i0] = l0;
         S[i0][j] = l0;
       }
       if (i1 >= j && i1 < n) {
-        const T l1 = (i1 == j ? d : fma(-lp[i1], lj, S[i1][j])) * rd;
+        const T c1 = j >= 1 ? fma(-lp[i1], lj, S[i1][j]) : S[i1][j];
+        const T l1 = (i1 == j ? d : c1) * rd;
         lo[i1] = l1;
         S[i1][j] = l1;
       }
@@ -240,28 +244,49 @@ __global__ void __launch_bounds__(kInvThreads) tri_inv_kernel(const T* __restric
 // d_k = (N >> (56 - 7k)) & 127 carrying x's sign: x = sum_k d_k 2^(e - 7k) up to
 // 2^(e - 56). The digits are integers below 128 in magnitude, exact in bf16; plane k
 // (0..7) holds rows [k m_pad, (k+1) m_pad) of a [8 m_pad][64] array.
-__device__ __forceinline__ void split_row_digits(double x0, double x1, int row, int m_pad,
+__device__ __forceinline__ void split_row_digits(double x0, int c0, double x1, int c1, int row, int m_pad,
                                                  __nv_bfloat16* __restrict__ planes, int* __restrict__ rexp) {
+  // integer operations on the bit patterns only (the FP64 unit is the scarce one):
+  // |x| as an unsigned integer orders like |x|, so the row maximum is an integer max
+  const unsigned long long b0 = (unsigned long long)__double_as_longlong(x0),
+                           b1 = (unsigned long long)__double_as_longlong(x1);
+  const unsigned long long mag = 0x7FFFFFFFFFFFFFFFull;
+  unsigned long long amax = (b0 & mag) > (b1 & mag) ? (b0 & mag) : (b1 & mag);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, amax, o);
+    amax = t > amax ? t : amax;
+  }
+  // e = ilogb(max |x|) + 1, or 0 for a zero row
+  int e = 0;
+  if (amax != 0ull) {
+    const int ex = (int)(amax >> 52);
+    e = ex > 0 ? ex - 1022 : (63 - __clzll((long long)amax)) - 1074 + 1;
+  }
   const int lane = threadIdx.x & 31;
-  const double amax = warp_max(fmax(fabs(x0), fabs(x1)));
-  const int e = amax > 0.0 ? ilogb(amax) + 1 : 0;
   if (lane == 0) rexp[row] = e;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
-    const double x = h ? x1 : x0;
-    const unsigned long long N = (unsigned long long)ldexp(fabs(x), 56 - e);
-    const bool neg = x < 0.0;
+    const unsigned long long bits = h ? b1 : b0;
+    const int col = h ? c1 : c0;
+    // N = floor(|x| 2^(56-e)) with |x| = M 2^(E-1075): shift the 53-bit significand
+    const int E = (int)((bits >> 52) & 0x7FF);
+    const unsigned long long M = (bits & 0x000FFFFFFFFFFFFFull) | (E ? (1ull << 52) : 0ull);
+    const int sh = (E ? E : 1) - 1019 - e;
+    const unsigned long long N = sh >= 0 ? (M << sh) : (sh > -64 ? (M >> -sh) : 0ull);
+    const bool neg = (bits >> 63) != 0ull;
 #pragma unroll
     for (int k = 1; k <= 8; ++k) {
       const int d = (int)((N >> (56 - 7 * k)) & 127ull);
-      planes[((size_t)(k - 1) * m_pad + row) * 64 + lane + 32 * h] = __float2bfloat16_rn((float)(neg ? -d : d));
+      planes[((size_t)(k - 1) * m_pad + row) * 64 + col] = __float2bfloat16_rn((float)(neg ? -d : d));
     }
   }
 }
 
 // Panel below diagonal block k0: X = A W^T with W = L_kk^{-1} (solves X L_kk^T = A),
 // kTrsmRows rows per CTA (many small CTAs keep the panel solve short on the critical
-// path of the factorisation), written in place.
+// path of the factorisation), written in place. Only full 64-wide panels come here
+// (the last diagonal block has no panel below it).
 constexpr int kTrsmRows = 8;
 template <typename T>
 __global__ void __launch_bounds__(256) trsm_gemm_kernel(T* __restrict__ a, int D, int k0, const T* __restrict__ W,
@@ -284,50 +309,53 @@ __global__ void __launch_bounds__(256) trsm_gemm_kernel(T* __restrict__ a, int D
     As[i][c] = (i < rows && c < n) ? a[(size_t)(r0 + i) * D + k0 + c] : (T)0;
   }
   __syncthreads();
-  // thread -> (row = tid / 32, output columns lane and lane + 32); W[c][m] = 0 for m > c
-  const int rr = threadIdx.x >> 5, c0 = threadIdx.x & 31;
-  // W is lower triangular: column c0 < 32 only needs m < 32
-  T acc0 = (T)0, acc1 = (T)0;
-#pragma unroll 8
-  for (int m = 0; m < 32; ++m) {
-    const T x = As[rr][m];
-    acc0 = fma(x, Ws[c0][m], acc0);
-    acc1 = fma(x, Ws[c0 + 32][m], acc1);
+  // W is lower triangular (W[c][m] = 0 for m > c): lane l forms columns l and 63 - l,
+  // l + 1 and 64 - l terms, one 65-step loop with the same trip count in every lane
+  // (a predicated-off FP64 instruction would cost as much as a live one)
+  const int rr = threadIdx.x >> 5, l = threadIdx.x & 31;
+  T acc = (T)0, acc_a = (T)0;
+#pragma unroll 5
+  for (int t = 0; t <= NB; ++t) {
+    if (t == l + 1) {
+      acc_a = acc;
+      acc = (T)0;
+    }
+    const bool first = t <= l;
+    const int m = first ? t : t - l - 1;
+    const int col = first ? l : NB - 1 - l;
+    acc = fma(As[rr][m], Ws[col][m], acc);
   }
-#pragma unroll 8
-  for (int m = 32; m < NB; ++m) acc1 = fma(As[rr][m], Ws[c0 + 32][m], acc1);
+  const T acc_b = acc;
   if (rr < rows) {
-    if (c0 < n) a[(size_t)(r0 + rr) * D + k0 + c0] = acc0;
-    if (c0 + 32 < n) a[(size_t)(r0 + rr) * D + k0 + c0 + 32] = acc1;
+    a[(size_t)(r0 + rr) * D + k0 + l] = acc_a;
+    a[(size_t)(r0 + rr) * D + k0 + NB - 1 - l] = acc_b;
   }
   if constexpr (sizeof(T) == 8) {
     // the warp holds one whole panel row: split it into the digit planes of the
     // tensor-core trailing update (rows past the panel get zero digits)
-    if (planes != nullptr) split_row_digits(acc0, acc1, blockIdx.x * kTrsmRows + rr, m_pad, planes, rexp);
+    if (planes != nullptr)
+      split_row_digits(acc_a, l, acc_b, NB - 1 - l, blockIdx.x * kTrsmRows + rr, m_pad, planes, rexp);
   }
 }
 
-// Trailing update after block column k0: A_ij -= L_ik L_jk^T on 64 x 64 lower tiles.
-// part 0: every tile; part 1: only the next block column (bj = 0); part 2: the rest.
+// Trailing update after block column k0: A_ij -= L_ik L_jk^T on 64 x 64 lower tiles
+// (bi >= bj, block indices relative to the trailing matrix) with bj in [blk_lo, blk_hi),
+// column by column.
 template <typename T>
-__global__ void __launch_bounds__(256) syrk_update_kernel(T* __restrict__ a, int D, int k0, int part,
+__global__ void __launch_bounds__(256) syrk_update_kernel(T* __restrict__ a, int D, int k0, int blk_lo, int blk_hi,
                                                           const uint32_t* __restrict__ status) {
   __shared__ T As[16][NB + 2];
   __shared__ T Bs[16][NB + 2];
   if (*status & ST_NOT_PD) return;
   const int n = min(NB, D - k0);
-  const long long t = blockIdx.x;
-  int bi, bj;
-  if (part == 1) {
-    bi = (int)t;
-    bj = 0;
-  } else {
-    bi = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-    while ((long long)(bi + 1) * (bi + 2) / 2 <= t) ++bi;
-    while ((long long)bi * (bi + 1) / 2 > t) --bi;
-    bj = (int)(t - (long long)bi * (bi + 1) / 2);
-    if (part == 2) { ++bi; ++bj; }
+  const int below = (D - k0 - n + NB - 1) / NB;
+  int t = blockIdx.x, bj = blk_lo;
+  while (bj < blk_hi && t >= below - bj) {
+    t -= below - bj;
+    ++bj;
   }
+  if (bj >= blk_hi || bj >= below) return;
+  const int bi = bj + t;
   const int base = k0 + n;
   const int i0 = base + bi * NB, j0 = base + bj * NB;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
@@ -403,23 +431,32 @@ static cudaError_t cholesky_t(T* a, int D, const double* ridge, void* aux, uint3
   T* rdiag = (T*)((unsigned char*)aux + round256((size_t)nblk * NB * NB * sizeof(double)));
   const int m_pad = mpad_of(D);
   unsigned char* dig0 = (unsigned char*)rdiag + round256((size_t)nblk * NB * sizeof(double));
-  __nv_bfloat16* planes[2] = {(__nv_bfloat16*)dig0, (__nv_bfloat16*)(dig0 + round256(8 * (size_t)m_pad * 64 * 2))};
-  int* rexp0 = (int*)(dig0 + 2 * round256(8 * (size_t)m_pad * 64 * 2));
-  int* rexp[2] = {rexp0, (int*)((unsigned char*)rexp0 + round256((size_t)m_pad * sizeof(int)))};
+  // digit-plane buffers by panel mod 3 (two suffice for one column of look-ahead: the
+  // bulk update of panel kb ends before panel kb+2 is solved)
+  const size_t plane_bytes = round256(8 * (size_t)m_pad * 64 * 2), rexp_bytes = round256((size_t)m_pad * sizeof(int));
+  __nv_bfloat16* planes[3];
+  int* rexp[3];
+  for (int q = 0; q < 3; ++q) {
+    planes[q] = (__nv_bfloat16*)(dig0 + q * plane_bytes);
+    rexp[q] = (int*)(dig0 + 3 * plane_bytes + q * rexp_bytes);
+  }
   const bool tcu = tensor_update && sizeof(T) == 8;
-  // trailing update after block column kb (part: 0 all, 1 next block column, 2 the rest)
-  auto update = [&](int kb, int part, unsigned grid_all, unsigned grid_col, unsigned grid_rest,
-                    cudaStream_t st) -> cudaError_t {
+  // trailing update by panel kb of the 64-column blocks [lo, hi) of its trailing matrix
+  auto update = [&](int kb, int lo, int hi, cudaStream_t st) -> cudaError_t {
     const int k0 = kb * NB, b0 = k0 + NB;
+    const int below = nblk - kb - 1;
+    hi = std::min(hi, below);
+    if (lo >= hi) return cudaSuccess;
     if (tcu) {
       cudaEvent_t t0 = timer ? timer->begin(st) : nullptr;
-      const cudaError_t e =
-          launch_chol_update_tc((double*)a, D, b0, D - b0, planes[kb & 1], m_pad, rexp[kb & 1], part, status, st);
+      const cudaError_t e = launch_chol_update_tc((double*)a, D, b0, D - b0, planes[kb % 3], m_pad, rexp[kb % 3], lo,
+                                                  hi >= below ? (1 << 20) : hi, status, st);
       if (timer) timer->end(st, t0);
       return e;
     }
-    const unsigned g = part == 0 ? grid_all : (part == 1 ? grid_col : grid_rest);
-    if (g > 0) syrk_update_kernel<T><<<g, 256, 0, st>>>(a, D, k0, part, status);
+    long long g = 0;
+    for (int bj = lo; bj < hi; ++bj) g += below - bj;
+    if (g > 0) syrk_update_kernel<T><<<(unsigned)g, 256, 0, st>>>(a, D, k0, lo, hi, status);
     return cudaGetLastError();
   };
   const size_t sm_trsm = sizeof(T) * (NB + kTrsmRows) * (NB + 1);
@@ -437,27 +474,30 @@ static cudaError_t cholesky_t(T* a, int D, const double* ridge, void* aux, uint3
       // row of the update's 128-row tiles (rows >= `rows` get zeros)
       const int grid_rows = tcu ? (rows + 127) / 128 * 128 : rows;
       trsm_gemm_kernel<T><<<(grid_rows + kTrsmRows - 1) / kTrsmRows, 256, sm_trsm, st>>>(
-          a, D, k0, W + (size_t)kb * NB * NB, status, tcu ? planes[kb & 1] : nullptr, rexp[kb & 1], m_pad);
+          a, D, k0, W + (size_t)kb * NB * NB, status, tcu ? planes[kb % 3] : nullptr, rexp[kb % 3], m_pad);
     }
   };
   panel(0, s);
-  for (int kb = 0; kb < nblk - 1; ++kb) {
-    const int k0 = kb * NB;
-    const int below = nblk - kb - 1;
-    const long long all = (long long)below * (below + 1) / 2;
-    const long long rest = all - below;
-    cudaError_t e;
-    if (!ahead) {
-      if ((e = update(kb, 0, (unsigned)all, (unsigned)below, (unsigned)rest, s)) != cudaSuccess) return e;
+  cudaError_t e;
+  if (!ahead) {
+    for (int kb = 0; kb < nblk - 1; ++kb) {
+      if ((e = update(kb, 0, nblk, s)) != cudaSuccess) return e;
       panel(kb + 1, s);
-      continue;
     }
+    return cudaGetLastError();
+  }
+  // One block column of look-ahead: per panel kb, `side` (high priority) updates block
+  // column kb+1 and factors/solves panel kb+1 while `s` applies the rest of the update.
+  // Block column kb+1 gets panel kb-1's update from `s` at the previous step, hence the
+  // wait on evA. (Looking two columns ahead measured slower: the extra one-column
+  // update launch per panel cost more than the waits it removed.)
+  for (int kb = 0; kb < nblk - 1; ++kb) {
     if ((e = cudaEventRecord(evA, s)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(side, evA, 0)) != cudaSuccess) return e;
-    if ((e = update(kb, 1, (unsigned)all, (unsigned)below, (unsigned)rest, side)) != cudaSuccess) return e;
+    if ((e = update(kb, 0, 1, side)) != cudaSuccess) return e;
     panel(kb + 1, side);
     if ((e = cudaEventRecord(evB, side)) != cudaSuccess) return e;
-    if ((e = update(kb, 2, (unsigned)all, (unsigned)below, (unsigned)rest, s)) != cudaSuccess) return e;
+    if ((e = update(kb, 1, nblk, s)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(s, evB, 0)) != cudaSuccess) return e;
   }
   return cudaGetLastError();
@@ -467,7 +507,7 @@ size_t cholesky_aux_bytes(int D) {
   const size_t nblk = (size_t)(D + NB - 1) / NB;
   const size_t mp = (size_t)mpad_of(D);
   return round256(nblk * NB * NB * sizeof(double)) + round256(nblk * NB * sizeof(double)) +
-         2 * round256(8 * mp * 64 * 2) + 2 * round256(mp * sizeof(int));
+         3 * round256(8 * mp * 64 * 2) + 3 * round256(mp * sizeof(int));
 }
 
 // Which trailing update the double factorisation uses (mode 0 = automatic).

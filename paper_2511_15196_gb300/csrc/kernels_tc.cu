@@ -357,7 +357,8 @@ static cudaError_t launch(const CUtensorMap& a, const CUtensorMap& b, const Para
 // and the result, scaled by 2^(e_i + e_j - 14), is subtracted in FP64.
 // Tiles of 128 rows x 32 columns of the lower trailing matrix (two tiles' group
 // accumulators fit in TMEM, so the MMAs of one tile overlap the epilogue of the
-// previous one); part 1 = the next block column only, part 2 = the rest, part 0 = all.
+// previous one); a launch covers the 64-column blocks [blk_lo, blk_hi) of the
+// trailing matrix.
 namespace emu {
 constexpr int BM = 128, BN = 32, KD = 64, ND = 8, NC = 8;
 constexpr int A_PLANE = BM * KD * 2;
@@ -365,13 +366,14 @@ constexpr int B_PLANE = BN * KD * 2;
 constexpr int SMEM_DATA = ND * (A_PLANE + B_PLANE);  // 160 KB: leaves room on the SM for the panel kernels
 constexpr int SMEM_BYTES = SMEM_DATA + 1024 + 256;
 constexpr int ACC_COLS = NC * BN;  // one tile's eight group accumulators; two tiles fit in TMEM
-constexpr int P1_COLS = KD / BN;   // tile columns of the next block column (part 1)
+constexpr int BLK_COLS = KD / BN;  // tile columns per 64-column block
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
 
 struct Params {
   double* a;
-  int D, b0, m, m_pad, tiles_m, tiles_n, num_tiles, part;
+  int D, b0, m, m_pad, tiles_m, tiles_n, num_tiles;
+  int col_lo, col_hi;  // tile columns [col_lo, col_hi) of the lower trailing matrix
   const int* rexp;
   uint32_t* status;
 };
@@ -386,25 +388,22 @@ PHI4_DEV void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Tile u of the part's list: part 1 walks the next block column (P1_COLS tile
-// columns of every 128-row band), parts 0 and 2 the lower tiles band by band.
+// Tile u of the launch's list: 128-row bands from the top, in each the lower tiles
+// whose column lies in [col_lo, col_hi).
+PHI4_DEV int band_tiles(const Params& p, int mb) {
+  const int hi = min(min(p.col_hi, p.tiles_n), (mb * BM + BM - 1) / BN + 1);
+  return max(0, hi - p.col_lo);
+}
 PHI4_DEV void get_tile(const Params& p, int u, int& mb, int& bj) {
-  const int p1 = min(P1_COLS, p.tiles_n);
-  if (p.part == 1) {
-    mb = u / p1;
-    bj = u - mb * p1;
-    return;
-  }
-  const int first = p.part == 2 ? p1 : 0;
   int m = 0, base = 0;
   for (;;) {
-    const int cnt = max(0, min(p.tiles_n, (m * BM + BM - 1) / BN + 1) - first);
+    const int cnt = band_tiles(p, m);
     if (u < base + cnt) break;
     base += cnt;
     ++m;
   }
   mb = m;
-  bj = u - base + first;
+  bj = u - base + p.col_lo;
 }
 
 PHI4_DEV double pow2(int n) {
@@ -631,7 +630,7 @@ cudaError_t launch_syrk_tc(const void* XcTb, int ldx, int D, int N, double inv_n
 }
 
 cudaError_t launch_chol_update_tc(double* a, int D, int b0, int m, const void* planes, int m_pad, const int* rexp,
-                                  int part, uint32_t* status, cudaStream_t s) {
+                                  int blk_lo, int blk_hi, uint32_t* status, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
   CUtensorMap ma, mb;
   if (!tc::make_map(&ma, planes, 64, 8 * m_pad, 64, emu::BM) || !tc::make_map(&mb, planes, 64, 8 * m_pad, 64, emu::BN))
@@ -644,30 +643,29 @@ cudaError_t launch_chol_update_tc(double* a, int D, int b0, int m, const void* p
   p.m_pad = m_pad;
   p.tiles_m = (m + emu::BM - 1) / emu::BM;
   p.tiles_n = (m + emu::BN - 1) / emu::BN;
-  p.part = part;
+  p.col_lo = blk_lo * emu::BLK_COLS;
+  p.col_hi = blk_hi >= (1 << 20) ? (1 << 30) : blk_hi * emu::BLK_COLS;
+  int count = 0;
+  for (int mm = 0; mm < p.tiles_m; ++mm) {
+    const int hi = std::min(std::min(p.col_hi, p.tiles_n), (mm * emu::BM + emu::BM - 1) / emu::BN + 1);
+    count += std::max(0, hi - p.col_lo);
+  }
+  p.num_tiles = count;
   p.rexp = rexp;
   p.status = status;
-  const int p1 = std::min(emu::P1_COLS, p.tiles_n);
-  if (part == 1) {
-    p.num_tiles = p.tiles_m * p1;
-  } else {
-    int count = 0;
-    for (int mm = 0; mm < p.tiles_m; ++mm)
-      count += std::max(0, std::min(p.tiles_n, (mm * emu::BM + emu::BM - 1) / emu::BN + 1) - (part == 2 ? p1 : 0));
-    p.num_tiles = count;
-  }
   if (p.num_tiles == 0) return cudaSuccess;
   cudaError_t e =
       cudaFuncSetAttribute(emu::chol_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, emu::SMEM_BYTES);
   if (e != cudaSuccess) return e;
-  // the bulk of the update (part 2) may leave a few SMs to the look-ahead chain
-  // (next block column, diagonal block, panel solve), which would otherwise wait for
+  // the bulk of the update may leave a few SMs to the look-ahead chain (diagonal
+  // block, inverse, panel solve, next block columns), which would otherwise wait for
   // whole update CTAs to retire
   static const int reserve = [] {
     const char* v = getenv("PHI4_CHOL_UPDATE_RESERVE");
     return v ? std::max(0, atoi(v)) : 32;
   }();
-  const int avail = part == 2 ? std::max(1, sm_count() - reserve) : sm_count();
+  const bool bulk = blk_hi - blk_lo > 1;
+  const int avail = bulk ? std::max(1, sm_count() - reserve) : sm_count();
   const int grid = std::min(avail, p.num_tiles);
   emu::chol_update_kernel<<<grid, emu::NUM_THREADS, emu::SMEM_BYTES, s>>>(ma, mb, p);
   return cudaGetLastError();
