@@ -48,6 +48,27 @@ PHI4_DEV bool cta_mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_
   }
 }
 
+// Shared-memory progress counters between warps of one CTA: the producer publishes with
+// a release store, consumers poll with acquire loads (cheaper than an mbarrier round
+// trip when the value is already there). Waits are bounded like every spin here.
+PHI4_DEV void cta_flag_release(int* f, int v) {
+  asm volatile("st.release.cta.shared::cta.s32 [%0], %1;" ::"r"(cta_smem_addr(f)), "r"(v) : "memory");
+}
+PHI4_DEV int cta_flag_acquire(const int* f) {
+  int v;
+  asm volatile("ld.acquire.cta.shared::cta.s32 %0, [%1];" : "=r"(v) : "r"(cta_smem_addr(f)) : "memory");
+  return v;
+}
+PHI4_DEV bool cta_flag_wait_geq(const int* f, int target, volatile int* abort_flag) {
+  if (cta_flag_acquire(f) >= target) return true;
+  const long long t0 = clock64();
+  for (;;) {
+    if (cta_flag_acquire(f) >= target) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kSpinLimitCycles) return false;
+  }
+}
+
 PHI4_DEV double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -42,23 +42,39 @@ __device__ __forceinline__ bool positive_finite(float x) {
 // Factor the diagonal block A_kk = L_kk L_kk^T (+ ridge) in one CTA, right-looking by
 // columns with one column of look-ahead. On this part an FP64 instruction occupies
 // its SM sub-partition's FP64 unit for 64 cycles whatever its lane mask (rsqrt is
-// about six of them), so the layout is chosen by FP64 instruction count:
-//   warp 0 (alone on its sub-partition) runs the pivot chain: column j receives the
-//     update from column j-1, then rsqrt of its pivot and the scaling; it publishes
-//     L_:j in a ring of four shared vectors;
-//   warps 1-3 and 5-7 (warp 4 idles, sharing warp 0's sub-partition) hold the
-//     trailing elements packed column by column from the last column down, so the
-//     live set (columns >= j+2 at step j) is a prefix and every FP64 instruction has
-//     full lanes; at step j they update column j+2 first, signal, then the rest.
-// Two pairs of mbarriers carry the hand-offs: A[j & 1] (six update warps -> pivot
-// warp: column j+2 is ready) and B[j & 1] (pivot -> update warps: L_:j is published);
-// a barrier's next phase needs every waiter past the current one, so parity waits
-// cannot skip a phase. Waits are bounded (ST_TIMEOUT). rsqrt(pivot_j) goes to `rdiag`
-// for the inverse.
-constexpr int kPotrfThreads = 256;
+// about six of them), so the roles follow the FP64 instruction count:
+//   warp 0, alone on its sub-partition, runs only the scalar pivot chain: d_j ->
+//     rsqrt -> L_{j+1,j} -> d_{j+1} (nine FP64 instructions per column);
+//   warp 1 (the column warp) scales column j once rsqrt(d_j) is known and publishes
+//     L_:j in a ring of four shared vectors (and writes it out);
+//   warps 2, 3, 5, 6, 7, 9 hold the trailing elements packed column by column from
+//     the last column down, so the live set (columns >= k+2 at step k) is a prefix
+//     and every FP64 instruction has full lanes; at step k they update column k+2
+//     first, signal, then the rest. Warps 4 and 8 share warp 0's sub-partition and idle.
+// Hand-offs are mbarrier pairs (phase k on object k & 1, bounded parity waits):
+//   C(j): pivot -> column warp, rsqrt(d_j) and d_j are ready;
+//   B(k): column warp -> update warps, L_:k is published;
+//   A(k): update warps -> pivot, column k+2 has every update of columns <= k (and,
+//   since the update warps passed B(k) first, column k is published).
+// A barrier's next phase on the same object needs every waiter past the current one,
+// so no wait can skip a phase. (Polling shared-memory flags instead measured slower:
+// the spinning warps cost more than the mbarrier round trips.) rsqrt(d_j) goes to
+// `rdiag` for the inverse.
+constexpr int kPotrfThreads = 320;
 constexpr int kUpdWarps = 6;
 constexpr int kUpdThreads = 32 * kUpdWarps;
 constexpr int kUpdSlots = ((NB - 2) * (NB - 1) / 2 + kUpdThreads - 1) / kUpdThreads;  // 11
+__device__ __forceinline__ int upd_warp_index(int warp) {  // -1: not an update warp
+  switch (warp) {
+    case 2: return 0;
+    case 3: return 1;
+    case 5: return 2;
+    case 6: return 3;
+    case 7: return 4;
+    case 9: return 5;
+    default: return -1;
+  }
+}
 template <typename T>
 __global__ void __launch_bounds__(kPotrfThreads) potrf_kernel(T* __restrict__ a, int D, int k0,
                                                               const double* __restrict__ ridge,
@@ -66,11 +82,12 @@ __global__ void __launch_bounds__(kPotrfThreads) potrf_kernel(T* __restrict__ a,
   __shared__ T S[NB][NB + 1];
   __shared__ T lcol[4][NB];
   __shared__ T rds[NB];
+  __shared__ T dpiv[2];
   // update element e = slot * kUpdThreads + t of update thread t, packed (row << 8) | column:
   // columns from n-1 down to 2, rows >= column (column c = n-1-r for the triangular
   // root r of e, row = c + e - r(r+1)/2), so the live set of every step is a prefix
   __shared__ uint32_t eidx[kUpdSlots][kUpdThreads];
-  __shared__ __align__(8) uint64_t barA[2], barB[2];
+  __shared__ __align__(8) uint64_t barA[2], barB[2], barC[2];
   __shared__ int fail;
   __shared__ volatile int abort_flag;
   if (*status & ST_NOT_PD) return;
@@ -99,46 +116,76 @@ __global__ void __launch_bounds__(kPotrfThreads) potrf_kernel(T* __restrict__ a,
     for (int q = 0; q < 2; ++q) {
       cta_mbar_init(&barA[q], kUpdWarps);
       cta_mbar_init(&barB[q], 1);
+      cta_mbar_init(&barC[q], 1);
     }
   }
   __syncthreads();
+  const int uw = upd_warp_index(warp);
   if (warp == 0) {
+    // ---- pivot chain (every lane computes the same scalars). Iteration j: rsqrt(d_j)
+    // and publish it at once (the column warp and the update warps then have the
+    // iteration's remaining time to deliver what iteration j+1 waits for), then
+    // L_{j+1,j} and d_{j+1}. (Waiting first and publishing later measured slower: it
+    // lengthens the pivot -> column -> update -> pivot cycle.)
     bool ok = true;
-    const int i0 = lane, i1 = lane + 32;
+    T d = S[0][0];
+    T lprev = (T)0;  // L_{j,j-1}
     for (int j = 0; j < n; ++j) {
-      // column j has the updates of columns <= j-2
-      if (j >= 2 && !cta_mbar_wait(&barA[j & 1], ((j - 2) >> 1) & 1, &abort_flag)) {
-        abort_flag = 1;
-        break;
-      }
-      // column j-1's contribution (none for column 0: its ring slot was never written)
-      const T* lp = lcol[(j - 1) & 3];
-      const T lj = j >= 1 ? lp[j] : (T)0;
-      // the pivot, in every lane: the rsqrt chain starts without a shuffle
-      const T d = j >= 1 ? fma(-lj, lj, S[j][j]) : S[j][j];
       const bool good = positive_finite(d);
       ok = ok && good;
       const T rd = good ? rsqrt(d) : (T)0;
-      T* lo = lcol[j & 3];
-      if (j < 32 && i0 >= j) {
-        const T c0 = j >= 1 ? fma(-lp[i0], lj, S[i0][j]) : S[i0][j];
-        const T l0 = (i0 == j ? d : c0) * rd;
-        lo[i0] = l0;
-        S[i0][j] = l0;
+      if (lane == 0) {
+        rds[j] = rd;
+        dpiv[j & 1] = d;
+        cta_mbar_arrive(&barC[j & 1]);
       }
-      if (i1 >= j && i1 < n) {
-        const T c1 = j >= 1 ? fma(-lp[i1], lj, S[i1][j]) : S[i1][j];
-        const T l1 = (i1 == j ? d : c1) * rd;
-        lo[i1] = l1;
-        S[i1][j] = l1;
+      if (j + 1 >= n) break;
+      // L_{j+1,j} = (A_{j+1,j} - L_{j+1,j-1} L_{j,j-1}) rd_j needs column j's entry with
+      // every update of columns <= j-2 and column j-1 published; d_{j+1} needs
+      // A_{j+1,j+1} with the updates of columns <= j-1: all given by A(j-1)
+      T l1 = (T)0;
+      if (j >= 1) {
+        if (!cta_mbar_wait(&barA[(j - 1) & 1], ((j - 1) >> 1) & 1, &abort_flag)) {
+          abort_flag = 1;
+          break;
+        }
+        l1 = lcol[(j - 1) & 3][j + 1];
       }
-      if (lane == 0) rds[j] = rd;
-      __syncwarp();
-      if (j + 2 < n && lane == 0) cta_mbar_arrive(&barB[j & 1]);
+      const T lnext = fma(-l1, lprev, S[j + 1][j]) * rd;
+      d = fma(-lnext, lnext, S[j + 1][j + 1]);
+      lprev = lnext;
     }
     if (!ok && lane == 0) fail = 1;
-  } else if (warp != 4) {
-    const int bt = (warp < 4 ? warp - 1 : warp - 2) * 32 + lane;
+  } else if (warp == 1) {
+    // ---- column warp: L_:j = (A_:j - L_:j-1 L_{j,j-1}) rd_j, L_jj = d_j rd_j
+    const int i0 = lane, i1 = lane + 32;
+    for (int j = 0; j < n; ++j) {
+      if (!cta_mbar_wait(&barC[j & 1], (j >> 1) & 1, &abort_flag)) {
+        abort_flag = 1;
+        break;
+      }
+      const T rd = rds[j], dj = dpiv[j & 1];
+      const T* lp = lcol[(j - 1) & 3];
+      const T lj = j >= 1 ? lp[j] : (T)0;  // column 0 has no previous column (its ring slot is unwritten)
+      T* lo = lcol[j & 3];
+      if (j < 32 && i0 >= j) {
+        const T c0 = i0 == j ? dj : (j >= 1 ? fma(-lp[i0], lj, S[i0][j]) : S[i0][j]);
+        const T l0 = c0 * rd;
+        lo[i0] = l0;
+        a[(size_t)(k0 + i0) * D + k0 + j] = l0;
+      }
+      if (i1 >= j && i1 < n) {
+        const T c1 = i1 == j ? dj : (j >= 1 ? fma(-lp[i1], lj, S[i1][j]) : S[i1][j]);
+        const T l1 = c1 * rd;
+        lo[i1] = l1;
+        a[(size_t)(k0 + i1) * D + k0 + j] = l1;
+      }
+      __syncwarp();
+      if (lane == 0) cta_mbar_arrive(&barB[j & 1]);
+    }
+  } else if (uw >= 0) {
+    // ---- trailing update
+    const int bt = uw * 32 + lane;
     const int wbase = bt - lane;
     // The passes loop over live slots only, with warp-uniform bounds: a predicated-off
     // FP64 instruction would still hold the FP64 unit for its full 64 cycles.
@@ -151,8 +198,8 @@ __global__ void __launch_bounds__(kPotrfThreads) potrf_kernel(T* __restrict__ a,
       const int live = (n - k - 2) * (n - k - 1) / 2;  // elements of columns >= k+2
       const int rest = (n - k - 3) * (n - k - 2) / 2;  // elements of columns >= k+3
       // column k+2 (elements rest .. live-1) first
-#pragma unroll 1
       const int first = rest - wbase - 31;  // first slot whose warp range reaches e >= rest
+#pragma unroll 1
       for (int sl = first > 0 ? (first + kUpdThreads - 1) / kUpdThreads : 0; sl * kUpdThreads + wbase < live; ++sl) {
         const int e = sl * kUpdThreads + bt;
         if (e >= rest && e < live) {
@@ -193,9 +240,10 @@ __global__ void __launch_bounds__(kPotrfThreads) potrf_kernel(T* __restrict__ a,
     if (tid == 0) atomicOr(status, ST_NOT_PD);
     return;
   }
+  // L itself was written by the column warp; zeros above the diagonal
   for (int e = tid; e < n * n; e += kPotrfThreads) {
     const int i = e / n, c = e - (e / n) * n;
-    a[(size_t)(k0 + i) * D + k0 + c] = (c <= i) ? S[i][c] : (T)0;
+    if (c > i) a[(size_t)(k0 + i) * D + k0 + c] = (T)0;
   }
   if (tid < n) rdiag[tid] = rds[tid];
 }

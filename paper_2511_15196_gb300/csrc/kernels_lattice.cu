@@ -153,6 +153,36 @@ PHI4_DEV int accept_decision(double u, double log_alpha) {
   return log(u) < log_alpha;
 }
 
+// The same decision from the raw Philox words of u = (x + 1) 2^-53, x = (w0 << 21) |
+// (w1 >> 11), with no FP64 instruction on the common path (an FP64 instruction holds
+// its sub-partition's FP64 unit for 64 cycles on this part): the special cases of
+// log alpha are read from its bit pattern, u and log alpha are truncated to float with
+// integer operations (relative error <= 2^-23 each), and logf of the float u is within
+// 5e-6 of log u for |log u| <= 37; outside a 2e-5 band the float comparison decides,
+// inside it the double one does (rare).
+PHI4_DEV int accept_decision_bits(uint32_t w0, uint32_t w1, double log_alpha) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(log_alpha);
+  const unsigned long long mag = b & 0x7FFFFFFFFFFFFFFFull;
+  const unsigned long long x = ((unsigned long long)w0 << 21) | (unsigned long long)(w1 >> 11);
+  if (mag > 0x7FF0000000000000ull) return 0;                // NaN
+  if (mag == 0ull) return x != (1ull << 53) - 1ull;          // log alpha = 0: accept iff u < 1
+  if ((b >> 63) == 0ull) return 1;                           // log alpha > 0 (or +inf)
+  if (mag > 0x4044000000000000ull) return 0;                 // log alpha < -40 (or -inf) <= log 2^-53
+  // float of u (truncated): the top 24 bits of x + 1 <= 2^53 with its exponent
+  const unsigned long long x1 = x + 1ull;
+  const int lz = __clzll((long long)x1);                     // 11 .. 63
+  const int top = 63 - lz;                                   // x1 in [2^top, 2^(top+1))
+  const uint32_t man = top >= 23 ? (uint32_t)(x1 >> (top - 23)) : (uint32_t)(x1 << (23 - top));
+  const float uf = __uint_as_float(((uint32_t)(top - 53 + 127) << 23) | (man & 0x7FFFFFu));
+  // float of log alpha (truncated, negative, |log alpha| <= 40; tiny values flush to -0)
+  const int ex = (int)(mag >> 52) - 1023 + 127;
+  const float la = ex <= 0 ? -0.0f : __uint_as_float(0x80000000u | ((uint32_t)ex << 23) | (uint32_t)((mag >> 29) & 0x7FFFFFull));
+  const float lf = logf(uf);
+  if (lf < la - 2e-5f) return 1;
+  if (lf > la + 2e-5f) return 0;
+  return log((double)x1 * 0x1p-53) < log_alpha;
+}
+
 // Float fields with L % 4 == 0: each thread owns float4 groups of four sites of one
 // lattice row (kept in registers), reads the up/down neighbour groups and the two
 // horizontal end neighbours from the staged row, and keeps plain float partial sums
@@ -169,9 +199,9 @@ __global__ void __launch_bounds__(PPB* TPP) accept_vec_kernel(float* __restrict_
                                                               uint32_t* __restrict__ acc_count,
                                                               uint32_t* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[PPB][TPP / 32][2];
+  __shared__ float red[PPB][TPP / 32][2];
   __shared__ int accept_flag[PPB];
-  __shared__ double uni[PPB];
+  __shared__ uint2 uwords[PPB];
   const int g = threadIdx.x / TPP, t = threadIdx.x % TPP;
   const int i = blockIdx.x * PPB + g;
   const int L = p.L, D = p.D, ng = D >> 2;
@@ -197,10 +227,14 @@ __global__ void __launch_bounds__(PPB* TPP) accept_vec_kernel(float* __restrict_
       }
     }
   }
-  // the accept uniform, drawn by the group's last lane-0 while the others start the stencil
-  if (i < p.N && t == TPP - 32) {
+  // the particle's decision is taken by warp wd (rotating with the block so the serial
+  // double work lands on every sub-partition in turn); another warp draws its uniform's
+  // words while the others start the stencil
+  constexpr int kWarps = TPP / 32;
+  const int wd = (blockIdx.x + g) % kWarps;
+  if (i < p.N && t == ((wd + kWarps / 2) % kWarps) * 32) {
     const uint4 w = philox4x32_10(make_uint4(w0, sweep, (uint32_t)i, 0u), key);
-    uni[g] = uniform53(w.x, w.y);
+    uwords[g] = make_uint2(w.x, w.y);
   }
   __syncthreads();
   const float ck = (float)p.c_kin, cm = (float)(p.c_mass * p.m2), lm = (float)p.lam;
@@ -230,36 +264,43 @@ __global__ void __launch_bounds__(PPB* TPP) accept_vec_kernel(float* __restrict_
     }
   }
   // float warp trees (<= 32 partials of <= 4 groups each); the warps' results are
-  // combined in double. Double shuffles would keep GB300's slow FP64 pipe busy.
+  // combined in double by the decision warp, one lane per warp result (a 3-level
+  // double tree instead of a serial chain on one sub-partition)
   s = warp_sum(s);
   qq = warp_sum(qq);
   const int lane = t & 31, wg = t >> 5;
   if (lane == 0) {
-    red[g][wg][0] = (double)s;
-    red[g][wg][1] = (double)qq;
+    red[g][wg][0] = s;
+    red[g][wg][1] = qq;
   }
   __syncthreads();
-  if (i < p.N && t == 0) {
-    double Sp = 0.0, Qp = 0.0;
+  if (i < p.N && wg == wd) {
+    double Sp = lane < kWarps ? (double)red[g][lane][0] : 0.0;
+    double Qp = lane < kWarps ? (double)red[g][lane][1] : 0.0;
 #pragma unroll
-    for (int w = 0; w < TPP / 32; ++w) {
-      Sp += red[g][w][0];
-      Qp += red[g][w][1];
+    for (int o = kWarps / 2; o > 0; o >>= 1) {
+      Sp += __shfl_xor_sync(0xffffffffu, Sp, o);
+      Qp += __shfl_xor_sync(0xffffffffu, Qp, o);
     }
-    const double beta = *beta_ptr;
-    const double dS = Sp - S[i], dq2 = Qp - sq[i];
-    const double log_alpha = keep_ref ? (-beta * dS - 0.5 * dq2) : (-beta * dS - (1.0 - beta) * 0.5 * dq2);
-    int acc = accept_decision(uni[g], log_alpha);
-    if (!isfinite(Sp) || !isfinite(Qp)) {
-      atomicOr(status, ST_NONFINITE);
-      acc = 0;
-    }
-    accept_flag[g] = acc;
-    if (acc) {
-      S[i] = Sp;
-      sq[i] = Qp;
-      ell[i] = keep_ref ? -Sp : (-Sp + 0.5 * Qp + p.half_d_log2pi);
-      atomicAdd(acc_count, 1u);
+    if (lane == 0) {
+      const double beta = *beta_ptr;
+      const double dS = Sp - S[i], dq2 = Qp - sq[i];
+      const double log_alpha = keep_ref ? (-beta * dS - 0.5 * dq2) : (-beta * dS - (1.0 - beta) * 0.5 * dq2);
+      const uint2 uw = uwords[g];
+      int acc = accept_decision_bits(uw.x, uw.y, log_alpha);
+      const unsigned long long bs = (unsigned long long)__double_as_longlong(Sp),
+                               bq = (unsigned long long)__double_as_longlong(Qp);
+      if (((bs >> 52) & 0x7FF) == 0x7FF || ((bq >> 52) & 0x7FF) == 0x7FF) {  // not finite
+        atomicOr(status, ST_NONFINITE);
+        acc = 0;
+      }
+      accept_flag[g] = acc;
+      if (acc) {
+        S[i] = Sp;
+        sq[i] = Qp;
+        ell[i] = keep_ref ? -Sp : (-Sp + 0.5 * Qp + p.half_d_log2pi);
+        atomicAdd(acc_count, 1u);
+      }
     }
   }
   __syncthreads();

@@ -1,31 +1,50 @@
-// Philox normals written to a row-major buffer (one thread per block of 4 outputs).
+// Philox normals written to a row-major buffer (one thread per two blocks of 4 outputs).
+#include <algorithm>
 #include "internal.h"
 #include "philox.cuh"
 
 namespace phi4 {
 
+// Each thread makes two consecutive blocks of four normals (counter words 2 and 3 =
+// particle, block) of one row; rows come from the grid's y dimension (no 64-bit index
+// division), and the eight values of a thread are stored together.
 template <typename T>
 __global__ void normals_kernel(PhiloxKey key, uint32_t w0, uint32_t sub, int row0, int n_rows, int n_cols, int ld,
                                T* __restrict__ out) {
   const int nblk = (n_cols + 3) >> 2;
-  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= (long long)n_rows * nblk) return;
-  const int r = (int)(gid / nblk), b = (int)(gid % nblk);
-  const uint4 w = philox4x32_10(make_uint4(w0, sub, (uint32_t)(row0 + r), (uint32_t)b), key);
-  T* o = out + (size_t)r * ld + 4 * b;
-  const int left = n_cols - 4 * b;
-  if constexpr (sizeof(T) == 8) {
-    const double2 z01 = box_muller_f64(w.x, w.y), z23 = box_muller_f64(w.z, w.w);
-    const double z[4] = {z01.x, z01.y, z23.x, z23.y};
+  const int b0 = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (b0 >= nblk) return;
+  for (int r = blockIdx.y; r < n_rows; r += gridDim.y) {
+    T z[8];
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if (j < left) o[j] = z[j];
-  } else {
-    const float2 z01 = box_muller_f32(w.x, w.y), z23 = box_muller_f32(w.z, w.w);
-    const float z[4] = {z01.x, z01.y, z23.x, z23.y};
+    for (int h = 0; h < 2; ++h) {
+      const uint4 w = philox4x32_10(make_uint4(w0, sub, (uint32_t)(row0 + r), (uint32_t)(b0 + h)), key);
+      if constexpr (sizeof(T) == 8) {
+        const double2 z01 = box_muller_f64(w.x, w.y), z23 = box_muller_f64(w.z, w.w);
+        z[4 * h] = z01.x; z[4 * h + 1] = z01.y; z[4 * h + 2] = z23.x; z[4 * h + 3] = z23.y;
+      } else {
+        const float2 z01 = box_muller_f32(w.x, w.y), z23 = box_muller_f32(w.z, w.w);
+        z[4 * h] = to_t<T>(z01.x); z[4 * h + 1] = to_t<T>(z01.y);
+        z[4 * h + 2] = to_t<T>(z23.x); z[4 * h + 3] = to_t<T>(z23.y);
+      }
+    }
+    T* o = out + (size_t)r * ld + 4 * b0;
+    const int left = n_cols - 4 * b0;
+    if (left >= 8 && (((uintptr_t)o) & (8 * sizeof(T) - 1)) == 0) {
+      if constexpr (sizeof(T) == 2) {
+        *reinterpret_cast<uint4*>(o) = *reinterpret_cast<const uint4*>(z);
+      } else if constexpr (sizeof(T) == 4) {
+        reinterpret_cast<uint4*>(o)[0] = reinterpret_cast<const uint4*>(z)[0];
+        reinterpret_cast<uint4*>(o)[1] = reinterpret_cast<const uint4*>(z)[1];
+      } else {
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if (j < left) o[j] = to_t<T>(z[j]);
+        for (int j = 0; j < 8; ++j) o[j] = z[j];
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (j < left) o[j] = z[j];
+    }
   }
 }
 
@@ -34,9 +53,9 @@ cudaError_t launch_normals(uint64_t seed, uint64_t stream_id, uint32_t kind, uin
   if (n_rows <= 0 || n_cols <= 0) return cudaSuccess;
   const PhiloxKey key = philox_key(seed, stream_id);
   const uint32_t w0 = counter_word0(kind, step);
-  const long long work = (long long)n_rows * ((n_cols + 3) / 4);
+  const int nblk = (n_cols + 3) / 4;
   const int threads = 256;
-  const unsigned grid = (unsigned)((work + threads - 1) / threads);
+  const dim3 grid((unsigned)((nblk + 2 * threads - 1) / (2 * threads)), (unsigned)std::min(n_rows, 65535));
   switch (dtype) {
     case 0: normals_kernel<double><<<grid, threads, 0, s>>>(key, w0, sub, row0, n_rows, n_cols, ld, (double*)out); break;
     case 1: normals_kernel<float><<<grid, threads, 0, s>>>(key, w0, sub, row0, n_rows, n_cols, ld, (float*)out); break;
