@@ -338,7 +338,9 @@ def main():
     obs = run.observables()
     units_per_step = a.N * D * a.n_mcmc
     value = world * units_per_step * a.steps / (elapsed_ms * 1e-3)
-    mutation_ms = sum(stage_acc.get(k, [0, 0])[0] for k in ("normals", "propose", "accept"))
+    # wall time of the sweeps (their normals, proposal and accept overlap on three streams)
+    mutation_ms = stage_acc.get("mutation", [0, 0])[0] or \
+        sum(stage_acc.get(k, [0, 0])[0] for k in ("normals", "propose", "accept"))
 
     # roofline of the dominant kernel (kernel-level timers only: the Cholesky stage is
     # many kernels on two streams, its tensor-core trailing update is timed per launch)

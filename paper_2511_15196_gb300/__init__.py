@@ -20,7 +20,7 @@ SMC_RW, NS_SLICE = 0, 1
 FP64, FP32, MIXED_BF16 = 0, 1, 2
 DT_F64, DT_F32, DT_BF16 = 0, 1, 2
 RNG_INIT, RNG_RESAMPLE, RNG_PROPOSE, RNG_ACCEPT, RNG_NS_START, RNG_NS_DIRECTION, RNG_NS_SLICE = range(1, 8)
-N_STAGES = 13
+N_STAGES = 14
 
 _STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_NOT_PD", 4: "ERR_NONFINITE", 5: "ERR_DONE",
                  6: "ERR_WORKSPACE", 7: "ERR_TIMEOUT", 8: "ERR_UNSUPPORTED"}

@@ -11,6 +11,7 @@
 
 #include "philox.cuh"
 #include "run.h"
+#include <cstdlib>
 
 namespace phi4 {
 
@@ -61,6 +62,22 @@ phi4_status check_config(const phi4_config* c) {
   return PHI4_OK;
 }
 
+// The run's own streams and events (the caller's stream is not touched).
+void release_streams(phi4_run* r) {
+  for (cudaStream_t* st : {&r->side, &r->s_norm, &r->s_gemm})
+    if (*st) {
+      cudaStreamSynchronize(*st);
+      cudaStreamDestroy(*st);
+      *st = nullptr;
+    }
+  for (cudaEvent_t* ev : {&r->evA, &r->evB, &r->ev_n[0], &r->ev_n[1], &r->ev_g[0], &r->ev_g[1], &r->ev_a[0],
+                          &r->ev_a[1], &r->ev_start})
+    if (*ev) {
+      cudaEventDestroy(*ev);
+      *ev = nullptr;
+    }
+}
+
 // Workspace layout; with base == nullptr only the total size is computed.
 struct Layout {
   size_t off = 0;
@@ -84,6 +101,7 @@ void lay_out(phi4_run* r, Layout& L) {
     r->ldl = (D + 7) & ~7;
     r->zdtype = PHI4_DT_BF16;
     r->Z = L.take((size_t)N * r->ldz * 2);
+    r->Z2 = L.take((size_t)N * r->ldz * 2);
     r->Lg = L.take((size_t)D * r->ldl * 2);
   } else {
     r->ldz = D;
@@ -286,6 +304,12 @@ phi4_status step_front(phi4_run* r, bool single_cta_bisect) {
 }
 
 // Back of a temperature: the n_mcmc random-walk sweeps (normals, proposal, accept).
+// In the mixed form on L % 4 == 0 lattices the increment Delta = s Z L^T does not
+// depend on the fields, so sweep t+1's normals (stream s_norm, ALU-bound) and proposal
+// GEMM (stream s_gemm, tensor cores) run while sweep t's accept (the run's stream,
+// HBM-bound) runs: Z and Delta are double-buffered (Delta in the two halves of the
+// proposal buffer) and events order each buffer's writer after its last reader. The
+// arithmetic of every sweep is unchanged.
 phi4_status step_back(phi4_run* r) {
   const phi4_config& c = r->cfg;
   const int N = c.N, D = r->D;
@@ -293,6 +317,47 @@ phi4_status step_back(phi4_run* r) {
   const uint32_t t = (uint32_t)r->t;
   CUDA_TRY(cudaMemsetAsync(r->acc_count, 0, 4, s));
   const ActionParams ap = action_params(r);
+  StageScope wall(r, STG_MUTATION);
+  if (c.precision == PHI4_MIXED_BF16 && c.L % 4 == 0 && r->Z2) {
+    void* Zb[2] = {r->Z, r->Z2};
+    void* Db[2] = {r->prop, (unsigned char*)r->prop + (size_t)N * D * 2};
+    CUDA_TRY(cudaEventRecord(r->ev_start, s));  // the factor and the fields are ready
+    CUDA_TRY(cudaStreamWaitEvent(r->s_norm, r->ev_start, 0));
+    CUDA_TRY(cudaStreamWaitEvent(r->s_gemm, r->ev_start, 0));
+    LaunchTimer* tn = r->timing ? &r->norm_timer : nullptr;
+    LaunchTimer* tg = r->timing ? &r->gemm_timer : nullptr;
+    // (normals on the GEMM's stream, i.e. only the accept overlapped, measured slower)
+    cudaStream_t sn = r->s_norm;
+    for (int sweep = 0; sweep < c.n_mcmc; ++sweep) {
+      const int q = sweep & 1;
+      // normals into Z[q] once the GEMM of sweep-2 has read it
+      if (sweep >= 2) CUDA_TRY(cudaStreamWaitEvent(sn, r->ev_g[q], 0));
+      cudaEvent_t a0 = tn ? tn->begin(sn) : nullptr;
+      CUDA_TRY(launch_normals(c.seed, c.stream_id, RNG_PROPOSE, t, (uint32_t)sweep, 0, N, D, r->ldz, r->zdtype,
+                              Zb[q], sn));
+      if (tn) tn->end(sn, a0);
+      CUDA_TRY(cudaEventRecord(r->ev_n[q], sn));
+      // Delta[q] = s Z[q] L^T once the normals are there and the accept of sweep-2 read it
+      CUDA_TRY(cudaStreamWaitEvent(r->s_gemm, r->ev_n[q], 0));
+      if (sweep >= 2) CUDA_TRY(cudaStreamWaitEvent(r->s_gemm, r->ev_a[q], 0));
+      cudaEvent_t a1 = tg ? tg->begin(r->s_gemm) : nullptr;
+      CUDA_TRY(launch_propose_tc(Db[q], Zb[q], r->ldz, r->Lg, r->ldl, N, D, (float)r->scale, r->status, r->s_gemm));
+      if (tg) tg->end(r->s_gemm, a1);
+      CUDA_TRY(cudaEventRecord(r->ev_g[q], r->s_gemm));
+      // the accept chain on the run's stream
+      CUDA_TRY(cudaStreamWaitEvent(s, r->ev_g[q], 0));
+      {
+        StageScope sc(r, STG_ACCEPT);
+        CUDA_TRY(launch_accept_delta((float*)r->phi, Db[q], ap, c.keep_reference, r->S, r->sq, r->ell,
+                                     r->scal + SC_BETA, c.seed, c.stream_id, t, (uint32_t)sweep, r->acc_count,
+                                     r->status, s));
+      }
+      CUDA_TRY(cudaEventRecord(r->ev_a[q], s));
+      r->kernel_launches += 3;
+    }
+    r->n_evals += (int64_t)N * c.n_mcmc;
+    return PHI4_OK;
+  }
   for (int sweep = 0; sweep < c.n_mcmc; ++sweep) {
     phi4_status ps = propose(r, t, (uint32_t)sweep);
     if (ps != PHI4_OK) return ps;
@@ -428,9 +493,7 @@ phi4_status smc_init(const phi4_config* cfg, void* d_workspace, size_t workspace
   cudaStream_t s = r->stream;
   auto fail = [&](cudaError_t e, const char* what) {
     set_error("%s: %s", what, cudaGetErrorString(e));
-    if (r->evA) cudaEventDestroy(r->evA);
-    if (r->evB) cudaEventDestroy(r->evB);
-    if (r->side) cudaStreamDestroy(r->side);
+    release_streams(r);
     delete r;
     return PHI4_ERR_CUDA;
   };
@@ -441,6 +504,16 @@ phi4_status smc_init(const phi4_config* cfg, void* d_workspace, size_t workspace
     return fail(e, "look-ahead stream");
   if ((e = cudaEventCreateWithFlags(&r->evA, cudaEventDisableTiming)) != cudaSuccess) return fail(e, "event");
   if ((e = cudaEventCreateWithFlags(&r->evB, cudaEventDisableTiming)) != cudaSuccess) return fail(e, "event");
+  if (r->Z2) {
+    if ((e = cudaStreamCreateWithFlags(&r->s_norm, cudaStreamNonBlocking)) != cudaSuccess) return fail(e, "stream");
+    if ((e = cudaStreamCreateWithFlags(&r->s_gemm, cudaStreamNonBlocking)) != cudaSuccess) return fail(e, "stream");
+    for (int q = 0; q < 2; ++q) {
+      if ((e = cudaEventCreateWithFlags(&r->ev_n[q], cudaEventDisableTiming)) != cudaSuccess) return fail(e, "event");
+      if ((e = cudaEventCreateWithFlags(&r->ev_g[q], cudaEventDisableTiming)) != cudaSuccess) return fail(e, "event");
+      if ((e = cudaEventCreateWithFlags(&r->ev_a[q], cudaEventDisableTiming)) != cudaSuccess) return fail(e, "event");
+    }
+    if ((e = cudaEventCreateWithFlags(&r->ev_start, cudaEventDisableTiming)) != cudaSuccess) return fail(e, "event");
+  }
   if ((e = cudaMemsetAsync(r->scal, 0, SC_COUNT * 8, s)) != cudaSuccess) return fail(e, "memset");
   if ((e = cudaMemsetAsync(r->status, 0, 16, s)) != cudaSuccess) return fail(e, "memset");
   if ((e = launch_normals(cfg->seed, cfg->stream_id, RNG_INIT, 0, 0, 0, cfg->N, r->D, r->D, r->dtype, r->phi, s)) !=
@@ -589,12 +662,9 @@ phi4_status smc_free(phi4_run* r) {
   }
   for (auto e : r->pool) cudaEventDestroy(e);
   r->upd_timer.release();
-  if (r->side) {
-    cudaStreamSynchronize(r->side);
-    cudaStreamDestroy(r->side);
-  }
-  if (r->evA) cudaEventDestroy(r->evA);
-  if (r->evB) cudaEventDestroy(r->evB);
+  r->norm_timer.release();
+  r->gemm_timer.release();
+  release_streams(r);
   delete r;
   return PHI4_OK;
 }

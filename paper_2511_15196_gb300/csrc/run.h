@@ -8,9 +8,10 @@
 static const char* const kStageNames[PHI4_N_STAGES] = {"bisect_reweight", "resample", "gather", "covariance",
                                                  "cholesky",        "normals",  "propose", "accept",
                                                  "observables",     "ns_select", "ns_slice", "other",
-                                                 "chol_update"};
+                                                 "chol_update",     "mutation"};
 enum { STG_BISECT, STG_RESAMPLE, STG_GATHER, STG_COV, STG_CHOL, STG_NORMALS, STG_PROPOSE, STG_ACCEPT, STG_OBS,
-       STG_NS_SELECT, STG_NS_SLICE, STG_OTHER, STG_CHOL_UPDATE /* kernel-level, inside STG_CHOL */ };
+       STG_NS_SELECT, STG_NS_SLICE, STG_OTHER, STG_CHOL_UPDATE /* kernel-level, inside STG_CHOL */,
+       STG_MUTATION /* wall time of the n_mcmc sweeps (their stages overlap on three streams) */ };
 
 // Device scalars of a run (one 256-byte block).
 enum { SC_OUT = 0 /* 8 doubles: bisection results */, SC_KAHAN = 8 /* 2 */, SC_BETA = 10, SC_RIDGE = 11,
@@ -46,6 +47,13 @@ struct phi4_run {
   std::vector<cudaEvent_t> pool;
   double stage_ms[PHI4_N_STAGES] = {0};
   phi4::LaunchTimer upd_timer;  // the tensor-core trailing-update launches (STG_CHOL_UPDATE)
+  // pipelined sweeps of the mixed form: normals and proposal GEMM of sweep t+1 run on
+  // their own streams while sweep t's accept runs on `stream`
+  void* Z2 = nullptr;                 // second normals buffer
+  cudaStream_t s_norm = nullptr, s_gemm = nullptr;
+  cudaEvent_t ev_n[2] = {nullptr, nullptr}, ev_g[2] = {nullptr, nullptr}, ev_a[2] = {nullptr, nullptr};
+  cudaEvent_t ev_start = nullptr;
+  phi4::LaunchTimer norm_timer, gemm_timer;  // STG_NORMALS / STG_PROPOSE on those streams
   int64_t kernel_launches = 0;  // kernels this run has launched
   int ridge_level = 0;          // decades above chol_jitter_rel that made the last Cholesky succeed
   void* chol_aux = nullptr;     // diagonal-block inverses of the blocked Cholesky
@@ -103,11 +111,16 @@ inline void collect_stage_times(phi4_run* r) {
     r->pool.push_back(rec.b);
   }
   r->pending.clear();
-  const double before = r->upd_timer.ms;
-  const int64_t nb = r->upd_timer.launches;
-  r->upd_timer.collect();
-  r->stage_ms[STG_CHOL_UPDATE] += r->upd_timer.ms - before;
-  r->stage_launches[STG_CHOL_UPDATE] += r->upd_timer.launches - nb;
+  auto take = [&](phi4::LaunchTimer& tm, int stage) {
+    const double before = tm.ms;
+    const int64_t nb = tm.launches;
+    tm.collect();
+    r->stage_ms[stage] += tm.ms - before;
+    r->stage_launches[stage] += tm.launches - nb;
+  };
+  take(r->upd_timer, STG_CHOL_UPDATE);
+  take(r->norm_timer, STG_NORMALS);
+  take(r->gemm_timer, STG_PROPOSE);
 }
 
 
