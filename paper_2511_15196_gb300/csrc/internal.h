@@ -89,6 +89,8 @@ struct LaunchTimer {
       if (cudaEventElapsedTime(&t, pr.first, pr.second) == cudaSuccess) {
         ms += t;
         launches += 1;
+      } else {
+        (void)cudaGetLastError();  // a failed query must not surface at an unrelated call
       }
       pool.push_back(pr.first);
       pool.push_back(pr.second);
