@@ -143,12 +143,15 @@ def test_free_field_precision_forms_bf16():
     assert np.isfinite(res[p.MIXED_BF16][:, 0]).all() and exact == pytest.approx(-185.9853908122, abs=1e-9)
 
 
-@pytest.mark.parametrize("L", [16, 10], ids=["pipelined_sweeps", "sequential_sweeps"])
-def test_mixed_runs_are_deterministic(L):
+@pytest.mark.parametrize("L,N", [(16, 2048), (20, 300), (10, 2048)],
+                         ids=["pipelined_sweeps", "pipelined_ragged", "sequential_sweeps"])
+def test_mixed_runs_are_deterministic(L, N):
     # L % 4 == 0: the sweeps' normals, proposal GEMM and accept overlap on three streams
     # with double-buffered normals and increments; a buffer reused before its reader
-    # finished would make two identical runs differ. L = 10 takes the sequential path.
-    cfg = gpu_cfg(L=L, N=2048, n_mcmc=6, precision=p.MIXED_BF16, seed=5)
+    # finished would make two identical runs differ. L = 20, N = 300: D = 400 and an odd
+    # number of 128-row tiles (the GEMM's two-CTA clusters pad the last pair). L = 10
+    # takes the sequential path.
+    cfg = gpu_cfg(L=L, N=N, n_mcmc=6, precision=p.MIXED_BF16, seed=5)
     runs = [p.Run(cfg) for _ in range(2)]
     for _ in range(3):
         b = [r.temper_step() for r in runs]
