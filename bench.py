@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=2048, help="particles in the oracle's bounded sample")
-    ap.add_argument("--workload", default="single", choices=["single", "batch"],
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "kernels"],
                     help="single: one L=64 run; batch: 64 independent runs of mixed lattice sizes")
     ap.add_argument("--batch-runs", type=int, default=64)
     return ap.parse_args()
@@ -120,6 +120,39 @@ def run_batch(a):
     b.close()
     if dist is not None:
         dist.destroy_process_group()
+    return 0
+
+
+def run_kernels(a):
+    """The hot kernels one by one at the benchmark size, through the kernel-level C ABI, for
+    ncu captures (no timing, no JSON line): two proposal GEMMs, two fused accepts, two FP64
+    Cholesky factorisations of a 4096 x 4096 SPD matrix, three bf16 normal draws."""
+    import torch
+    import paper_2511_15196_gb300 as p
+    N, L = 8192, 64
+    D = L * L
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    phi = 0.5 * torch.randn(N, D, device="cuda", generator=g)
+    Lc = torch.tril(0.02 * torch.randn(D, D, device="cuda", dtype=torch.float64, generator=g)) + \
+        0.3 * torch.eye(D, device="cuda", dtype=torch.float64)
+    Lb = Lc.to(torch.bfloat16)
+    for i in range(2):
+        p.rw_propose(phi, Lb, p.MIXED_BF16, 2.38 / L, 1, 0, 1, i)
+    S, sq = p.action(phi, L, -4.0, 8.0)
+    ell = -S + 0.5 * sq
+    delta = (0.01 * torch.randn(N, D, device="cuda", generator=g)).half()
+    for i in range(2):
+        p.rw_accept_delta(phi.clone(), delta, L, -4.0, 8.0, S.clone(), sq.clone(), ell.clone(), 0.02, 1, 0, 1, i)
+    A = torch.randn(D, D, device="cuda", dtype=torch.float64, generator=g) * 0.01
+    A = A @ A.T + torch.eye(D, device="cuda", dtype=torch.float64)
+    for i in range(2):
+        p.cholesky(A.clone(), 1e-8)
+    Zb = torch.empty(N, D, dtype=torch.bfloat16, device="cuda")
+    for i in range(3):
+        p.philox_normals(Zb, 7, 0, p.RNG_PROPOSE, 1, i)
+    torch.cuda.synchronize()
+    print("kernels workload done")
     return 0
 
 
@@ -276,6 +309,8 @@ def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
+    if a.workload == "kernels":
+        return run_kernels(a)
     if a.workload == "batch":
         return run_batch(a)
     import torch
@@ -394,28 +429,36 @@ def main():
     run.close()
 
     if not a.no_e2e:
-        # the same metric through the public API with host buffers: every step copies the
-        # population in from pinned host memory and reads beta and log Z back
-        r2 = p.Run(cfg)
-        host = r2.particles().cpu().pin_memory()
-        for _ in range(2):
-            r2.load_particles(host)
-            r2.temper_step()
+        # the same metric through the public API with the population held in pinned host
+        # memory: the same run (seed, warm-up steps) as the device-timed one, and every
+        # timed step copies the population in (H2D), advances one temperature, copies the
+        # new population out (D2H) and reads log Z back
+        r2 = fresh()
+        r2.set_stage_timing(False)
+        for _ in range(a.warmup):
+            if r2.temper_step() >= 1.0:
+                r2 = fresh()
+        host = torch.empty((a.N, D), dtype=torch.float64 if prec == 0 else torch.float32).pin_memory()
+        r2.copy_particles(host)
         torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
         t0 = time.perf_counter()
         n_done = 0
-        for _ in range(max(2, a.steps // 2)):
+        for _ in range(a.steps):
             r2.load_particles(host)
             b = r2.temper_step()
+            r2.copy_particles(host)
             lz = r2.log_evidence()
             n_done += 1
             if b >= 1.0:
                 break
         torch.cuda.synchronize()
         e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+        nbytes = host.numel() * host.element_size()
         line["e2e"] = {"value": world * units_per_step * n_done / e2e_s, "unit": "site-updates/s",
-                       "h2d_bytes_per_step": host.numel() * host.element_size(), "d2h_bytes_per_step": 8 + 16,
-                       "steps": n_done}
+                       "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 16, "steps": n_done,
+                       "ms_per_step": e2e_s * 1e3 / n_done}
         del lz
         r2.close()
     if rank == 0 and not a.no_cpu_baseline:

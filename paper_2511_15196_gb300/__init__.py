@@ -223,6 +223,11 @@ class Run:
     def load_particles(self, src):
         _check(lib().smc_load_particles(self.handle, _ptr(src), src.numel() * src.element_size()))
 
+    def copy_particles(self, dst):
+        """Copy the current fields into `dst` (a host or device tensor of N x D elements)."""
+        _check(lib().smc_copy_particles(self.handle, _ptr(dst), dst.numel() * dst.element_size()))
+        return dst
+
     def kernel_launches(self):
         n = ctypes.c_int64()
         _check(lib().phi4_kernel_launches(self.handle, ctypes.byref(n)))

@@ -119,9 +119,10 @@ cudaError_t launch_cholesky(double* a, int D, const double* ridge, uint32_t* sta
                             cudaStream_t side = nullptr, cudaEvent_t evA = nullptr, cudaEvent_t evB = nullptr,
                             int mode = 0, LaunchTimer* timer = nullptr);
 // A22 -= P P^T from the digit planes of the panel P (kernels_tc.cu), on the 64-column
-// blocks [blk_lo, blk_hi) of the trailing matrix (blk_hi >= 2^20: to the end)
+// blocks [blk_lo, blk_hi) of the trailing matrix (blk_hi >= 2^20: to the end);
+// leave_sms: the bulk update beside the look-ahead chain keeps a few SMs free for it
 cudaError_t launch_chol_update_tc(double* a, int D, int b0, int m, const void* planes, int m_pad, const int* rexp,
-                                  int blk_lo, int blk_hi, uint32_t* status, cudaStream_t s);
+                                  int blk_lo, int blk_hi, bool leave_sms, uint32_t* status, cudaStream_t s);
 int cholesky_launches(int D);  // kernels one launch_cholesky enqueues
 // float factorisation of the lower triangle of sigma (copied into a) for the plain FP32 form
 cudaError_t launch_cholesky_f32(const double* sigma, float* a, int D, const double* ridge, uint32_t* status,

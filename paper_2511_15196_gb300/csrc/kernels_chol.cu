@@ -498,7 +498,7 @@ static cudaError_t cholesky_t(T* a, int D, const double* ridge, void* aux, uint3
     if (tcu) {
       cudaEvent_t t0 = timer ? timer->begin(st) : nullptr;
       const cudaError_t e = launch_chol_update_tc((double*)a, D, b0, D - b0, planes[kb % 3], m_pad, rexp[kb % 3], lo,
-                                                  hi >= below ? (1 << 20) : hi, status, st);
+                                                  hi >= below ? (1 << 20) : hi, ahead && lo >= 1, status, st);
       if (timer) timer->end(st, t0);
       return e;
     }

@@ -689,7 +689,7 @@ cudaError_t launch_syrk_tc(const void* XcTb, int ldx, int D, int N, double inv_n
 }
 
 cudaError_t launch_chol_update_tc(double* a, int D, int b0, int m, const void* planes, int m_pad, const int* rexp,
-                                  int blk_lo, int blk_hi, uint32_t* status, cudaStream_t s) {
+                                  int blk_lo, int blk_hi, bool leave_sms, uint32_t* status, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
   CUtensorMap ma, mb;
   if (!tc::make_map(&ma, planes, 64, 8 * m_pad, 64, emu::BM) || !tc::make_map(&mb, planes, 64, 8 * m_pad, 64, emu::BN))
@@ -723,8 +723,7 @@ cudaError_t launch_chol_update_tc(double* a, int D, int b0, int m, const void* p
     const char* v = getenv("PHI4_CHOL_UPDATE_RESERVE");
     return v ? std::max(0, atoi(v)) : 32;
   }();
-  const bool bulk = blk_hi - blk_lo > 1;
-  const int avail = bulk ? std::max(1, sm_count() - reserve) : sm_count();
+  const int avail = leave_sms ? std::max(1, sm_count() - reserve) : sm_count();
   const int grid = std::min(avail, p.num_tiles);
   emu::chol_update_kernel<<<grid, emu::NUM_THREADS, emu::SMEM_BYTES, s>>>(ma, mb, p);
   return cudaGetLastError();
