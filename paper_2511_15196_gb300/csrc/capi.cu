@@ -64,14 +64,14 @@ phi4_status check_config(const phi4_config* c) {
 
 // The run's own streams and events (the caller's stream is not touched).
 void release_streams(phi4_run* r) {
-  for (cudaStream_t* st : {&r->side, &r->s_norm, &r->s_gemm})
+  for (cudaStream_t* st : {&r->side, &r->s_norm, &r->s_gemm, &r->s_acc})
     if (*st) {
       cudaStreamSynchronize(*st);
       cudaStreamDestroy(*st);
       *st = nullptr;
     }
   for (cudaEvent_t* ev : {&r->evA, &r->evB, &r->ev_n[0], &r->ev_n[1], &r->ev_g[0], &r->ev_g[1], &r->ev_a[0],
-                          &r->ev_a[1], &r->ev_start})
+                          &r->ev_a[1], &r->ev_start, &r->ev_done})
     if (*ev) {
       cudaEventDestroy(*ev);
       *ev = nullptr;
@@ -305,10 +305,11 @@ phi4_status step_front(phi4_run* r, bool single_cta_bisect) {
 
 // Back of a temperature: the n_mcmc random-walk sweeps (normals, proposal, accept).
 // In the mixed form on L % 4 == 0 lattices the increment Delta = s Z L^T does not
-// depend on the fields, so sweep t+1's normals (stream s_norm, ALU-bound) and proposal
-// GEMM (stream s_gemm, tensor cores) run while sweep t's accept (the run's stream,
-// HBM-bound) runs: Z and Delta are double-buffered (Delta in the two halves of the
-// proposal buffer) and events order each buffer's writer after its last reader. The
+// depend on the fields, so sweep t+1's normals (stream s_norm, ALU-bound, lowest
+// priority) and proposal GEMM (stream s_gemm, tensor cores) run while sweep t's
+// accept (stream s_acc, HBM-bound, highest priority: it carries the fields' chain)
+// runs: Z and Delta are double-buffered (Delta in the two halves of the proposal
+// buffer) and events order each buffer's writer after its last reader. The
 // arithmetic of every sweep is unchanged.
 phi4_status step_back(phi4_run* r) {
   const phi4_config& c = r->cfg;
@@ -324,8 +325,11 @@ phi4_status step_back(phi4_run* r) {
     CUDA_TRY(cudaEventRecord(r->ev_start, s));  // the factor and the fields are ready
     CUDA_TRY(cudaStreamWaitEvent(r->s_norm, r->ev_start, 0));
     CUDA_TRY(cudaStreamWaitEvent(r->s_gemm, r->ev_start, 0));
+    CUDA_TRY(cudaStreamWaitEvent(r->s_acc, r->ev_start, 0));
+    cudaStream_t sa = r->s_acc;
     LaunchTimer* tn = r->timing ? &r->norm_timer : nullptr;
     LaunchTimer* tg = r->timing ? &r->gemm_timer : nullptr;
+    LaunchTimer* ta = r->timing ? &r->acc_timer : nullptr;
     // (normals on the GEMM's stream, i.e. only the accept overlapped, measured slower)
     cudaStream_t sn = r->s_norm;
     for (int sweep = 0; sweep < c.n_mcmc; ++sweep) {
@@ -344,17 +348,18 @@ phi4_status step_back(phi4_run* r) {
       CUDA_TRY(launch_propose_tc(Db[q], Zb[q], r->ldz, r->Lg, r->ldl, N, D, (float)r->scale, r->status, r->s_gemm));
       if (tg) tg->end(r->s_gemm, a1);
       CUDA_TRY(cudaEventRecord(r->ev_g[q], r->s_gemm));
-      // the accept chain on the run's stream
-      CUDA_TRY(cudaStreamWaitEvent(s, r->ev_g[q], 0));
-      {
-        StageScope sc(r, STG_ACCEPT);
-        CUDA_TRY(launch_accept_delta((float*)r->phi, Db[q], ap, c.keep_reference, r->S, r->sq, r->ell,
-                                     r->scal + SC_BETA, c.seed, c.stream_id, t, (uint32_t)sweep, r->acc_count,
-                                     r->status, s));
-      }
-      CUDA_TRY(cudaEventRecord(r->ev_a[q], s));
+      // the accept chain
+      CUDA_TRY(cudaStreamWaitEvent(sa, r->ev_g[q], 0));
+      cudaEvent_t a2 = ta ? ta->begin(sa) : nullptr;
+      CUDA_TRY(launch_accept_delta((float*)r->phi, Db[q], ap, c.keep_reference, r->S, r->sq, r->ell,
+                                   r->scal + SC_BETA, c.seed, c.stream_id, t, (uint32_t)sweep, r->acc_count,
+                                   r->status, sa));
+      if (ta) ta->end(sa, a2);
+      CUDA_TRY(cudaEventRecord(r->ev_a[q], sa));
       r->kernel_launches += 3;
     }
+    CUDA_TRY(cudaEventRecord(r->ev_done, sa));  // the last accept follows every GEMM and normals draw
+    CUDA_TRY(cudaStreamWaitEvent(s, r->ev_done, 0));
     r->n_evals += (int64_t)N * c.n_mcmc;
     return PHI4_OK;
   }
@@ -505,8 +510,15 @@ phi4_status smc_init(const phi4_config* cfg, void* d_workspace, size_t workspace
   if ((e = cudaEventCreateWithFlags(&r->evA, cudaEventDisableTiming)) != cudaSuccess) return fail(e, "event");
   if ((e = cudaEventCreateWithFlags(&r->evB, cudaEventDisableTiming)) != cudaSuccess) return fail(e, "event");
   if (r->Z2) {
-    if ((e = cudaStreamCreateWithFlags(&r->s_norm, cudaStreamNonBlocking)) != cudaSuccess) return fail(e, "stream");
-    if ((e = cudaStreamCreateWithFlags(&r->s_gemm, cudaStreamNonBlocking)) != cudaSuccess) return fail(e, "stream");
+    // block scheduling favours the accept chain, then the GEMM, then the normals
+    const int mid_prio = (lo_prio + hi_prio) / 2;
+    if ((e = cudaStreamCreateWithPriority(&r->s_norm, cudaStreamNonBlocking, lo_prio)) != cudaSuccess)
+      return fail(e, "stream");
+    if ((e = cudaStreamCreateWithPriority(&r->s_gemm, cudaStreamNonBlocking, mid_prio)) != cudaSuccess)
+      return fail(e, "stream");
+    if ((e = cudaStreamCreateWithPriority(&r->s_acc, cudaStreamNonBlocking, hi_prio)) != cudaSuccess)
+      return fail(e, "stream");
+    if ((e = cudaEventCreateWithFlags(&r->ev_done, cudaEventDisableTiming)) != cudaSuccess) return fail(e, "event");
     for (int q = 0; q < 2; ++q) {
       if ((e = cudaEventCreateWithFlags(&r->ev_n[q], cudaEventDisableTiming)) != cudaSuccess) return fail(e, "event");
       if ((e = cudaEventCreateWithFlags(&r->ev_g[q], cudaEventDisableTiming)) != cudaSuccess) return fail(e, "event");
@@ -664,6 +676,7 @@ phi4_status smc_free(phi4_run* r) {
   r->upd_timer.release();
   r->norm_timer.release();
   r->gemm_timer.release();
+  r->acc_timer.release();
   release_streams(r);
   delete r;
   return PHI4_OK;

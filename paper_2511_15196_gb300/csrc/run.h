@@ -50,7 +50,10 @@ struct phi4_run {
   // pipelined sweeps of the mixed form: normals and proposal GEMM of sweep t+1 run on
   // their own streams while sweep t's accept runs on `stream`
   void* Z2 = nullptr;                 // second normals buffer
-  cudaStream_t s_norm = nullptr, s_gemm = nullptr;
+  // accept (the fields' chain, highest priority), GEMM, normals (lowest priority)
+  cudaStream_t s_norm = nullptr, s_gemm = nullptr, s_acc = nullptr;
+  cudaEvent_t ev_done = nullptr;
+  phi4::LaunchTimer acc_timer;  // STG_ACCEPT on s_acc
   cudaEvent_t ev_n[2] = {nullptr, nullptr}, ev_g[2] = {nullptr, nullptr}, ev_a[2] = {nullptr, nullptr};
   cudaEvent_t ev_start = nullptr;
   phi4::LaunchTimer norm_timer, gemm_timer;  // STG_NORMALS / STG_PROPOSE on those streams
@@ -121,6 +124,7 @@ inline void collect_stage_times(phi4_run* r) {
   take(r->upd_timer, STG_CHOL_UPDATE);
   take(r->norm_timer, STG_NORMALS);
   take(r->gemm_timer, STG_PROPOSE);
+  take(r->acc_timer, STG_ACCEPT);
 }
 
 

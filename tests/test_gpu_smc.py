@@ -28,8 +28,10 @@ def oracle_cfg(**kw):
     return SMCConfig(**base)
 
 
-@pytest.mark.parametrize("L,N", [(8, 1024), (1, 64), (2, 256), (12, 300)])
+@pytest.mark.parametrize("L,N", [(8, 1024), (1, 64), (2, 256), (12, 300), (16, 512), (20, 300)])
 def test_fp64_steps_match_oracle(L, N):
+    # L = 16, 20 (D = 256, 400): the factorisation uses the tensor-core trailing update and
+    # the look-ahead schedule (D = 400 with a ragged last block)
     run = p.Run(gpu_cfg(L=L, N=N, n_mcmc=4, seed=3))
     ref = SMC(oracle_cfg(L=L, N=N, n_mcmc=4, seed=3))
     for _ in range(3):
