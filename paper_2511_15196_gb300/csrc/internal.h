@@ -144,8 +144,10 @@ cudaError_t launch_propose_tc(void* delta_f16, const void* Zb, int ldz, const vo
                               float scale, uint32_t* status, cudaStream_t s);
 // prop = phi + float(delta) elementwise (float fields)
 cudaError_t launch_apply_delta(const float* phi, const void* delta_f16, float* prop, long long n, cudaStream_t s);
-cudaError_t launch_syrk_tc(const void* XcTb, int ldx, int D, int N, double inv_nm1, double* sigma,
-                           uint32_t* status, cudaStream_t s);
+// Sigma = 2^(-s_i - s_j) (2^(2a) H H^T + 2^a (H L^T + L H^T) + L L^T) / (N - 1) on the
+// lower triangle, exact digit products on the tensor cores (H, L: D x N bf16 digit planes).
+cudaError_t launch_gram_tc(const void* H, const void* Lo, int ldx, int D, int N, const int* shift, int a,
+                           double inv_nm1, double* sigma, uint32_t* status, cudaStream_t s);
 
 // kernels_ns.cu
 cudaError_t launch_ns_select(const double* logl, int N, int k, int32_t* order, double* ns, double* dead,

@@ -1,7 +1,14 @@
 // Particle covariance (App. A: a single covariance re-estimated from the
 // population at every outer step): column means, centred and transposed copy
-// Xc^T (in the GEMM operand type), Sigma = Xc^T Xc / (N - 1) on the lower
-// triangle, and the ridge delta = jitter_rel * trace(Sigma) / D.
+// Xc^T, Sigma = Xc^T Xc / (N - 1) on the lower triangle, and the ridge
+// delta = jitter_rel * trace(Sigma) / D.
+// FP64 and FP32 forms: Xc^T in the state type and a SIMT SYRK. Mixed form: Xc^T as
+// two planes of fixed-point digits per site and an exact Gram matrix on the tensor
+// cores (launch_gram_tc): the computed Sigma is the covariance of the rounded fields,
+// positive semi-definite by construction, where bf16 operands with fp32 sums over N
+// terms perturb it by ~sqrt(N) 2^-24 of sum |x||y| and make a nearly singular
+// covariance indefinite.
+#include <algorithm>
 #include "internal.h"
 #include "common.cuh"
 
@@ -62,6 +69,90 @@ __global__ void center_transpose_kernel(const T* __restrict__ phi, int N, int D,
   }
 }
 
+// Mixed form: per site j the mean (as colmean) and the shift s_j = B - e_j, where
+// 2^(e_j - 1) <= max_n |phi_nj - mean_j| < 2^e_j (from the column's extrema), so that
+// every centred field scaled by 2^s_j lies within 2^B.
+__global__ void __launch_bounds__(kColTile* kRowLanes) colstats_kernel(const float* __restrict__ phi, int N, int D,
+                                                                       int B, double* __restrict__ mean,
+                                                                       int* __restrict__ shift) {
+  __shared__ double part[kRowLanes][kColTile];
+  __shared__ float pmin[kRowLanes][kColTile], pmax[kRowLanes][kColTile];
+  const int tx = threadIdx.x % kColTile, ty = threadIdx.x / kColTile;
+  const int j = blockIdx.x * kColTile + tx;
+  KahanF k;
+  float lo = INFINITY, hi = -INFINITY;
+  if (j < D) {
+    for (int n = ty; n < N; n += kRowLanes) {
+      const float v = phi[(size_t)n * D + j];
+      k.add(v);
+      lo = fminf(lo, v);
+      hi = fmaxf(hi, v);
+    }
+  }
+  part[ty][tx] = k.value();
+  pmin[ty][tx] = lo;
+  pmax[ty][tx] = hi;
+  __syncthreads();
+  if (ty == 0 && j < D) {
+    double t = 0.0;
+    for (int r = 0; r < kRowLanes; ++r) {
+      t += part[r][tx];
+      lo = fminf(lo, pmin[r][tx]);
+      hi = fmaxf(hi, pmax[r][tx]);
+    }
+    const double mu = t / N;
+    mean[j] = mu;
+    const double dev = fmax((double)hi - mu, mu - (double)lo);
+    int e = 0;
+    if (dev > 0.0) frexp(dev, &e);
+    shift[j] = dev > 0.0 ? B - e : 0;
+  }
+}
+
+// Digit planes of the mixed form: x = phi_nj - mean_j (in float, the mean as a
+// float pair), v = rint(x 2^s_j) with |v| <= 2^B, h = rint(v 2^-a), l = v - 2^a h
+// (|l| <= 2^(a-1), |h| <= 2^(B-a)); H[j][n] = h, Lo[j][n] = l as exact bf16 integers,
+// transposed through a 32 x 32 shared tile.
+__global__ void center_digits_kernel(const float* __restrict__ phi, int N, int D, const double* __restrict__ mean,
+                                     const int* __restrict__ shift, int a, __nv_bfloat16* __restrict__ H,
+                                     __nv_bfloat16* __restrict__ Lo, int ldx) {
+  __shared__ float th[32][33], tl[32][33];
+  __shared__ float mhi[32], mlo[32];
+  __shared__ int sh[32];
+  const int n0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  if (tid < 32) {
+    const int j = j0 + tid;
+    const double mu = j < D ? mean[j] : 0.0;
+    const float m1 = (float)mu;
+    mhi[tid] = m1;
+    mlo[tid] = (float)(mu - (double)m1);
+    sh[tid] = j < D ? shift[j] : 0;
+  }
+  __syncthreads();
+  const float pa = ldexpf(1.f, a), ra = ldexpf(1.f, -a);
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int n = n0 + r, j = j0 + threadIdx.x;
+    float h = 0.f, l = 0.f;
+    if (n < N && j < D) {
+      const float x = (phi[(size_t)n * D + j] - mhi[threadIdx.x]) - mlo[threadIdx.x];
+      const float v = rintf(ldexpf(x, sh[threadIdx.x]));
+      h = rintf(v * ra);
+      l = fmaf(-h, pa, v);
+    }
+    th[r][threadIdx.x] = h;
+    tl[r][threadIdx.x] = l;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int j = j0 + r, n = n0 + threadIdx.x;
+    if (n < N && j < D) {
+      H[(size_t)j * ldx + n] = __float2bfloat16_rn(th[threadIdx.x][r]);
+      Lo[(size_t)j * ldx + n] = __float2bfloat16_rn(tl[threadIdx.x][r]);
+    }
+  }
+}
+
 __global__ void ridge_kernel(const double* __restrict__ sigma, int D, double jitter_rel, double* __restrict__ ridge) {
   __shared__ double red[64];
   double s = 0.0;
@@ -77,7 +168,7 @@ size_t covariance_scratch_bytes(int N, int D, int precision) {
   if (precision == 0) return mean + align256((size_t)D * N * sizeof(double));
   if (precision == 1) return mean + align256((size_t)D * N * sizeof(float));
   const size_t ldx = ((size_t)N + 7) & ~(size_t)7;
-  return mean + align256((size_t)D * ldx * 2);
+  return mean + align256((size_t)D * sizeof(int)) + 2 * align256((size_t)D * ldx * 2);
 }
 
 cudaError_t launch_covariance(const void* phi, int precision, int N, int D, double* sigma, void* scratch,
@@ -96,17 +187,24 @@ cudaError_t launch_covariance(const void* phi, int precision, int N, int D, doub
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return launch_syrk_simt(xct, 0, D, N, N, inv, sigma, s);
   }
-  colmean_kernel<float><<<mgrid, kColTile * kRowLanes, 0, s>>>((const float*)phi, N, D, mean);
   if (precision == 1) {
+    colmean_kernel<float><<<mgrid, kColTile * kRowLanes, 0, s>>>((const float*)phi, N, D, mean);
     center_transpose_kernel<float, float><<<tgrid, tblock, 0, s>>>((const float*)phi, N, D, mean, (float*)xct, N);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return launch_syrk_simt(xct, 1, D, N, N, inv, sigma, s);
   }
+  // mixed: B = 23 - ceil(log2 N) (at most 14) keeps every digit-product sum within 2^23
+  int c = 0;
+  while ((1 << c) < N) ++c;
+  const int B = std::min(14, 23 - c), a = (B + 1) / 2;
   const int ldx = (N + 7) & ~7;
-  center_transpose_kernel<float, __nv_bfloat16>
-      <<<tgrid, tblock, 0, s>>>((const float*)phi, N, D, mean, (__nv_bfloat16*)xct, ldx);
+  int* shift = (int*)(base + align256((size_t)D * sizeof(double)));
+  __nv_bfloat16* H = (__nv_bfloat16*)((unsigned char*)shift + align256((size_t)D * sizeof(int)));
+  __nv_bfloat16* Lo = H + align256((size_t)D * ldx * 2) / 2;
+  colstats_kernel<<<mgrid, kColTile * kRowLanes, 0, s>>>((const float*)phi, N, D, B, mean, shift);
+  center_digits_kernel<<<tgrid, tblock, 0, s>>>((const float*)phi, N, D, mean, shift, a, H, Lo, ldx);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return launch_syrk_tc(xct, ldx, D, N, inv, sigma, status, s);
+  return launch_gram_tc(H, Lo, ldx, D, N, shift, a, inv, sigma, status, s);
 }
 
 cudaError_t launch_ridge(const double* sigma, int D, double jitter_rel, double* ridge, cudaStream_t s) {

@@ -1,15 +1,15 @@
-// tcgen05 tensor-core GEMM with TMA operand staging (sm_103a), for the one
-// dense contraction of the sampler:
+// tcgen05 tensor-core kernels with TMA operand staging (sm_103a):
 //   proposal   increment Delta = s Z L^T stored as fp16 (Z: N x D normals, L: D x D
 //              lower Cholesky factor; a 256-column tile [n0, n0+256) only needs
-//              k < n0+256); the accept kernel forms Phi + Delta while it loads Phi, and
-//   covariance Sigma = Xc^T Xc / (N-1) on the lower triangle (Xc^T: D x N).
-// Both operands are bf16, K-contiguous, loaded by TMA into 128B-swizzled shared
-// tiles; one elected thread issues tcgen05.mma (M=128, N=256, K=16, fp32
-// accumulate) into one of two TMEM accumulators while four epilogue warps drain
-// the other one with tcgen05.ld and apply the epilogue to global memory.
+//              k < n0+256); the accept kernel forms Phi + Delta while it loads Phi;
+//   covariance the mixed form's Sigma as the exact Gram matrix of fixed-point digits
+//              (namespace gram);
+//   Cholesky   the FP64 trailing update, exactly emulated with bf16 digits (namespace emu).
+// Operands are bf16, K-contiguous, loaded by TMA into 128B-swizzled shared tiles; one
+// elected thread issues tcgen05.mma (fp32 accumulate) into TMEM while epilogue warps
+// drain the accumulators with tcgen05.ld and apply the epilogue to global memory.
 // Persistent CTAs (one per SM) walk a static tile list; warp 0 = TMA producer,
-// warp 1 = MMA issuer (and TMEM owner), warps 2..5 = epilogue.
+// warp 1 = MMA issuer (and TMEM owner), the other warps = epilogue.
 // Every mbarrier wait is bounded (about one second); a wait that gives up sets
 // ST_TIMEOUT and an abort flag that stops the other roles.
 #include <cuda.h>
@@ -40,8 +40,6 @@ struct Params {
   int tiles_m, tiles_n, num_tiles;
   __half* delta;
   float scale;
-  double* sigma;
-  double inv;
   uint32_t* status;
 };
 
@@ -155,30 +153,15 @@ template <int MODE>
 __host__ __device__ constexpr int cluster_size() { return MODE == 0 ? 2 : 1; }
 
 // Work unit u -> this CTA's tile (mb, nb) and number of K blocks. Proposal units are
-// pairs of row tiles (rank 0 and 1 of the cluster) on one column tile.
+// pairs of row tiles (rank 0 and 1 of the cluster) on one column tile, column tiles in
+// decreasing K extent (heaviest first).
 template <int MODE>
 PHI4_DEV void get_tile(const Params& p, int u, int rank, int& mb, int& nb, int& kblocks) {
-  if (MODE == 0) {
-    // proposal: column tiles in decreasing K extent (heaviest first)
-    const int pm = (p.tiles_m + 1) / 2;
-    nb = p.tiles_n - 1 - u / pm;
-    mb = (u % pm) * 2 + rank;
-    const int kend = min(p.K, (nb + 1) * BN);
-    kblocks = (kend + BK - 1) / BK;
-  } else {
-    // covariance: tiles that touch the lower triangle, row-block by row-block
-    int m = 0, base = 0;
-    for (;;) {
-      const int cnt = min(p.tiles_n, (m * BM + BM - 1) / BN + 1);
-      if (u < base + cnt) break;
-      base += cnt;
-      ++m;
-    }
-    mb = m;
-    nb = u - base;
-    kblocks = (p.K + BK - 1) / BK;
-    (void)rank;
-  }
+  const int pm = (p.tiles_m + 1) / 2;
+  nb = p.tiles_n - 1 - u / pm;
+  mb = (u % pm) * 2 + rank;
+  const int kend = min(p.K, (nb + 1) * BN);
+  kblocks = (kend + BK - 1) / BK;
 }
 
 template <int MODE>
@@ -297,35 +280,26 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         tmem_ld32(trow + (uint32_t)(c * 32), v);
         const int gn0 = nb * BN + c * 32;
         if (gm < p.M && gn0 < p.Nn) {
-          if (MODE == 0) {
-            const size_t o = (size_t)gm * p.Nn + gn0;
-            if (gn0 + 32 <= p.Nn && (p.Nn & 7) == 0) {
-              uint4* dst = reinterpret_cast<uint4*>(p.delta + o);
+          const size_t o = (size_t)gm * p.Nn + gn0;
+          if (gn0 + 32 <= p.Nn && (p.Nn & 7) == 0) {
+            uint4* dst = reinterpret_cast<uint4*>(p.delta + o);
 #pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                uint4 pk;
-                __half2 h0 = __floats2half2_rn(p.scale * v[8 * j], p.scale * v[8 * j + 1]);
-                __half2 h1 = __floats2half2_rn(p.scale * v[8 * j + 2], p.scale * v[8 * j + 3]);
-                __half2 h2 = __floats2half2_rn(p.scale * v[8 * j + 4], p.scale * v[8 * j + 5]);
-                __half2 h3 = __floats2half2_rn(p.scale * v[8 * j + 6], p.scale * v[8 * j + 7]);
-                pk.x = *reinterpret_cast<uint32_t*>(&h0);
-                pk.y = *reinterpret_cast<uint32_t*>(&h1);
-                pk.z = *reinterpret_cast<uint32_t*>(&h2);
-                pk.w = *reinterpret_cast<uint32_t*>(&h3);
-                dst[j] = pk;
-              }
-            } else {
-#pragma unroll
-              for (int j = 0; j < 32; ++j)
-                if (gn0 + j < p.Nn) p.delta[o + j] = __float2half_rn(p.scale * v[j]);
+            for (int j = 0; j < 4; ++j) {
+              uint4 pk;
+              __half2 h0 = __floats2half2_rn(p.scale * v[8 * j], p.scale * v[8 * j + 1]);
+              __half2 h1 = __floats2half2_rn(p.scale * v[8 * j + 2], p.scale * v[8 * j + 3]);
+              __half2 h2 = __floats2half2_rn(p.scale * v[8 * j + 4], p.scale * v[8 * j + 5]);
+              __half2 h3 = __floats2half2_rn(p.scale * v[8 * j + 6], p.scale * v[8 * j + 7]);
+              pk.x = *reinterpret_cast<uint32_t*>(&h0);
+              pk.y = *reinterpret_cast<uint32_t*>(&h1);
+              pk.z = *reinterpret_cast<uint32_t*>(&h2);
+              pk.w = *reinterpret_cast<uint32_t*>(&h3);
+              dst[j] = pk;
             }
           } else {
-            double* row = p.sigma + (size_t)gm * p.Nn;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int gn = gn0 + j;
-              if (gn < p.Nn && gn <= gm) row[gn] = (double)v[j] * p.inv;
-            }
+            for (int j = 0; j < 32; ++j)
+              if (gn0 + j < p.Nn) p.delta[o + j] = __float2half_rn(p.scale * v[j]);
           }
         }
       }
@@ -401,6 +375,206 @@ static cudaError_t launch(const CUtensorMap& a, const CUtensorMap& b, const Para
 }
 
 }  // namespace tc
+
+// ---------------------------------------------------------------------------
+// Mixed-form covariance as an exact Gram matrix on the tensor cores.
+// The centred fields of site j are rounded to integers v = rint(x 2^s_j), |v| <= 2^B,
+// and split into two digits v = 2^a h + l (small integers, exact in bf16); the digit
+// planes H and L are D x N, K-contiguous. Three TMEM accumulators per 128 x 128 tile
+// collect  G_hh = H H^T,  G_x = H L^T + L H^T  and  G_ll = L L^T  over the whole K = N:
+// with N <= 2^c and B = 23 - c (a = ceil(B/2)) every partial sum is an integer of
+// magnitude <= 2^23, so the fp32 accumulation is exact and
+//   Sigma_ij = 2^(-s_i - s_j) (2^(2a) G_hh + 2^a G_x + G_ll) / (N - 1)
+// is the covariance of the rounded fields up to one final FP64 rounding: positive
+// semi-definite like the matrix it stands for, so the factorisation's ridge only has
+// to absorb the Cholesky's own rounding. The combination is done in 64-bit integers
+// and turned into a double with integer operations; one FP64 multiply per element.
+// Persistent CTAs walk the lower tiles; warp 0 = TMA (four 16 KB digit tiles per
+// stage), warp 1 = MMA (four MMAs per K step), warps 2..9 = epilogue (the tile's three
+// accumulators use 384 of the 512 TMEM columns, so the next tile's MMAs wait for the
+// epilogue to drain them).
+namespace gram {
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 3;
+constexpr int TILE_BYTES = BM * BK * 2;
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;  // A_H, A_L, B_H, B_L
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int NUM_THREADS = 320;
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+struct Params {
+  int D, K, num_tiles, a;
+  const int* shift;
+  double inv;
+  double* sigma;
+  uint32_t* status;
+};
+
+// lower tile u (row block by row block: row block m holds tiles 0..m)
+PHI4_DEV void get_tile(int u, int& mb, int& nb) {
+  int m = 0;
+  while (u > m) {
+    u -= m + 1;
+    ++m;
+  }
+  mb = m;
+  nb = u;
+}
+
+// t 2^n as a double (exact for |t| < 2^53), built with integer operations.
+PHI4_DEV double i64_pow2(long long t, int n) {
+  if (t == 0) return 0.0;
+  const unsigned long long sg = t < 0 ? 0x8000000000000000ull : 0ull;
+  const unsigned long long u = t < 0 ? (unsigned long long)(-t) : (unsigned long long)t;
+  const int lz = __clzll(u);
+  const int ex = 1023 + (63 - lz) + n;
+  if (ex <= 0 || ex >= 2047) return ldexp((double)t, n);
+  const unsigned long long man = (u << (lz - 11)) & 0x000FFFFFFFFFFFFFull;
+  return __longlong_as_double((long long)(sg | ((unsigned long long)ex << 52) | man));
+}
+
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    gram_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CUtensorMap tmL, Params p) {
+  using namespace tc;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;
+  uint64_t* tempty = tfull + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(tfull, 1);
+    mbar_init(tempty, 8);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmH) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmL) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const int kblocks = (p.K + BK - 1) / BK;
+  auto give_up = [&]() {
+    *abort_flag = 1;
+    atomicOr(p.status, ST_TIMEOUT);
+  };
+  if (warp == 0) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      for (int u = blockIdx.x; u < p.num_tiles && !*abort_flag; u += gridDim.x) {
+        int mb, nb;
+        get_tile(u, mb, nb);
+        for (int kb = 0; kb < kblocks; ++kb) {
+          if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) { give_up(); break; }
+          uint8_t* st = smem + stage * STAGE_BYTES;
+          mbar_expect_tx(&full[stage], STAGE_BYTES);
+          tma_load_2d(&tmH, &full[stage], st, kb * BK, mb * BM);
+          tma_load_2d(&tmL, &full[stage], st + TILE_BYTES, kb * BK, mb * BM);
+          tma_load_2d(&tmH, &full[stage], st + 2 * TILE_BYTES, kb * BK, nb * BN);
+          tma_load_2d(&tmL, &full[stage], st + 3 * TILE_BYTES, kb * BK, nb * BN);
+          if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0, tphase = 0;
+      const uint32_t t_hh = tmem_base, t_x = tmem_base + BN, t_ll = tmem_base + 2 * BN;
+      for (int u = blockIdx.x; u < p.num_tiles && !*abort_flag; u += gridDim.x) {
+        // the epilogue has read the previous tile's accumulators
+        if (!mbar_wait(tempty, tphase ^ 1u, abort_flag)) { give_up(); break; }
+        tc_fence_after();
+        bool ok = true;
+        for (int kb = 0; kb < kblocks; ++kb) {
+          if (!mbar_wait(&full[stage], phase, abort_flag)) { give_up(); ok = false; break; }
+          tc_fence_after();
+          const uint32_t s0 = smem_u32(smem + stage * STAGE_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t ah = sdesc(s0 + kk * 32), al = sdesc(s0 + TILE_BYTES + kk * 32);
+            const uint64_t bh = sdesc(s0 + 2 * TILE_BYTES + kk * 32), bl = sdesc(s0 + 3 * TILE_BYTES + kk * 32);
+            const uint32_t acc = (kb | kk) != 0;
+            umma_idesc(t_hh, ah, bh, IDESC, acc);
+            umma_idesc(t_x, ah, bl, IDESC, acc);
+            umma_idesc(t_x, al, bh, IDESC, 1u);
+            umma_idesc(t_ll, al, bl, IDESC, acc);
+          }
+          umma_commit(&empty[stage]);
+          if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+        }
+        if (!ok) break;
+        umma_commit(tfull);
+        tphase ^= 1u;
+      }
+    }
+  } else {
+    // warps 2..9: lane quarter q of the accumulators, columns [grp * 64, grp * 64 + 64)
+    const int q = warp & 3, grp = (warp - 2) >> 2;
+    const int r = q * 32 + lane;
+    const int a = p.a;
+    uint32_t tphase = 0;
+    for (int u = blockIdx.x; u < p.num_tiles; u += gridDim.x) {
+      int mb, nb;
+      get_tile(u, mb, nb);
+      if (!mbar_wait(tfull, tphase, abort_flag)) { give_up(); break; }
+      tphase ^= 1u;
+      tc_fence_after();
+      const int gm = mb * BM + r;
+      const bool row_ok = gm < p.D;
+      const int si = row_ok ? p.shift[gm] : 0;
+      double* row = p.sigma + (size_t)(row_ok ? gm : 0) * p.D;
+      const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16);
+#pragma unroll 1
+      for (int c = 0; c < 2; ++c) {
+        const int col = grp * 64 + c * 32;
+        float hh[32], xx[32], ll[32];
+        tmem_ld32(trow + (uint32_t)col, hh);
+        tmem_ld32(trow + (uint32_t)(BN + col), xx);
+        tmem_ld32(trow + (uint32_t)(2 * BN + col), ll);
+        if (c == 1) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tempty);  // this warp's accumulators are in registers
+        }
+        const int gn0 = nb * BN + col;
+        if (row_ok) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int gn = gn0 + j;
+            if (gn <= gm) {
+              const long long t = ((long long)__float2int_rn(hh[j]) << (2 * a)) +
+                                  ((long long)__float2int_rn(xx[j]) << a) + (long long)__float2int_rn(ll[j]);
+              row[gn] = i64_pow2(t, -(si + p.shift[gn])) * p.inv;
+            }
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512) : "memory");
+  }
+}
+}  // namespace gram
 
 // ---------------------------------------------------------------------------
 // FP64 Cholesky trailing update on the tensor cores (exact digit emulation).
@@ -668,24 +842,26 @@ cudaError_t launch_propose_tc(void* delta_f16, const void* Zb, int ldz, const vo
   return tc::launch<0>(ma, mb, p, s);
 }
 
-cudaError_t launch_syrk_tc(const void* XcTb, int ldx, int D, int N, double inv_nm1, double* sigma, uint32_t* status,
-                           cudaStream_t s) {
-  CUtensorMap ma, mb;
-  if (!tc::make_map(&ma, XcTb, N, D, ldx, tc::BM) || !tc::make_map(&mb, XcTb, N, D, ldx, tc::BN))
+cudaError_t launch_gram_tc(const void* H, const void* Lo, int ldx, int D, int N, const int* shift, int a,
+                           double inv_nm1, double* sigma, uint32_t* status, cudaStream_t s) {
+  CUtensorMap mh, ml;
+  if (!tc::make_map(&mh, H, N, D, ldx, gram::BM) || !tc::make_map(&ml, Lo, N, D, ldx, gram::BM))
     return cudaErrorInvalidValue;
-  tc::Params p{};
-  p.M = D;
-  p.Nn = D;
+  const int tiles = (D + gram::BM - 1) / gram::BM;
+  gram::Params p{};
+  p.D = D;
   p.K = N;
-  p.tiles_m = (D + tc::BM - 1) / tc::BM;
-  p.tiles_n = (D + tc::BN - 1) / tc::BN;
-  int count = 0;
-  for (int m = 0; m < p.tiles_m; ++m) count += std::min(p.tiles_n, (m * tc::BM + tc::BM - 1) / tc::BN + 1);
-  p.num_tiles = count;
-  p.sigma = sigma;
+  p.num_tiles = tiles * (tiles + 1) / 2;
+  p.a = a;
+  p.shift = shift;
   p.inv = inv_nm1;
+  p.sigma = sigma;
   p.status = status;
-  return tc::launch<1>(ma, mb, p, s);
+  cudaError_t e = cudaFuncSetAttribute(gram::gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, gram::SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  const int grid = std::min(sm_count(), p.num_tiles);
+  gram::gram_kernel<<<grid, gram::NUM_THREADS, gram::SMEM_BYTES, s>>>(mh, ml, p);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_chol_update_tc(double* a, int D, int b0, int m, const void* planes, int m_pad, const int* rexp,

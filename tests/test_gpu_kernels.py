@@ -5,6 +5,8 @@ identical seeded inputs. Tolerances:
     dot-product bound gamma_K = K u / (1 - K u), u = 2^-24, on sum |a||b|;
   * bf16 tensor-core GEMMs: operand rounding 2 u_b + u_b^2 (u_b = 2^-8) plus gamma_K,
     both on sum |a||b|, plus the fp16 rounding u_h = 2^-11 of the stored increment;
+  * mixed covariance (exact Gram of fixed-point digits): the rounding of each centred
+    field to its site's grid, propagated through Xc^T Xc, plus one FP64 rounding;
   * integer and index results (resampling, gather): bit-exact.
 """
 import math
@@ -157,6 +159,32 @@ def _cov_bound_terms(X):
     return Xc, A
 
 
+def _digit_bits(N):
+    """Fixed-point width B of the mixed covariance: every sum of N digit products stays
+    within 2^23 (exact in the fp32 accumulators), at most two 7-bit digits."""
+    return min(14, 23 - int(math.ceil(math.log2(N))))
+
+
+def _mixed_cov_bound(X):
+    """|Sigma_gpu - Sigma| for the mixed covariance: each centred field moves by at most
+    E_nj = g_j (the grid step 2^(e_j - B) of its site, a full step so that an exponent
+    one larger on the device is covered) + float centring and mean errors; through
+    Xc^T Xc / (N - 1) that is (|Xc|^T E + E^T |Xc| + E^T E) / (N - 1), plus one FP64
+    rounding of the result."""
+    N = X.shape[0]
+    B = _digit_bits(N)
+    mu = X.mean(0)
+    Xc = X - mu
+    dev = np.abs(Xc).max(0)
+    e = np.frexp(dev)[1]
+    g = np.ldexp(1.0, e - B)
+    E = g[None, :] + 2.0 ** -20 * (np.abs(X) + np.abs(X).mean(0)[None, :])
+    A = np.abs(Xc)
+    M = (A.T @ E + E.T @ A + E.T @ E) / (N - 1)
+    _, ref = ocov.sample_covariance(X)
+    return M * 1.0001 + 2.0 ** -50 * np.abs(ref) + 1e-300
+
+
 @pytest.mark.parametrize("N,L", [(1000, 12), (257, 24), (4096, 32), (300, 3)])
 @pytest.mark.parametrize("precision", [p.FP64, p.FP32, p.MIXED_BF16], ids=["fp64", "fp32", "bf16"])
 def test_covariance(N, L, precision):
@@ -174,10 +202,52 @@ def test_covariance(N, L, precision):
     elif precision == p.FP32:
         bound = (2 * U32 + gamma(N)) * A[low] * 1.0001 + 1e-30
     else:
-        bound = (2 * UB + UB * UB + gamma(N)) * A[low] * 1.0001 + 1e-30
+        bound = _mixed_cov_bound(X)[low]
     assert (err <= bound).all(), (err / bound).max()
     # the strictly upper triangle is untouched
     assert (sig[np.triu_indices(D, 1)] == 0).all()
+
+
+@pytest.mark.parametrize("N,L", [(300, 32), (8192, 8), (2, 4)])
+def test_mixed_covariance_is_psd(N, L):
+    """The mixed covariance is the Gram matrix of the rounded fields: positive
+    semi-definite up to FP64 rounding, also when N <= D makes it singular (with bf16
+    operands and fp32 sums over N its null space would come out indefinite)."""
+    D = L * L
+    X = inputs.broken_phase_fields(N, D, seed=7 + N).astype(np.float32)
+    sig = p.covariance(cuda(X), p.MIXED_BF16).cpu().numpy()
+    S = np.tril(sig) + np.tril(sig, -1).T
+    w = np.linalg.eigvalsh(S)
+    assert w[0] >= -1e-13 * max(w[-1], 1e-300) * D, (w[0], w[-1])
+
+
+def test_mixed_covariance_exact_at_the_digit_bound():
+    """Fields whose digits reach the bound (|h| = 2^(B-a), |l| = 2^(a-1)) on N = 8192
+    particles, so that the digit-product sums reach 2^23: the device result equals the
+    exact Gram matrix of the rounded fields over N - 1, bit for bit."""
+    N, L = 8192, 8
+    D = L * L
+    B = _digit_bits(N)
+    a = (B + 1) // 2
+    assert (B, a) == (10, 5)
+    g = np.random.default_rng(11)
+    # per site one magnitude: 1 - 2^-11 rounds half-way up to v = 2^B (h = 32, l = 0);
+    # 1008/1024 gives v = 1008 (h = 32, l = -16); 0.5 + 2^-11 rounds half-way down to 512
+    mags = np.array([1.0 - 2.0 ** -11, 1008.0 / 1024.0, 0.5 + 2.0 ** -11])[np.arange(D) % 3]
+    signs = np.ones((N, D))
+    for j in range(D):  # exactly N/2 negative entries per site: the mean is exactly zero
+        signs[g.permutation(N)[: N // 2], j] = -1.0
+    X = (signs * mags[None, :]).astype(np.float32)
+    assert (X.astype(np.float64).sum(0) == 0).all()
+    sig = p.covariance(cuda(X), p.MIXED_BF16).cpu().numpy()
+    e = np.frexp(np.abs(X.astype(np.float64)).max(0))[1]
+    s = B - e
+    v = np.rint(np.ldexp(X.astype(np.float64), s[None, :])).astype(np.int64)
+    assert np.abs(v).max() == 2 ** B
+    G = v.T @ v  # exact integer Gram
+    want = np.ldexp(G.astype(np.float64), -(s[:, None] + s[None, :])) * (1.0 / (N - 1))
+    low = np.tril_indices(D)
+    np.testing.assert_array_equal(sig[low], want[low])
 
 
 # ------------------------------------------------------------------ Cholesky
