@@ -390,8 +390,8 @@ def main():
         # (pairs k + l <= 9 of eight 7-bit digits) of the 64-wide panel per lower element
         nb = (D + 63) // 64
         elems = sum((D - 64 * (kb + 1)) * (D - 64 * (kb + 1) + 1) // 2 for kb in range(nb - 1))
-        # per panel: the next block column and the rest (one column of look-ahead)
-        n_fact = n_l / max(sum(min(2, nb - kb - 1) for kb in range(nb - 1)), 1)
+        # one Cholesky stage per factorisation attempt
+        n_fact = stage_acc.get("cholesky", [0, 0])[1]
         units = 36 * 2 * 64 * elems * n_fact / max(n_l, 1)
         work = ("tensor", units, "TFLOP/s")
         extra = {"fp64_equivalent_tflops": 2 * 64 * elems * n_fact / (ms_tot * 1e-3) / 1e12,

@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kPotrfThreads) potrf_kernel(T* __restrict__ a,
       const T* lp = lcol[(j - 1) & 3];
       const T lj = j >= 1 ? lp[j] : (T)0;  // column 0 has no previous column (its ring slot is unwritten)
       T* lo = lcol[j & 3];
-      if (j < 32 && i0 >= j) {
+      if (j < 32 && i0 >= j && i0 < n) {
         const T c0 = i0 == j ? dj : (j >= 1 ? fma(-lp[i0], lj, S[i0][j]) : S[i0][j]);
         const T l0 = c0 * rd;
         lo[i0] = l0;

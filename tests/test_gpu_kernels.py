@@ -266,6 +266,23 @@ def test_cholesky_fp64(D, mode):
     assert (np.triu(Lg, 1) == 0).all()
 
 
+@pytest.mark.parametrize("mode", [1, 2], ids=["simt", "tc_emulated"])
+@pytest.mark.parametrize("D", [1, 5, 9, 144, 400])
+def test_cholesky_writes_nothing_past_the_matrix(D, mode):
+    """Last diagonal blocks narrower than a warp (D mod 64 < 32): the factorisation
+    writes only the D x D matrix (a guard band after it keeps its sentinel)."""
+    A = inputs.spd_matrix(D, seed=D + 1, cond=1e3)
+    guard = 8192
+    buf = torch.full((D * D + guard,), -7.25, dtype=torch.float64, device="cuda")
+    buf[: D * D] = torch.as_tensor(A.ravel(), device="cuda")
+    a = buf[: D * D].view(D, D)
+    a, st = p.cholesky(a, 1e-3, mode=mode)
+    assert int(st.cpu()[0]) == 0
+    assert (buf[D * D:] == -7.25).all()
+    ref = np.linalg.cholesky(A + 1e-3 * np.eye(D))
+    np.testing.assert_allclose(a.cpu().numpy(), ref, rtol=0, atol=1e-11 * np.abs(ref).max())
+
+
 @pytest.mark.parametrize("D", [384, 2048, 4096])
 def test_cholesky_tensor_update_matches_fp64(D):
     # the exact-digit tensor-core trailing update against the FP64 SIMT update and LAPACK
