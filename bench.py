@@ -387,9 +387,11 @@ def main():
     extra = {}
     if dom == "chol_update":
         # exact digit emulation of the FP64 update A22 -= P P^T: 36 bf16 digit-plane products
-        # (pairs k + l <= 9 of eight 7-bit digits) of the 64-wide panel per lower element
+        # (pairs k + l <= 9 of eight 7-bit digits) of the 64-wide panel per lower element;
+        # the timed launches are the bulk of each panel's update (the trailing matrix
+        # without the next block column, (m - 64)(m - 63)/2 lower elements)
         nb = (D + 63) // 64
-        elems = sum((D - 64 * (kb + 1)) * (D - 64 * (kb + 1) + 1) // 2 for kb in range(nb - 1))
+        elems = sum((D - 64 * (kb + 2)) * (D - 64 * (kb + 2) + 1) // 2 for kb in range(nb - 2))
         # one Cholesky stage per factorisation attempt
         n_fact = stage_acc.get("cholesky", [0, 0])[1]
         units = 36 * 2 * 64 * elems * n_fact / max(n_l, 1)

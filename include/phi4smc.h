@@ -183,12 +183,13 @@ phi4_status phi4_kernel_launches(const phi4_run* run, int64_t* out);
  * stage on the run's stream; phi4_stage_times returns accumulated milliseconds
  * and launch counts since the last reset, for stage ids 0..PHI4_N_STAGES-1
  * (names from phi4_stage_name). Synchronises the run's stream. Stage 12
- * ("chol_update") is kernel-level: event pairs around each tensor-core trailing
- * update launch of the Cholesky, on the stream it runs on; its time is part of
- * stage 4 ("cholesky"). In the mixed form the sweeps run on three streams
- * (normals and proposal GEMM of the next sweep beside the current accept): stages 5
- * and 6 are then kernel-level event pairs on their own streams and stage 13
- * ("mutation") is the wall time of all n_mcmc sweeps on the run's stream. */
+ * ("chol_update") is kernel-level: event pairs around the launch of the bulk of each
+ * tensor-core trailing update of the Cholesky (all but the next block column), on
+ * the stream it runs on; its time is part of stage 4 ("cholesky"). In the mixed form
+ * the sweeps run on three streams (normals and proposal GEMM of the next sweep
+ * beside the current accept): stages 5, 6 and 7 are then kernel-level event pairs on
+ * their own streams and stage 13 ("mutation") is the wall time of all n_mcmc sweeps
+ * on the run's stream. */
 #define PHI4_N_STAGES 14
 phi4_status phi4_set_stage_timing(phi4_run* run, int32_t enable);
 phi4_status phi4_stage_times(phi4_run* run, double* ms_out, int64_t* launches_out, int32_t reset);

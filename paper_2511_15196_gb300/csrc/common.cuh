@@ -21,6 +21,13 @@ constexpr long long kSpinLimitCycles = 2000000000LL;
 
 // CTA-scope mbarrier helpers (shared-memory barrier objects, phase parity waits).
 PHI4_DEV uint32_t cta_smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation waits here until the previous kernel of its stream has completed and
+// its writes are visible (immediately when launched without it); `pdl_trigger` lets
+// the next such kernel be launched before this one ends.
+PHI4_DEV void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+PHI4_DEV void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 PHI4_DEV void cta_mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(cta_smem_addr(bar)), "r"(count) : "memory");
 }

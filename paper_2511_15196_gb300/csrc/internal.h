@@ -114,7 +114,7 @@ cudaError_t launch_copy_lower(const double* src, double* dst, int D, cudaStream_
 // inverses. With side != nullptr the look-ahead schedule uses `side` and the two events.
 size_t cholesky_aux_bytes(int D);
 // mode: 0 automatic (tensor-core trailing update for D >= 256), 1 FP64 SIMT update, 2 tensor-core update
-// `timer` (optional) brackets every tensor-core trailing-update launch.
+// `timer` (optional) brackets every tensor-core launch of the bulk of a trailing update.
 cudaError_t launch_cholesky(double* a, int D, const double* ridge, uint32_t* status, void* aux, cudaStream_t s,
                             cudaStream_t side = nullptr, cudaEvent_t evA = nullptr, cudaEvent_t evB = nullptr,
                             int mode = 0, LaunchTimer* timer = nullptr);

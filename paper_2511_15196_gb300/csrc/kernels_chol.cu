@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(kPotrfThreads) potrf_kernel(T* __restrict__ a,
   __shared__ __align__(8) uint64_t barA[2], barB[2], barC[2];
   __shared__ int fail;
   __shared__ volatile int abort_flag;
+  pdl_wait();
   if (*status & ST_NOT_PD) return;
   const int n = min(NB, D - k0);
   const T r = ridge ? (T)*ridge : (T)0;
@@ -232,6 +233,7 @@ __global__ void __launch_bounds__(kPotrfThreads) potrf_kernel(T* __restrict__ a,
     }
   }
   __syncthreads();
+  pdl_trigger();  // the inverse may launch: only the zero fill and rdiag remain
   if (abort_flag) {
     if (tid == 0) atomicOr(status, ST_TIMEOUT);
     return;
@@ -261,6 +263,7 @@ __global__ void __launch_bounds__(kInvThreads) tri_inv_kernel(const T* __restric
                                                               const uint32_t* __restrict__ status) {
   __shared__ T Ls[NB][NB + 1];
   __shared__ T rds[NB];
+  pdl_wait();
   if (*status & ST_NOT_PD) return;
   const int n = min(NB, D - k0);
   const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
@@ -283,6 +286,7 @@ __global__ void __launch_bounds__(kInvThreads) tri_inv_kernel(const T* __restric
     if (m < 31) acc0 = fma(-Ls[i0][m], w, acc0);
     acc1 = fma(-Ls[i1][m], w, acc1);
   }
+  pdl_trigger();
 }
 
 // Exact digit split of one panel row for the tensor-core trailing update. The warp
@@ -344,6 +348,7 @@ __global__ void __launch_bounds__(256) trsm_gemm_kernel(T* __restrict__ a, int D
   extern __shared__ __align__(16) unsigned char chol_smem[];
   T(*Ws)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(chol_smem);
   T(*As)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(chol_smem + sizeof(T) * NB * (NB + 1));
+  pdl_wait();
   if (*status & ST_NOT_PD) return;
   const int n = min(NB, D - k0);
   const int r0 = k0 + n + blockIdx.x * kTrsmRows;
@@ -469,6 +474,23 @@ cudaError_t launch_copy_lower(const double* src, double* dst, int D, cudaStream_
 // the next block column's update and its diagonal/panel factorisation run on `side`
 // while `s` applies the rest of the trailing update (look-ahead); the arithmetic of
 // every tile is the same either way, so both schedules give identical results.
+// Launch with programmatic stream serialisation (the kernel calls pdl_wait first).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 template <typename T>
 static cudaError_t cholesky_t(T* a, int D, const double* ridge, void* aux, uint32_t* status, cudaStream_t s,
                               cudaStream_t side, cudaEvent_t evA, cudaEvent_t evB, bool tensor_update,
@@ -496,10 +518,12 @@ static cudaError_t cholesky_t(T* a, int D, const double* ridge, void* aux, uint3
     hi = std::min(hi, below);
     if (lo >= hi) return cudaSuccess;
     if (tcu) {
-      cudaEvent_t t0 = timer ? timer->begin(st) : nullptr;
+      // timed: the bulk of each update (an event between the next block column's update
+      // and the diagonal block would stop the latter's programmatic early launch)
+      cudaEvent_t t0 = timer && lo >= 1 ? timer->begin(st) : nullptr;
       const cudaError_t e = launch_chol_update_tc((double*)a, D, b0, D - b0, planes[kb % 3], m_pad, rexp[kb % 3], lo,
                                                   hi >= below ? (1 << 20) : hi, ahead && lo >= 1, status, st);
-      if (timer) timer->end(st, t0);
+      if (t0) timer->end(st, t0);
       return e;
     }
     long long g = 0;
@@ -510,19 +534,22 @@ static cudaError_t cholesky_t(T* a, int D, const double* ridge, void* aux, uint3
   const size_t sm_trsm = sizeof(T) * (NB + kTrsmRows) * (NB + 1);
   cudaError_t e0 = cudaFuncSetAttribute(trsm_gemm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_trsm);
   if (e0 != cudaSuccess) return e0;
+  // the chain's kernels are launched as programmatic dependents of their predecessors
+  // (each waits for it at entry), so their launch latency overlaps the predecessor
   auto panel = [&](int kb, cudaStream_t st) {
     const int k0 = kb * NB;
-    potrf_kernel<T><<<1, kPotrfThreads, 0, st>>>(a, D, k0, ridge, rdiag + (size_t)kb * NB, status);
+    launch_pdl(potrf_kernel<T>, 1, kPotrfThreads, 0, st, a, D, k0, ridge, rdiag + (size_t)kb * NB, status);
     const int rows = D - k0 - min(NB, D - k0);
     if (rows > 0) {
       // the inverse only feeds the panel solve
-      tri_inv_kernel<T><<<min(NB, D - k0), kInvThreads, 0, st>>>(a, D, k0, rdiag + (size_t)kb * NB, W + (size_t)kb * NB * NB,
-                                                        status);
+      launch_pdl(tri_inv_kernel<T>, min(NB, D - k0), kInvThreads, 0, st, (const T*)a, D, k0,
+                 (const T*)(rdiag + (size_t)kb * NB), W + (size_t)kb * NB * NB, (const uint32_t*)status);
       // with the tensor-core update the solve also writes the digit planes, for every
       // row of the update's 128-row tiles (rows >= `rows` get zeros)
       const int grid_rows = tcu ? (rows + 127) / 128 * 128 : rows;
-      trsm_gemm_kernel<T><<<(grid_rows + kTrsmRows - 1) / kTrsmRows, 256, sm_trsm, st>>>(
-          a, D, k0, W + (size_t)kb * NB * NB, status, tcu ? planes[kb % 3] : nullptr, rexp[kb % 3], m_pad);
+      launch_pdl(trsm_gemm_kernel<T>, (grid_rows + kTrsmRows - 1) / kTrsmRows, 256, sm_trsm, st, a, D, k0,
+                 (const T*)(W + (size_t)kb * NB * NB), (const uint32_t*)status,
+                 tcu ? planes[kb % 3] : (__nv_bfloat16*)nullptr, rexp[kb % 3], m_pad);
     }
   };
   panel(0, s);

@@ -590,7 +590,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 // Tiles of 128 rows x 32 columns of the lower trailing matrix (two tiles' group
 // accumulators fit in TMEM, so the MMAs of one tile overlap the epilogue of the
 // previous one); a launch covers the 64-column blocks [blk_lo, blk_hi) of the
-// trailing matrix.
+// trailing matrix, each CTA a contiguous run of its tile list, so that the 128 KB of
+// A digit planes are loaded once per 128-row band rather than once per tile.
 namespace emu {
 constexpr int BM = 128, BN = 32, KD = 64, ND = 8, NC = 8;
 constexpr int A_PLANE = BM * KD * 2;
@@ -659,6 +660,7 @@ constexpr int NUM_THREADS = 320;  // TMA warp, MMA warp, two epilogue warpgroups
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     chol_update_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Params p) {
   using namespace tc;
+  pdl_trigger();  // the diagonal block's kernel (one CTA) may launch and wait for this one
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
@@ -696,18 +698,25 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     *abort_flag = 1;
     atomicOr(p.status, ST_TIMEOUT);
   };
+  // a contiguous run of the tile list per CTA: consecutive tiles mostly share a band
+  const int chunk = (p.num_tiles + gridDim.x - 1) / gridDim.x;
+  const int u_lo = min(p.num_tiles, (int)blockIdx.x * chunk), u_hi = min(p.num_tiles, u_lo + chunk);
   if (warp == 0) {
     if (lane == 0) {
       uint32_t phase = 0;
-      for (int u = blockIdx.x; u < p.num_tiles && !*abort_flag; u += gridDim.x) {
+      int prev_mb = -1;
+      for (int u = u_lo; u < u_hi && !*abort_flag; ++u) {
         int mb, bj;
         get_tile(p, u, mb, bj);
         if (!mbar_wait(empty, phase ^ 1u, abort_flag)) { give_up(); break; }
-        mbar_expect_tx(full, SMEM_DATA);
+        // the band's A digit planes stay in shared memory while the band lasts
+        const bool load_a = mb != prev_mb;
+        mbar_expect_tx(full, load_a ? SMEM_DATA : ND * B_PLANE);
         for (int k = 0; k < ND; ++k) {
-          tma_load_2d(&tmA, full, sA + k * A_PLANE, 0, k * p.m_pad + mb * BM);
+          if (load_a) tma_load_2d(&tmA, full, sA + k * A_PLANE, 0, k * p.m_pad + mb * BM);
           tma_load_2d(&tmB, full, sB + k * B_PLANE, 0, k * p.m_pad + bj * BN);
         }
+        prev_mb = mb;
         phase ^= 1u;
       }
     }
@@ -715,7 +724,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     if (lane == 0) {
       uint32_t phase = 0, tph = 0;  // tph bit b: phase parity of accumulator set b
       int it = 0;
-      for (int u = blockIdx.x; u < p.num_tiles && !*abort_flag; u += gridDim.x, ++it) {
+      for (int u = u_lo; u < u_hi && !*abort_flag; ++u, ++it) {
         const int buf = it & 1;
         // the epilogue must have drained this accumulator set (two tiles back)
         if (!mbar_wait(tempty + buf, ((tph >> buf) & 1u) ^ 1u, abort_flag)) { give_up(); break; }
@@ -748,7 +757,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const int r = q * 32 + lane;
     uint32_t tph = 0;
     int it = 0;
-    for (int u = blockIdx.x; u < p.num_tiles; u += gridDim.x, ++it) {
+    for (int u = u_lo; u < u_hi; ++u, ++it) {
       const int buf = it & 1;
       int mb, bj;
       get_tile(p, u, mb, bj);
