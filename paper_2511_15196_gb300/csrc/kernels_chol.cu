@@ -341,7 +341,7 @@ __device__ __forceinline__ void split_row_digits(double x0, int c0, double x1, i
 // (the last diagonal block has no panel below it).
 constexpr int kTrsmRows = 8;
 template <typename T>
-__global__ void __launch_bounds__(256) trsm_gemm_kernel(T* __restrict__ a, int D, int k0, const T* __restrict__ W,
+__global__ void __launch_bounds__(kTrsmRows * 32) trsm_gemm_kernel(T* __restrict__ a, int D, int k0, const T* __restrict__ W,
                                                         const uint32_t* __restrict__ status,
                                                         __nv_bfloat16* __restrict__ planes, int* __restrict__ rexp,
                                                         int m_pad) {
@@ -547,7 +547,7 @@ static cudaError_t cholesky_t(T* a, int D, const double* ridge, void* aux, uint3
       // with the tensor-core update the solve also writes the digit planes, for every
       // row of the update's 128-row tiles (rows >= `rows` get zeros)
       const int grid_rows = tcu ? (rows + 127) / 128 * 128 : rows;
-      launch_pdl(trsm_gemm_kernel<T>, (grid_rows + kTrsmRows - 1) / kTrsmRows, 256, sm_trsm, st, a, D, k0,
+      launch_pdl(trsm_gemm_kernel<T>, (grid_rows + kTrsmRows - 1) / kTrsmRows, kTrsmRows * 32, sm_trsm, st, a, D, k0,
                  (const T*)(W + (size_t)kb * NB * NB), (const uint32_t*)status,
                  tcu ? planes[kb % 3] : (__nv_bfloat16*)nullptr, rexp[kb % 3], m_pad);
     }

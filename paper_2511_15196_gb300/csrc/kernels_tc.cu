@@ -611,6 +611,14 @@ struct Params {
   uint32_t* status;
 };
 
+// tcgen05.ld of 16 columns without the wait (the caller issues tmem_wait_ld before use)
+PHI4_DEV void tmem_ld16_nw(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(taddr));
+}
+PHI4_DEV void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 PHI4_DEV void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
@@ -777,24 +785,40 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         av[t] = (row_ok && jc < p.m && jc <= ir) ? arow[jc] : 0.0;
       }
       float hi[16], lo[16];
-      tmem_ld16(trow + (uint32_t)((NC - 1) * BN), hi);
-#pragma unroll
-      for (int t = 0; t < 16; ++t) lo[t] = 0.f;
-#pragma unroll 1
-      for (int c = NC; c >= 2; --c) {
-        float uu[16];
-        tmem_ld16(trow + (uint32_t)((c - 2) * BN), uu);
+      // (hi, lo) <- (hi, lo) 2^-7 + U  in double-float (TwoSum, then renormalise)
+      auto horner = [&](const uint32_t(&ur)[16]) {
 #pragma unroll
         for (int t = 0; t < 16; ++t) {
-          // (hi, lo) <- (hi, lo) 2^-7 + U_c  in double-float (TwoSum, then renormalise)
+          const float uu = __uint_as_float(ur[t]);
           const float h = hi[t] * 0.0078125f, l = lo[t] * 0.0078125f;
-          const float s = h + uu[t];
+          const float s = h + uu;
           const float bb = s - h;
-          const float err = (h - (s - bb)) + (uu[t] - bb);
+          const float err = (h - (s - bb)) + (uu - bb);
           const float l2 = l + err;
           const float hs = s + l2;
           lo[t] = l2 - (hs - s);
           hi[t] = hs;
+        }
+      };
+      {
+        // the eight group accumulators U_9 .. U_2, two loads in flight per wait
+        uint32_t r0[16], r1[16];
+        tmem_ld16_nw(trow + (uint32_t)((NC - 1) * BN), r0);
+        tmem_ld16_nw(trow + (uint32_t)((NC - 2) * BN), r1);
+        tmem_wait_ld();
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          hi[t] = __uint_as_float(r0[t]);
+          lo[t] = 0.f;
+        }
+        horner(r1);
+#pragma unroll 1
+        for (int g = NC - 3; g >= 0; g -= 2) {
+          tmem_ld16_nw(trow + (uint32_t)(g * BN), r0);
+          tmem_ld16_nw(trow + (uint32_t)((g - 1) * BN), r1);
+          tmem_wait_ld();
+          horner(r0);
+          horner(r1);
         }
       }
       tc_fence_before();
