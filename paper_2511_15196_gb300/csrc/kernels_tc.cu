@@ -148,6 +148,13 @@ PHI4_DEV void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// tcgen05.ld of 32 columns, no wait::ld (the caller waits before use)
+PHI4_DEV void tmem_ld32_nw(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+               : "r"(taddr));
+}
+
 // CTAs per cluster: the proposal's clusters of two share each B (factor) tile.
 template <int MODE>
 __host__ __device__ constexpr int cluster_size() { return MODE == 0 ? 2 : 1; }
@@ -543,10 +550,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll 1
       for (int c = 0; c < 2; ++c) {
         const int col = grp * 64 + c * 32;
-        float hh[32], xx[32], ll[32];
-        tmem_ld32(trow + (uint32_t)col, hh);
-        tmem_ld32(trow + (uint32_t)(BN + col), xx);
-        tmem_ld32(trow + (uint32_t)(2 * BN + col), ll);
+        uint32_t hh[32], xx[32], ll[32];
+        tmem_ld32_nw(trow + (uint32_t)col, hh);
+        tmem_ld32_nw(trow + (uint32_t)(BN + col), xx);
+        tmem_ld32_nw(trow + (uint32_t)(2 * BN + col), ll);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (c == 1) {
           tc_fence_before();
           __syncwarp();
@@ -558,8 +566,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           for (int j = 0; j < 32; ++j) {
             const int gn = gn0 + j;
             if (gn <= gm) {
-              const long long t = ((long long)__float2int_rn(hh[j]) << (2 * a)) +
-                                  ((long long)__float2int_rn(xx[j]) << a) + (long long)__float2int_rn(ll[j]);
+              const long long t = ((long long)__float2int_rn(__uint_as_float(hh[j])) << (2 * a)) +
+                                  ((long long)__float2int_rn(__uint_as_float(xx[j])) << a) +
+                                  (long long)__float2int_rn(__uint_as_float(ll[j]));
               row[gn] = i64_pow2(t, -(si + p.shift[gn])) * p.inv;
             }
           }
