@@ -164,3 +164,18 @@ def test_mixed_runs_are_deterministic(L, N):
     assert o[0]["acc_rate"] == o[1]["acc_rate"] and 0.0 < o[0]["acc_rate"] < 1.0
     for r in runs:
         r.close()
+
+
+def test_paper_mode_logz_L10():
+    # the paper's setting (Sec. 3, App. A): L = 10, Eq. (1) with factors 1/2, m^2 = -4,
+    # lambda = 1, target exp(-U_0 - S), N = 5000, n_MCMC = 3 V, ESS target 0.9. The
+    # library's log Z is log E_N(0,I)[exp(-S_E)] (about -36.65 here); the paper prints that
+    # value minus (V/4) log(pi) (checked at L = 10, 15, 18): Tables 1 and 3 give -65.26
+    # (SMC-RW), -65.20 / -65.4 (NS), -65.64 / -65.7 (SMC-HMC). Loose window +-0.5 around
+    # -65.4 (the paper's runs differ in seeds, float32 arithmetic and inner kernels).
+    from paper_2511_15196_gb300 import ess_sweep
+    row = ess_sweep.sweep([0.9], seeds=2)[0]
+    assert -65.9 < row["logz_paper_convention"] < -64.9, row
+    assert -37.2 < row["logz_mean"] < -36.1, row
+    assert row["logz_sd"] < 0.5, row
+    assert 0.5 < row["mode_balance"] < 2.0, row
