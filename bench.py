@@ -126,7 +126,8 @@ def run_batch(a):
 def run_kernels(a):
     """The hot kernels one by one at the benchmark size, through the kernel-level C ABI, for
     ncu captures (no timing, no JSON line): two proposal GEMMs, two fused accepts, two FP64
-    Cholesky factorisations of a 4096 x 4096 SPD matrix, three bf16 normal draws."""
+    Cholesky factorisations of a 4096 x 4096 SPD matrix, three bf16 normal draws, two mixed
+    covariances (exact Gram of fixed-point digits) of the 8192 x 4096 population."""
     import torch
     import paper_2511_15196_gb300 as p
     N, L = 8192, 64
@@ -151,6 +152,8 @@ def run_kernels(a):
     Zb = torch.empty(N, D, dtype=torch.bfloat16, device="cuda")
     for i in range(3):
         p.philox_normals(Zb, 7, 0, p.RNG_PROPOSE, 1, i)
+    for i in range(2):
+        p.covariance(phi, p.MIXED_BF16)
     torch.cuda.synchronize()
     print("kernels workload done")
     return 0
