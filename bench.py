@@ -403,13 +403,23 @@ def main():
                  "factorizations": n_fact}
     else:
         work = {
-            "propose": ("tensor", a.N * D * (D + 1), "TFLOP/s"),
+            # the mixed form's proposal runs on the tensor cores, the FP32 / FP64 forms' on the
+            # SIMT FMA units
+            "propose": ("tensor" if prec == 2 else "alu", a.N * D * (D + 1), "TFLOP/s"),
             "accept": ("hbm", a.N * D * ((4 + 2) if prec == 2 else (8 if prec == 0 else 4)) + a.N * D * acc *
                        (8 if prec == 0 else 4), "GB/s"),
             "normals": ("hbm", a.N * D * (2 if prec == 2 else 4 * (2 if prec == 0 else 1)), "GB/s"),
         }[dom]
     bound, units, unit = work
-    if unit == "TFLOP/s":
+    if unit == "TFLOP/s" and bound == "alu":
+        # derived from unit counts and the maximum SM clock (2070 MHz, 152 SMs): FP32, 128 FMA
+        # lanes per SM per cycle; FP64, one warp instruction per 64 cycles on each of the four
+        # sub-partitions (measured issue cost on this part), i.e. 2 lanes per SM per cycle
+        achieved = units / avg_s / 1e12
+        peak = 152 * 2070e6 * 2 * (128 if prec == 1 else 2) / 1e12
+        peak_src = "derived %s FMA peak (152 SMs x %s lanes/cycle x 2 flop x 2070 MHz)" % (
+            "FP32" if prec == 1 else "FP64", "128" if prec == 1 else "2")
+    elif unit == "TFLOP/s":
         achieved = units / avg_s / 1e12
         peak = bf16_s
         peak_src = "%s bf16 sustained (kernel timed inside a long step)" % src
