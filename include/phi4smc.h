@@ -74,7 +74,7 @@ typedef enum { PHI4_DT_F64 = 0, PHI4_DT_F32 = 1, PHI4_DT_BF16 = 2 } phi4_dtype;
 /* Stream kinds of the Philox counter word 0 (bits 24..31). */
 typedef enum {
   PHI4_RNG_INIT = 1, PHI4_RNG_RESAMPLE = 2, PHI4_RNG_PROPOSE = 3, PHI4_RNG_ACCEPT = 4,
-  PHI4_RNG_NS_START = 5, PHI4_RNG_NS_DIRECTION = 6, PHI4_RNG_NS_SLICE = 7
+  PHI4_RNG_NS_START = 5, PHI4_RNG_NS_DIRECTION = 6, PHI4_RNG_NS_SLICE = 7, PHI4_RNG_FLIP = 8
 } phi4_rng_kind;
 
 typedef struct {
@@ -98,8 +98,18 @@ typedef struct {
   uint64_t seed, stream_id;  /* Philox key material */
   int32_t chol_mode;         /* double Cholesky trailing update: 0 automatic (tensor cores for D >= 256),
                                 1 FP64 SIMT, 2 FP64-accurate exact-digit emulation on the tensor cores */
-  int32_t reserved;          /* zero */
+  int32_t flags;             /* PHI4_FLAG_* bits, 0 for the sampler as the paper runs it */
 } phi4_config;
+
+/* phi4_config.flags. Z2_FLIP (SMC): after each temperature's sweeps every particle is
+ * negated with probability 1/2 (one Philox bit per particle, stream kind
+ * PHI4_RNG_FLIP, counter (kind << 24 | temperature, 0, particle, 0), bit 0 of the first
+ * word). Every tempered target is even in phi (S is even and the reference N(0, I) is
+ * symmetric), so the global flip phi -> -phi is a Metropolis move accepted with
+ * probability 1; S, |phi|^2 and the log-weights are unchanged. The paper leaves such
+ * symmetry moves out of its black-box samplers (Sec. 2) and gives them to its AHMC
+ * control. */
+#define PHI4_FLAG_Z2_FLIP 1
 
 typedef struct {
   double beta;               /* current inverse temperature (SMC) */

@@ -34,6 +34,7 @@ KIND_ACCEPT = 4
 KIND_NS_START = 5
 KIND_NS_DIRECTION = 6
 KIND_NS_SLICE = 7
+KIND_FLIP = 8
 
 
 def philox4x32_10(c0, c1, c2, c3, k0, k1):

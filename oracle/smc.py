@@ -10,6 +10,8 @@ Outer step at temperature index t (t = 1, 2, ...), in the paper's order:
   4. re-estimate the particle covariance and its Cholesky factor (ridge level
      carried over from the previous step);
   5. n_mcmc random-walk Metropolis sweeps targeting gamma_{beta + dbeta};
+  5'. optionally (z2_flip) the global move phi -> -phi per particle with a Philox bit
+     (KIND_FLIP, t, 0, particle, 0), bit 0 of word 0;
   6. refresh ell from the cached S and |phi|^2.
 Initial particles are N(0, I_D) draws (KIND_INIT, 0, 0, particle, block).
 """
@@ -39,6 +41,7 @@ class SMCConfig:
     stream: int = 0
     normal_bits: int = 32          # 32: double-precision draws; 24: single-precision draws
     max_steps: int = 100000
+    z2_flip: bool = False          # global phi -> -phi move after each temperature's sweeps
 
     @property
     def D(self):
@@ -47,6 +50,19 @@ class SMCConfig:
     @property
     def scale(self):
         return self.rw_scale if self.rw_scale > 0 else mutation.rw_scale_default(self.D)
+
+
+def z2_flip(phi, seed, stream, t):
+    """Global symmetry move: particle n is negated when bit 0 of the first Philox word of
+    counter (KIND_FLIP << 24 | t, 0, n, 0) is set. The tempered targets are even in phi
+    (the action is a sum of even terms and the reference N(0, I) is symmetric), so the
+    move is a Metropolis proposal with acceptance ratio 1; S, |phi|^2 and the
+    log-weights are unchanged. (The paper gives such moves to its AHMC control only.)"""
+    w = philox.words(seed, stream, philox.KIND_FLIP, t, 0, np.arange(phi.shape[0]), [0])[:, 0, 0]
+    flip = (w & np.uint64(1)) == np.uint64(1)
+    out = phi.copy()
+    out[flip] = -out[flip]
+    return out
 
 
 class SMC:
@@ -95,6 +111,8 @@ class SMC:
                 self.phi, self.S, self.sq, Lc, c.scale, beta_new, c.L, c.m2, c.lam, c.c_kin, c.c_mass,
                 c.keep_reference, c.seed, c.stream, t, s, c.normal_bits)
             n_acc += int(acc.sum())
+        if c.z2_flip:
+            self.phi = z2_flip(self.phi, c.seed, c.stream, t)
         self.ell = lattice.tempering_loglik(self.S, self.sq, c.D, c.keep_reference)
         self.beta = beta_new
         rec = {"t": t, "beta": beta_new, "dbeta": dbeta, "ess": ess, "logz_inc": inc,

@@ -19,7 +19,8 @@ PHI4_OK, PHI4_ERR_ARG, PHI4_ERR_CUDA, PHI4_ERR_NOT_PD, PHI4_ERR_NONFINITE, PHI4_
 SMC_RW, NS_SLICE = 0, 1
 FP64, FP32, MIXED_BF16 = 0, 1, 2
 DT_F64, DT_F32, DT_BF16 = 0, 1, 2
-RNG_INIT, RNG_RESAMPLE, RNG_PROPOSE, RNG_ACCEPT, RNG_NS_START, RNG_NS_DIRECTION, RNG_NS_SLICE = range(1, 8)
+RNG_INIT, RNG_RESAMPLE, RNG_PROPOSE, RNG_ACCEPT, RNG_NS_START, RNG_NS_DIRECTION, RNG_NS_SLICE, RNG_FLIP = range(1, 9)
+FLAG_Z2_FLIP = 1
 N_STAGES = 14
 
 _STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_NOT_PD", 4: "ERR_NONFINITE", 5: "ERR_DONE",
@@ -41,7 +42,7 @@ class CConfig(ctypes.Structure):
                 ("ns_stop_frac", ctypes.c_double), ("chol_jitter_rel", ctypes.c_double),
                 ("bisect_iters", ctypes.c_int32), ("slice_max_shrink", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint64), ("chol_mode", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("flags", ctypes.c_int32)]
 
 
 class CObs(ctypes.Structure):
@@ -76,12 +77,14 @@ class Config:
     seed: int = 0
     stream_id: int = 0
     chol_mode: int = 0
+    flags: int = 0  # FLAG_Z2_FLIP: global phi -> -phi move after each temperature's sweeps
 
     def to_c(self):
         return CConfig(self.L, self.N, self.kind, self.precision, self.m2, self.lam, self.c_kin, self.c_mass,
                        int(bool(self.keep_reference)), self.n_mcmc, self.ess_target, self.rw_scale,
                        self.ns_n_delete, self.ns_slice_steps, self.ns_stop_frac, self.chol_jitter_rel,
-                       self.bisect_iters, self.slice_max_shrink, self.seed, self.stream_id, self.chol_mode, 0)
+                       self.bisect_iters, self.slice_max_shrink, self.seed, self.stream_id, self.chol_mode,
+                       self.flags)
 
 
 _lib = None
@@ -472,6 +475,20 @@ def rw_accept_delta(phi, delta, L, m2, lam, S, sq, ell, beta, seed, stream_id, s
                                       _ptr(S), _ptr(sq), _ptr(ell), _ptr(b), seed, stream_id, step, sweep, _ptr(cnt),
                                       _stream(stream)))
     return cnt
+
+
+def kappa_config(kappa, lam, **kw):
+    """Config for the kappa-parameterised action of App. G,
+        S = (kappa/2) sum_{x,mu} (phi_{x+mu} - phi_x)^2 + sum_x [phi_x^2 + lambda (phi_x^2 - 1)^2],
+    in the library's form: c_kin = kappa/2 (the kinetic sum equals sum_x sum_mu
+    phi_x (2 phi_x - phi_{x+mu} - phi_{x-mu})), c_mass = 1, m2 = 1 - 2 lambda, quartic lambda.
+    The dropped constant lambda V shifts log Z by kappa_logz_shift(lambda, V)."""
+    return Config(c_kin=0.5 * kappa, c_mass=1.0, m2=1.0 - 2.0 * lam, lam=lam, **kw)
+
+
+def kappa_logz_shift(lam, D):
+    """log Z of the kappa form minus log Z of its kappa_config run: -lambda V."""
+    return -lam * D
 
 
 def default_rw_scale(D):

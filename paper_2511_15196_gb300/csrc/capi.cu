@@ -59,6 +59,8 @@ phi4_status check_config(const phi4_config* c) {
   }
   ARG_CHECK(c->chol_jitter_rel >= 0.0 && isfinite(c->chol_jitter_rel), "chol_jitter_rel invalid");
   ARG_CHECK(c->chol_mode >= 0 && c->chol_mode <= 2, "chol_mode = %d unknown", c->chol_mode);
+  ARG_CHECK((c->flags & ~PHI4_FLAG_Z2_FLIP) == 0, "flags 0x%x: unknown bits", c->flags);
+  ARG_CHECK(!(c->flags & PHI4_FLAG_Z2_FLIP) || c->kind == PHI4_SMC_RW, "the Z2 flip move is an SMC move");
   return PHI4_OK;
 }
 
@@ -303,7 +305,7 @@ phi4_status step_front(phi4_run* r, bool single_cta_bisect) {
   return refit_enqueue(r, r->phi, N);
 }
 
-// Back of a temperature: the n_mcmc random-walk sweeps (normals, proposal, accept).
+// The n_mcmc random-walk sweeps of a temperature (normals, proposal, accept).
 // In the mixed form on L % 4 == 0 lattices the increment Delta = s Z L^T does not
 // depend on the fields, so sweep t+1's normals (stream s_norm, ALU-bound, lowest
 // priority) and proposal GEMM (stream s_gemm, tensor cores) run while sweep t's
@@ -311,7 +313,7 @@ phi4_status step_front(phi4_run* r, bool single_cta_bisect) {
 // runs: Z and Delta are double-buffered (Delta in the two halves of the proposal
 // buffer) and events order each buffer's writer after its last reader. The
 // arithmetic of every sweep is unchanged.
-phi4_status step_back(phi4_run* r) {
+static phi4_status step_sweeps(phi4_run* r) {
   const phi4_config& c = r->cfg;
   const int N = c.N, D = r->D;
   cudaStream_t s = r->stream;
@@ -388,6 +390,18 @@ phi4_status step_back(phi4_run* r) {
     r->kernel_launches += 1;
   }
   r->n_evals += (int64_t)N * c.n_mcmc;
+  return PHI4_OK;
+}
+
+// Back of a temperature: the sweeps, then (PHI4_FLAG_Z2_FLIP) the global Z2 move.
+phi4_status step_back(phi4_run* r) {
+  phi4_status ps = step_sweeps(r);
+  if (ps != PHI4_OK) return ps;
+  if (r->cfg.flags & PHI4_FLAG_Z2_FLIP) {
+    const int dt = r->cfg.precision == PHI4_FP64 ? PHI4_DT_F64 : PHI4_DT_F32;
+    CUDA_TRY(launch_z2_flip(r->cfg.seed, r->cfg.stream_id, (uint32_t)r->t, r->phi, dt, r->cfg.N, r->D, r->stream));
+    r->kernel_launches += 1;
+  }
   return PHI4_OK;
 }
 

@@ -33,6 +33,10 @@ cudaError_t launch_accept_delta(float* phi, const void* delta_f16, const ActionP
                                 double* S, double* sq, double* ell, const double* beta, uint64_t seed,
                                 uint64_t stream_id, uint32_t step, uint32_t sweep, uint32_t* acc_count,
                                 uint32_t* status, cudaStream_t s);
+// Z2 move: negate row n of phi (dtype 0 double, 1 float) when the Philox flip bit of
+// (RNG_FLIP, step, particle n) is set.
+cudaError_t launch_z2_flip(uint64_t seed, uint64_t stream_id, uint32_t step, void* phi, int dtype, int N, int D,
+                           cudaStream_t s);
 cudaError_t launch_magnetisation(const void* phi, int dtype, int N, int D, double* M, cudaStream_t s);
 
 // kernels_temper.cu

@@ -48,6 +48,33 @@ __global__ void normals_kernel(PhiloxKey key, uint32_t w0, uint32_t sub, int row
   }
 }
 
+// Global Z2 move: row n of phi is negated when bit 0 of the first Philox word of
+// counter (w0, 0, n, 0) is set. Grid (column chunks, rows); the row's bit is drawn once
+// per block.
+template <typename T>
+__global__ void z2_flip_kernel(PhiloxKey key, uint32_t w0, int N, int D, T* __restrict__ phi) {
+  __shared__ int flip;
+  const int n = blockIdx.y;
+  if (threadIdx.x == 0) flip = (int)(philox4x32_10(make_uint4(w0, 0u, (uint32_t)n, 0u), key).x & 1u);
+  __syncthreads();
+  if (!flip) return;
+  T* row = phi + (size_t)n * D;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < D; j += gridDim.x * blockDim.x) row[j] = -row[j];
+}
+
+cudaError_t launch_z2_flip(uint64_t seed, uint64_t stream_id, uint32_t step, void* phi, int dtype, int N, int D,
+                           cudaStream_t s) {
+  if (N <= 0 || D <= 0) return cudaSuccess;
+  const PhiloxKey key = philox_key(seed, stream_id);
+  const uint32_t w0 = counter_word0(RNG_FLIP, step);
+  const dim3 grid((unsigned)std::min((D + 255) / 256, 16), (unsigned)std::min(N, 65535));
+  if (N > 65535) return cudaErrorInvalidValue;
+  if (dtype == 0) z2_flip_kernel<double><<<grid, 256, 0, s>>>(key, w0, N, D, (double*)phi);
+  else if (dtype == 1) z2_flip_kernel<float><<<grid, 256, 0, s>>>(key, w0, N, D, (float*)phi);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_normals(uint64_t seed, uint64_t stream_id, uint32_t kind, uint32_t step, uint32_t sub,
                            int row0, int n_rows, int n_cols, int ld, int dtype, void* out, cudaStream_t s) {
   if (n_rows <= 0 || n_cols <= 0) return cudaSuccess;

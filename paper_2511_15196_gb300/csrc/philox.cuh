@@ -14,7 +14,7 @@ constexpr uint32_t kPhiloxM0 = 0xD2511F53u, kPhiloxM1 = 0xCD9E8D57u;
 constexpr uint32_t kPhiloxW0 = 0x9E3779B9u, kPhiloxW1 = 0xBB67AE85u;
 
 enum : uint32_t { RNG_INIT = 1, RNG_RESAMPLE = 2, RNG_PROPOSE = 3, RNG_ACCEPT = 4,
-                  RNG_NS_START = 5, RNG_NS_DIRECTION = 6, RNG_NS_SLICE = 7 };
+                  RNG_NS_START = 5, RNG_NS_DIRECTION = 6, RNG_NS_SLICE = 7, RNG_FLIP = 8 };
 
 struct PhiloxKey { uint32_t k0, k1; };
 

@@ -476,3 +476,16 @@ def test_accept_fp32_decisions():
     gacc = np.all(tphi.cpu().numpy() == prop, axis=1)
     assert (gacc[~near] == acc[~near]).all()
     assert 0.05 < acc.mean() < 0.95
+
+
+def test_kappa_config_action_on_the_gpu():
+    # the kappa form of App. G through kappa_config's coefficients, on the action kernel
+    g = np.random.default_rng(10)
+    L, kappa, lam = 8, 0.27, 0.8
+    phi = g.standard_normal((33, L * L))
+    cfg = p.kappa_config(kappa, lam, L=L, N=33)
+    S, _ = p.action(cuda(phi), L, cfg.m2, cfg.lam, cfg.c_kin, cfg.c_mass)
+    f = phi.reshape(33, L, L)
+    kin = sum(((np.roll(f, -1, axis=a) - f) ** 2).sum(axis=(1, 2)) for a in (1, 2))
+    s_kappa = 0.5 * kappa * kin + (f ** 2 + lam * (f ** 2 - 1.0) ** 2).sum(axis=(1, 2))
+    np.testing.assert_allclose(S.cpu().numpy() - p.kappa_logz_shift(lam, L * L), s_kappa, rtol=1e-12)

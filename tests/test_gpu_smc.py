@@ -50,6 +50,44 @@ def test_fp64_steps_match_oracle(L, N):
     run.close()
 
 
+@pytest.mark.parametrize("precision", [p.FP64, p.FP32], ids=["fp64", "fp32"])
+def test_z2_flip_matches_oracle(precision):
+    # the same particles flip on both sides (one Philox bit per particle and temperature)
+    L, N = 8, 512
+    run = p.Run(gpu_cfg(L=L, N=N, n_mcmc=3, seed=4, precision=precision, flags=p.FLAG_Z2_FLIP))
+    ref = SMC(oracle_cfg(L=L, N=N, n_mcmc=3, seed=4, z2_flip=True,
+                         normal_bits=32 if precision == p.FP64 else 24))
+    for _ in range(2):
+        run.temper_step()
+        ref.temper_step()
+        phi = run.particles().cpu().numpy().astype(np.float64)
+        if precision == p.FP64:
+            assert np.abs(phi - ref.phi).max() < 1e-8
+        else:
+            # float fields: the signs of the row means agree wherever the row mean is clear
+            Mg, Mo = phi.mean(axis=1), ref.phi.mean(axis=1)
+            clear = np.abs(Mo) > 1e-3
+            assert (np.sign(Mg[clear]) == np.sign(Mo[clear])).mean() > 0.99
+    run.close()
+
+
+def test_z2_flip_balances_the_modes_mixed():
+    # broken phase on the pipelined mixed path (L % 4 == 0)
+    run = p.Run(gpu_cfg(L=16, N=2048, n_mcmc=4, seed=6, precision=p.MIXED_BF16, flags=p.FLAG_Z2_FLIP))
+    for _ in range(4):
+        run.temper_step()
+    M = run.particles().cpu().numpy().mean(axis=1)
+    assert abs((M > 0).mean() - 0.5) < 4 * math.sqrt(0.25 / 2048)
+    run.close()
+
+
+def test_flags_are_checked():
+    with pytest.raises(RuntimeError):
+        p.Run(gpu_cfg(L=4, N=64, flags=2))
+    with pytest.raises(RuntimeError):
+        p.Run(gpu_cfg(L=4, N=64, kind=p.NS_SLICE, ns_n_delete=8, flags=p.FLAG_Z2_FLIP))
+
+
 def test_run_to_completion_and_done_status():
     run = p.Run(gpu_cfg(L=4, N=512, seed=1))
     obs = run.run()

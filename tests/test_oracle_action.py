@@ -85,3 +85,16 @@ def test_loglik_and_target():
     # log gamma_beta interpolates: beta = 0 is the reference log density up to a constant, beta = 1 is -S
     np.testing.assert_allclose(lattice.log_target(S, sq, 0.0), -0.5 * sq)
     np.testing.assert_allclose(lattice.log_target(S, sq, 1.0), -S)
+
+
+def test_kappa_form_maps_onto_the_action_coefficients():
+    # App. G: (kappa/2) sum_{x,mu} (phi_{x+mu} - phi_x)^2 + sum_x [phi_x^2 + lam (phi_x^2 - 1)^2]
+    # equals the library form with c_kin = kappa/2, c_mass = 1, m2 = 1 - 2 lam, plus lam V
+    g = np.random.default_rng(9)
+    L, kappa, lam = 5, 0.37, 1.3
+    phi = g.standard_normal((6, L * L))
+    f = phi.reshape(6, L, L)
+    kin = sum(((np.roll(f, -1, axis=a) - f) ** 2).sum(axis=(1, 2)) for a in (1, 2))
+    s_kappa = 0.5 * kappa * kin + (f ** 2 + lam * (f ** 2 - 1.0) ** 2).sum(axis=(1, 2))
+    s_lib = lattice.action(phi, L, 1.0 - 2.0 * lam, lam, 0.5 * kappa, 1.0)
+    np.testing.assert_allclose(s_lib + lam * L * L, s_kappa, rtol=1e-13)

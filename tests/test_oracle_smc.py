@@ -61,3 +61,32 @@ def test_z2_symmetry_and_determinism():
     assert abs(M.mean()) < 3.0 * absM.mean() / math.sqrt(1024 * 4) + 4 * M.std(ddof=1) / 2
     again = SMC(SMCConfig(seed=0, **cfg)).run()
     assert again == ms[0]
+
+
+def test_z2_flip_move_is_exact_and_keeps_the_evidence():
+    # the global move phi -> -phi leaves the action and |phi|^2 of every particle as they are
+    # (a sum of even terms) and flips about half of them, each with its own Philox bit
+    from oracle import lattice
+    from oracle.smc import z2_flip
+    g = np.random.default_rng(3)
+    phi = g.standard_normal((4096, 16)) + 0.7
+    out = z2_flip(phi, 11, 0, 5)
+    flipped = (out[:, 0] != phi[:, 0])
+    assert np.array_equal(out[flipped], -phi[flipped]) and np.array_equal(out[~flipped], phi[~flipped])
+    assert abs(flipped.mean() - 0.5) < 4 * math.sqrt(0.25 / 4096)
+    np.testing.assert_allclose(lattice.action(out, 4, -4.0, 8.0), lattice.action(phi, 4, -4.0, 8.0), rtol=1e-13)
+    assert not np.array_equal(z2_flip(phi, 11, 0, 6)[:, 0] != phi[:, 0], flipped)  # a new bit per temperature
+    # evidence of the 2 x 2 torus (transfer matrix) with the move on: unbiased as without it
+    lz = seeds_logz(dict(L=2, N=2048, m2=-4.0, lam=8.0, rho=0.9, n_mcmc=10, z2_flip=True), 6)
+    ref = exact("torus2", 2, -4.0, 8.0)
+    se = lz.std(ddof=1) / math.sqrt(len(lz))
+    assert abs(lz.mean() + 0.5 * lz.var(ddof=1) - ref) < 4.0 * se + 0.01
+
+
+def test_z2_flip_balances_the_modes():
+    # broken phase, L = 4: the final population's sign of M is balanced with the move
+    r = SMC(SMCConfig(L=4, N=2048, m2=-4.0, lam=8.0, rho=0.5, n_mcmc=5, seed=2, z2_flip=True))
+    r.run()
+    M = r.phi.mean(axis=1)
+    frac = (M > 0).mean()
+    assert abs(frac - 0.5) < 4 * math.sqrt(0.25 / 2048)
