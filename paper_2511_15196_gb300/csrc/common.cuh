@@ -76,6 +76,17 @@ PHI4_DEV bool cta_flag_wait_geq(const int* f, int target, volatile int* abort_fl
   }
 }
 
+// Progress counter in global memory between CTAs of one (co-resident) grid: release
+// store after the producer's writes, acquire loads by the consumers.
+PHI4_DEV void gpu_flag_release(int* f, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(f), "r"(v) : "memory");
+}
+PHI4_DEV int gpu_flag_acquire(const int* f) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+  return v;
+}
+
 PHI4_DEV double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

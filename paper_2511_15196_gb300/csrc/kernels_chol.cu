@@ -6,6 +6,7 @@
 // kernels see the bit and return.
 #include <math.h>
 #include <algorithm>
+#include <cstdlib>
 #include "internal.h"
 #include "common.cuh"
 
@@ -75,10 +76,13 @@ __device__ __forceinline__ int upd_warp_index(int warp) {  // -1: not an update 
     default: return -1;
   }
 }
+// The diagonal block's factorisation. With col_flag, column j of L and rsqrt(d_j) are
+// published behind a release store of j + 1 (the streamed inverse consumes them); -1
+// tells the consumers that the factorisation stopped.
 template <typename T>
-__global__ void __launch_bounds__(kPotrfThreads) potrf_kernel(T* __restrict__ a, int D, int k0,
-                                                              const double* __restrict__ ridge,
-                                                              T* __restrict__ rdiag, uint32_t* __restrict__ status) {
+__device__ __forceinline__ void potrf_body(T* __restrict__ a, int D, int k0, const double* __restrict__ ridge,
+                                           T* __restrict__ rdiag, uint32_t* __restrict__ status, int* col_flag,
+                                           int pub_every) {
   __shared__ T S[NB][NB + 1];
   __shared__ T lcol[4][NB];
   __shared__ T rds[NB];
@@ -90,8 +94,10 @@ __global__ void __launch_bounds__(kPotrfThreads) potrf_kernel(T* __restrict__ a,
   __shared__ __align__(8) uint64_t barA[2], barB[2], barC[2];
   __shared__ int fail;
   __shared__ volatile int abort_flag;
-  pdl_wait();
-  if (*status & ST_NOT_PD) return;
+  if (*status & ST_NOT_PD) {
+    if (col_flag && threadIdx.x == 0) gpu_flag_release(col_flag, -1);
+    return;
+  }
   const int n = min(NB, D - k0);
   const T r = ridge ? (T)*ridge : (T)0;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -183,6 +189,15 @@ __global__ void __launch_bounds__(kPotrfThreads) potrf_kernel(T* __restrict__ a,
       }
       __syncwarp();
       if (lane == 0) cta_mbar_arrive(&barB[j & 1]);
+      if (col_flag && (j % pub_every == pub_every - 1 || j == n - 1)) {
+        // columns up to j and their rsqrt(d) for the streamed inverse, pub_every at a time
+        // (a fence per column would sit on this warp's part of the pivot cycle)
+        const int j0 = j - j % pub_every;
+        if (lane <= j - j0) rdiag[j0 + lane] = rds[j0 + lane];
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) gpu_flag_release(col_flag, j + 1);
+      }
     }
   } else if (uw >= 0) {
     // ---- trailing update
@@ -233,13 +248,12 @@ __global__ void __launch_bounds__(kPotrfThreads) potrf_kernel(T* __restrict__ a,
     }
   }
   __syncthreads();
-  pdl_trigger();  // the inverse may launch: only the zero fill and rdiag remain
-  if (abort_flag) {
-    if (tid == 0) atomicOr(status, ST_TIMEOUT);
-    return;
-  }
-  if (fail) {
-    if (tid == 0) atomicOr(status, ST_NOT_PD);
+  pdl_trigger();  // the next kernel may launch: only the zero fill and rdiag remain
+  if (abort_flag || fail) {
+    if (tid == 0) {
+      atomicOr(status, abort_flag ? ST_TIMEOUT : ST_NOT_PD);
+      if (col_flag) gpu_flag_release(col_flag, -1);
+    }
     return;
   }
   // L itself was written by the column warp; zeros above the diagonal
@@ -250,43 +264,74 @@ __global__ void __launch_bounds__(kPotrfThreads) potrf_kernel(T* __restrict__ a,
   if (tid < n) rdiag[tid] = rds[tid];
 }
 
-// W = L_kk^{-1} (lower) for the panel solve: column c of W per CTA, by right-looking
-// forward substitution of L w = e_c in warp 0 with rows lane and lane + 32 in
-// registers; w_m = (accumulated value) * rdiag_m, then rows below subtract L_im w_m.
-// All four warps stage the needed part of L in shared memory first (independent
-// loads, so their latencies overlap). One CTA per column spreads the FP64 work over
-// many SMs.
-constexpr int kInvThreads = 128;
 template <typename T>
-__global__ void __launch_bounds__(kInvThreads) tri_inv_kernel(const T* __restrict__ a, int D, int k0,
-                                                              const T* __restrict__ rdiag, T* __restrict__ W,
-                                                              const uint32_t* __restrict__ status) {
-  __shared__ T Ls[NB][NB + 1];
-  __shared__ T rds[NB];
+__global__ void __launch_bounds__(kPotrfThreads) potrf_kernel(T* __restrict__ a, int D, int k0,
+                                                              const double* __restrict__ ridge,
+                                                              T* __restrict__ rdiag, uint32_t* __restrict__ status) {
   pdl_wait();
+  potrf_body<T>(a, D, k0, ridge, rdiag, status, nullptr, 1);
+}
+
+// Column c of W = L_kk^{-1} (lower; it turns the panel solve into a product) while the
+// diagonal block is being factored: right-looking forward substitution of L w = e_c with
+// rows lane and lane + 32 in warp 0's registers, w_m = (accumulated value) rsqrt(d_m),
+// then rows below subtract L_im w_m; step m is taken as soon as column m of L and
+// rsqrt(d_m) are published (loads from L2). One CTA per column spreads the FP64 work
+// over many SMs. Bounded waits; a published -1 ends it.
+template <typename T>
+__device__ __forceinline__ void inv_streamed(const T* __restrict__ a, int D, int k0, const T* __restrict__ rdiag,
+                                             T* __restrict__ W, uint32_t* __restrict__ status,
+                                             const int* col_flag, int c) {
   if (*status & ST_NOT_PD) return;
   const int n = min(NB, D - k0);
-  const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
   if (c >= n) return;
-  // the part of L this column needs: rows i > c, columns c <= m < i
-#pragma unroll 4
-  for (int e = tid; e < NB * NB; e += kInvThreads) {
-    const int i = e >> 6, m = e & 63;
-    if (i < n && m >= c && m < i) Ls[i][m] = a[(size_t)(k0 + i) * D + k0 + m];
-  }
-  if (tid < n) rds[tid] = rdiag[tid];
-  for (int i = tid; i < c; i += kInvThreads) W[i * NB + c] = (T)0;
-  __syncthreads();
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int i = tid; i < c; i += blockDim.x) W[i * NB + c] = (T)0;
   if (tid >= 32) return;
   const int i0 = lane, i1 = lane + 32;
   T acc0 = (i0 == c) ? (T)1 : (T)0, acc1 = (i1 == c) ? (T)1 : (T)0;
+  int have = 0;  // columns every lane has seen published (warp-uniform)
   for (int m = c; m < n; ++m) {
-    const T w = __shfl_sync(0xffffffffu, m < 32 ? acc0 : acc1, m & 31) * rds[m];
+    if (have < m + 1) {
+      // every lane acquires the flag itself; the decisions are taken warp-wide so that
+      // no lane leaves while another still waits in a shuffle
+      const long long t0 = clock64();
+      for (;;) {
+        const int f = gpu_flag_acquire(col_flag);
+        if (__any_sync(0xffffffffu, f < 0)) return;
+        if (__all_sync(0xffffffffu, f >= m + 1)) {
+          have = __reduce_min_sync(0xffffffffu, (unsigned)f);
+          break;
+        }
+        const int late = lane == 0 ? (clock64() - t0 > kSpinLimitCycles) : 0;
+        if (__shfl_sync(0xffffffffu, late, 0)) {
+          if (lane == 0) atomicOr(status, ST_TIMEOUT);
+          return;
+        }
+        __nanosleep(64);
+      }
+    }
+    const T l0 = (m < 31 && i0 > m) ? a[(size_t)(k0 + i0) * D + k0 + m] : (T)0;
+    const T l1 = (i1 > m && i1 < n) ? a[(size_t)(k0 + i1) * D + k0 + m] : (T)0;
+    const T w = __shfl_sync(0xffffffffu, m < 32 ? acc0 : acc1, m & 31) * rdiag[m];
     if (lane == (m & 31)) W[m * NB + c] = w;
-    if (m < 31) acc0 = fma(-Ls[i0][m], w, acc0);
-    acc1 = fma(-Ls[i1][m], w, acc1);
+    if (m < 31) acc0 = fma(-l0, w, acc0);
+    acc1 = fma(-l1, w, acc1);
   }
-  pdl_trigger();
+}
+
+// Diagonal block (CTA 0) and the 64 columns of its inverse (CTAs 1..64) in one grid,
+// launched cooperatively so that all CTAs are resident: the inverse trails the
+// factorisation by about one column instead of starting after it.
+template <typename T>
+__global__ void __launch_bounds__(kPotrfThreads) potrf_inv_kernel(T* __restrict__ a, int D, int k0,
+                                                                  const double* __restrict__ ridge,
+                                                                  T* __restrict__ rdiag, T* __restrict__ W,
+                                                                  uint32_t* __restrict__ status, int* col_flag,
+                                                                  int pub_every) {
+  pdl_wait();
+  if (blockIdx.x == 0) potrf_body<T>(a, D, k0, ridge, rdiag, status, col_flag, pub_every);
+  else inv_streamed<T>(a, D, k0, rdiag, W, status, col_flag, (int)blockIdx.x - 1);
 }
 
 // Exact digit split of one panel row for the tensor-core trailing update. The warp
@@ -474,6 +519,23 @@ cudaError_t launch_copy_lower(const double* src, double* dst, int D, cudaStream_
 // the next block column's update and its diagonal/panel factorisation run on `side`
 // while `s` applies the rest of the trailing update (look-ahead); the arithmetic of
 // every tile is the same either way, so both schedules give identical results.
+// Cooperative launch: every CTA of the grid resident at once (the streamed inverse's
+// CTAs wait on the factorising CTA).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_coop(void (*kern)(KArgs...), int grid, int block, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // Launch with programmatic stream serialisation (the kernel calls pdl_wait first).
 template <typename... KArgs, typename... Args>
 static cudaError_t launch_pdl(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t st,
@@ -510,6 +572,17 @@ static cudaError_t cholesky_t(T* a, int D, const double* ridge, void* aux, uint3
     planes[q] = (__nv_bfloat16*)(dig0 + q * plane_bytes);
     rexp[q] = (int*)(dig0 + 3 * plane_bytes + q * rexp_bytes);
   }
+  // columns the diagonal block publishes at a time to its streamed inverse (1..32)
+  static const int kPublishEvery = [] {
+    const char* v = getenv("PHI4_PUBLISH_EVERY");
+    return v ? std::min(32, std::max(1, atoi(v))) : 8;
+  }();
+  // per diagonal block, the count of its published columns (streamed inverse)
+  int* col_flags = (int*)(dig0 + 3 * plane_bytes + 3 * rexp_bytes);
+  {
+    const cudaError_t e = cudaMemsetAsync(col_flags, 0, (size_t)nblk * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+  }
   const bool tcu = tensor_update && sizeof(T) == 8;
   // trailing update by panel kb of the 64-column blocks [lo, hi) of its trailing matrix
   auto update = [&](int kb, int lo, int hi, cudaStream_t st) -> cudaError_t {
@@ -538,12 +611,14 @@ static cudaError_t cholesky_t(T* a, int D, const double* ridge, void* aux, uint3
   // (each waits for it at entry), so their launch latency overlaps the predecessor
   auto panel = [&](int kb, cudaStream_t st) {
     const int k0 = kb * NB;
-    launch_pdl(potrf_kernel<T>, 1, kPotrfThreads, 0, st, a, D, k0, ridge, rdiag + (size_t)kb * NB, status);
     const int rows = D - k0 - min(NB, D - k0);
-    if (rows > 0) {
-      // the inverse only feeds the panel solve
-      launch_pdl(tri_inv_kernel<T>, min(NB, D - k0), kInvThreads, 0, st, (const T*)a, D, k0,
-                 (const T*)(rdiag + (size_t)kb * NB), W + (size_t)kb * NB * NB, (const uint32_t*)status);
+    if (rows <= 0) {  // the last diagonal block: no panel, no inverse
+      launch_pdl(potrf_kernel<T>, 1, kPotrfThreads, 0, st, a, D, k0, ridge, rdiag + (size_t)kb * NB, status);
+    } else {
+      // the diagonal block with its inverse streamed beside it (the inverse only feeds
+      // the panel solve)
+      launch_coop(potrf_inv_kernel<T>, 1 + min(NB, D - k0), kPotrfThreads, st, a, D, k0, ridge,
+                  rdiag + (size_t)kb * NB, W + (size_t)kb * NB * NB, status, col_flags + kb, kPublishEvery);
       // with the tensor-core update the solve also writes the digit planes, for every
       // row of the update's 128-row tiles (rows >= `rows` get zeros)
       const int grid_rows = tcu ? (rows + 127) / 128 * 128 : rows;
@@ -582,7 +657,7 @@ size_t cholesky_aux_bytes(int D) {
   const size_t nblk = (size_t)(D + NB - 1) / NB;
   const size_t mp = (size_t)mpad_of(D);
   return round256(nblk * NB * NB * sizeof(double)) + round256(nblk * NB * sizeof(double)) +
-         3 * round256(8 * mp * 64 * 2) + 3 * round256(mp * sizeof(int));
+         3 * round256(8 * mp * 64 * 2) + 3 * round256(mp * sizeof(int)) + round256(nblk * sizeof(int));
 }
 
 // Which trailing update the double factorisation uses (mode 0 = automatic).
@@ -605,7 +680,7 @@ cudaError_t launch_cholesky_f32(const double* sigma, float* a, int D, const doub
 
 int cholesky_launches(int D) {
   const int nblk = (D + NB - 1) / NB;
-  return nblk + 4 * (nblk - 1);  // diagonal blocks; per panel: inverse, solve, two update parts
+  return nblk + 3 * (nblk - 1);  // diagonal blocks (with their inverses); per panel: solve, two update parts
 }
 
 cudaError_t launch_factor_convert(const double* Lc, int D, int dtype, void* out, int ld, cudaStream_t s) {
