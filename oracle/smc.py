@@ -9,7 +9,8 @@ Outer step at temperature index t (t = 1, 2, ...), in the paper's order:
   3. systematic resampling with offset word (KIND_RESAMPLE, t, 0, 0, 0)[0];
   4. re-estimate the particle covariance and its Cholesky factor (ridge level
      carried over from the previous step);
-  5. n_mcmc random-walk Metropolis sweeps targeting gamma_{beta + dbeta};
+  5. n_mcmc random-walk Metropolis sweeps targeting gamma_{beta + dbeta} (or, with
+     inner = "irmh", independent Metropolis-Hastings sweeps, oracle.irmh);
   5'. optionally (z2_flip) the global move phi -> -phi per particle with a Philox bit
      (KIND_FLIP, t, 0, particle, 0), bit 0 of word 0;
   6. refresh ell from the cached S and |phi|^2.
@@ -20,7 +21,7 @@ import math
 
 import numpy as np
 
-from . import covariance, lattice, mutation, observables, philox, resample, tempering
+from . import covariance, irmh, lattice, mutation, observables, philox, resample, tempering
 
 
 @dataclasses.dataclass
@@ -42,6 +43,7 @@ class SMCConfig:
     normal_bits: int = 32          # 32: double-precision draws; 24: single-precision draws
     max_steps: int = 100000
     z2_flip: bool = False          # global phi -> -phi move after each temperature's sweeps
+    inner: str = "rw"              # "rw": random-walk sweeps; "irmh": independent MH sweeps (oracle.irmh)
 
     @property
     def D(self):
@@ -102,15 +104,23 @@ class SMC:
         U = philox.word32(c.seed, c.stream, philox.KIND_RESAMPLE, t)
         anc = resample.systematic(w, U)
         self.phi, self.S, self.sq = self.phi[anc], self.S[anc], self.sq[anc]
-        _, Sigma = covariance.sample_covariance(self.phi)
+        mu, Sigma = covariance.sample_covariance(self.phi)
         Lc, delta, _, self.ridge_level = covariance.regularised_cholesky(Sigma, c.jitter_rel,
                                                                          start_level=self.ridge_level)
         n_acc = 0
-        for s in range(c.n_mcmc):
-            self.phi, self.S, self.sq, acc = mutation.rw_sweep(
-                self.phi, self.S, self.sq, Lc, c.scale, beta_new, c.L, c.m2, c.lam, c.c_kin, c.c_mass,
-                c.keep_reference, c.seed, c.stream, t, s, c.normal_bits)
-            n_acc += int(acc.sum())
+        if c.inner == "irmh":
+            r = irmh.whitened_sq_norm(self.phi, mu, Lc)
+            for s in range(c.n_mcmc):
+                self.phi, self.S, self.sq, r, acc, _ = irmh.irmh_sweep(
+                    self.phi, self.S, self.sq, r, Lc, mu, beta_new, c.L, c.m2, c.lam, c.c_kin, c.c_mass,
+                    c.keep_reference, c.seed, c.stream, t, s)
+                n_acc += int(acc.sum())
+        else:
+            for s in range(c.n_mcmc):
+                self.phi, self.S, self.sq, acc = mutation.rw_sweep(
+                    self.phi, self.S, self.sq, Lc, c.scale, beta_new, c.L, c.m2, c.lam, c.c_kin, c.c_mass,
+                    c.keep_reference, c.seed, c.stream, t, s, c.normal_bits)
+                n_acc += int(acc.sum())
         if c.z2_flip:
             self.phi = z2_flip(self.phi, c.seed, c.stream, t)
         self.ell = lattice.tempering_loglik(self.S, self.sq, c.D, c.keep_reference)

@@ -88,6 +88,26 @@ def test_flags_are_checked():
         p.Run(gpu_cfg(L=4, N=64, kind=p.NS_SLICE, ns_n_delete=8, flags=p.FLAG_Z2_FLIP))
 
 
+@pytest.mark.parametrize("precision", [p.FP64, p.FP32, p.MIXED_BF16], ids=["fp64", "fp32", "bf16"])
+def test_observables_match_oracle_summary(precision):
+    # a12: every population moment of M, the susceptibility and the mode balance of the
+    # device's smc_observables against the oracle's summary of the same device fields (the
+    # fields themselves are compared elsewhere; this pins the reduction and its formulas)
+    from oracle import observables as oobs
+    L, N = 8, 700
+    run = p.Run(gpu_cfg(L=L, N=N, n_mcmc=3, seed=8, precision=precision))
+    for _ in range(3):
+        run.temper_step()
+    o = run.observables()
+    phi = run.particles().cpu().numpy().astype(np.float64)
+    ref = oobs.summary(phi)
+    for k in ("mean_M", "mean_absM", "mean_M2", "chi"):
+        assert o[k] == pytest.approx(ref[k], rel=1e-10, abs=1e-13), k
+    assert o["mode_balance"] == pytest.approx(ref["mode_balance"], rel=1e-12)
+    assert 0.0 <= o["acc_rate"] <= 1.0 and o["n_steps"] == 3
+    run.close()
+
+
 def test_run_to_completion_and_done_status():
     run = p.Run(gpu_cfg(L=4, N=512, seed=1))
     obs = run.run()
