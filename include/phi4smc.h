@@ -55,7 +55,13 @@ typedef enum {
   PHI4_ERR_UNSUPPORTED = 8   /* configuration outside what this build supports */
 } phi4_status;
 
-typedef enum { PHI4_SMC_RW = 0, PHI4_NS_SLICE = 1 } phi4_kind;
+/* Samplers. SMC_RW: adaptive tempered SMC with covariance-preconditioned random-walk
+ * sweeps (Sec. 2 sampler (i)). NS_SLICE: nested sampling with slice rejuvenation
+ * (sampler (iv)). SMC_IRMH: the same tempered SMC with independent Metropolis-Hastings
+ * sweeps (sampler (ii)): each particle proposes mu + L z from the Gaussian of the
+ * population's mean mu and covariance L L^T, accepted with the tempered-target ratio
+ * times q(phi) / q(phi'); FP64 form, D <= 1024. */
+typedef enum { PHI4_SMC_RW = 0, PHI4_NS_SLICE = 1, PHI4_SMC_IRMH = 2 } phi4_kind;
 
 /* Arithmetic forms of a run.
  * FP64:      fields, proposal GEMM, covariance and everything else in double.

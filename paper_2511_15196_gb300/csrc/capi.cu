@@ -43,11 +43,14 @@ phi4_status check_config(const phi4_config* c) {
   ARG_CHECK(c != nullptr, "config is NULL");
   ARG_CHECK(c->L >= 1 && c->L <= 128, "L = %d outside [1, 128]", c->L);
   ARG_CHECK(c->N >= 2 && c->N <= 131072, "N = %d outside [2, 131072]", c->N);
-  ARG_CHECK(c->kind == PHI4_SMC_RW || c->kind == PHI4_NS_SLICE, "kind = %d unknown", c->kind);
+  ARG_CHECK(c->kind == PHI4_SMC_RW || c->kind == PHI4_NS_SLICE || c->kind == PHI4_SMC_IRMH, "kind = %d unknown",
+            c->kind);
+  ARG_CHECK(c->kind != PHI4_SMC_IRMH || (c->precision == PHI4_FP64 && c->L * c->L <= 1024),
+            "SMC-IRMH runs in the FP64 form with D <= 1024");
   ARG_CHECK(c->precision >= PHI4_FP64 && c->precision <= PHI4_MIXED_BF16, "precision = %d unknown", c->precision);
   ARG_CHECK(isfinite(c->m2) && isfinite(c->lambda) && c->lambda >= 0.0, "m2/lambda invalid");
   ARG_CHECK(isfinite(c->c_kin) && isfinite(c->c_mass) && c->c_kin >= 0.0, "c_kin/c_mass invalid");
-  if (c->kind == PHI4_SMC_RW) {
+  if (c->kind != PHI4_NS_SLICE) {
     ARG_CHECK(c->ess_target > 0.0 && c->ess_target < 1.0, "ess_target = %g outside (0, 1)", c->ess_target);
     ARG_CHECK(c->n_mcmc >= 0 && c->n_mcmc <= 100000, "n_mcmc = %d invalid", c->n_mcmc);
     ARG_CHECK(c->bisect_iters >= 1 && c->bisect_iters <= 200, "bisect_iters = %d invalid", c->bisect_iters);
@@ -60,7 +63,7 @@ phi4_status check_config(const phi4_config* c) {
   ARG_CHECK(c->chol_jitter_rel >= 0.0 && isfinite(c->chol_jitter_rel), "chol_jitter_rel invalid");
   ARG_CHECK(c->chol_mode >= 0 && c->chol_mode <= 2, "chol_mode = %d unknown", c->chol_mode);
   ARG_CHECK((c->flags & ~PHI4_FLAG_Z2_FLIP) == 0, "flags 0x%x: unknown bits", c->flags);
-  ARG_CHECK(!(c->flags & PHI4_FLAG_Z2_FLIP) || c->kind == PHI4_SMC_RW, "the Z2 flip move is an SMC move");
+  ARG_CHECK(!(c->flags & PHI4_FLAG_Z2_FLIP) || c->kind != PHI4_NS_SLICE, "the Z2 flip move is an SMC move");
   return PHI4_OK;
 }
 
@@ -132,6 +135,10 @@ void lay_out(phi4_run* r, Layout& L) {
   r->cov_scratch = L.take(r->cov_scratch_bytes);
   r->bisect_scratch = L.take(bisect_scratch_bytes(N));
   r->resample_scratch = L.take(resample_scratch_bytes(N));
+  if (c.kind == PHI4_SMC_IRMH) {
+    r->irmh_r = (double*)L.take(N * 8);
+    r->irmh_zz = (double*)L.take(N * 8);
+  }
   if (c.kind == PHI4_NS_SLICE) {
     r->ns_dead_cap = std::min<int64_t>((int64_t)4 * 1024 * 1024, (int64_t)512 * N);
     r->ns_dead = (double*)L.take((size_t)r->ns_dead_cap * 2 * 8);
@@ -365,6 +372,35 @@ static phi4_status step_sweeps(phi4_run* r) {
     r->n_evals += (int64_t)N * c.n_mcmc;
     return PHI4_OK;
   }
+  if (c.kind == PHI4_SMC_IRMH) {
+    // independent proposals mu + L z of the refit's mean (the covariance scratch's first
+    // D doubles) and factor; the Hastings factor from the whitened norms
+    const double* mu = (const double*)r->cov_scratch;
+    {
+      StageScope sc(r, STG_OTHER);
+      CUDA_TRY(launch_whitened_sq_norm((const double*)r->phi, mu, (const double*)r->Lg, r->ldl, N, D, r->irmh_r, s));
+      r->kernel_launches += 1;
+    }
+    for (int sweep = 0; sweep < c.n_mcmc; ++sweep) {
+      {
+        StageScope sc(r, STG_NORMALS);
+        CUDA_TRY(launch_normals(c.seed, c.stream_id, RNG_PROPOSE, t, (uint32_t)sweep, 0, N, D, D, PHI4_DT_F64, r->Z,
+                                s));
+      }
+      {
+        StageScope sc(r, STG_PROPOSE);
+        CUDA_TRY(launch_propose_simt(mu, r->prop, r->Z, r->Lg, PHI4_DT_F64, N, D, 1.0, s, 0));
+        CUDA_TRY(launch_row_sq_norm((const double*)r->Z, N, D, r->irmh_zz, s));
+      }
+      StageScope sc(r, STG_ACCEPT);
+      CUDA_TRY(launch_accept(r->phi, r->prop, PHI4_DT_F64, ap, c.keep_reference, r->S, r->sq, r->ell,
+                             r->scal + SC_BETA, c.seed, c.stream_id, t, (uint32_t)sweep, r->acc_count, r->status, s,
+                             r->irmh_zz, r->irmh_r));
+      r->kernel_launches += 4;
+    }
+    r->n_evals += (int64_t)N * c.n_mcmc;
+    return PHI4_OK;
+  }
   for (int sweep = 0; sweep < c.n_mcmc; ++sweep) {
     phi4_status ps = propose(r, t, (uint32_t)sweep);
     if (ps != PHI4_OK) return ps;
@@ -561,7 +597,7 @@ phi4_status smc_init(const phi4_config* cfg, void* d_workspace, size_t workspace
 
 phi4_status smc_temper_step(phi4_run* r, double* beta_out) {
   ARG_CHECK(r, "run is NULL");
-  ARG_CHECK(r->cfg.kind == PHI4_SMC_RW, "smc_temper_step on a nested-sampling run");
+  ARG_CHECK(r->cfg.kind != PHI4_NS_SLICE, "smc_temper_step on a nested-sampling run");
   ARG_CHECK(!r->batch, "smc_temper_step on a batch handle (use smc_temper_step_batch)");
   if (r->done) {
     set_error("beta already 1");
@@ -595,7 +631,7 @@ phi4_status ns_replace_step(phi4_run* r, int32_t* done_out) {
 phi4_status smc_log_evidence(const phi4_run* rc, double* logz, double* logz_err) {
   ARG_CHECK(rc, "run is NULL");
   phi4_run* r = const_cast<phi4_run*>(rc);
-  if (r->cfg.kind == PHI4_SMC_RW) {
+  if (r->cfg.kind != PHI4_NS_SLICE) {
     double k[2];
     CUDA_TRY(cudaMemcpyAsync(k, r->scal + SC_KAHAN, 16, cudaMemcpyDeviceToHost, r->stream));
     CUDA_TRY(cudaStreamSynchronize(r->stream));

@@ -24,10 +24,18 @@ cudaError_t launch_normals(uint64_t seed, uint64_t stream_id, uint32_t kind, uin
 // kernels_lattice.cu
 cudaError_t launch_action(const void* phi, int dtype, const ActionParams& p, double* S, double* sq,
                           double* ell, int keep_reference, cudaStream_t s);
+// irmh_zz / irmh_r (optional, SMC-IRMH): log alpha gains (zz - r) / 2 and an accepted
+// particle's r becomes its zz
 cudaError_t launch_accept(void* phi, const void* prop, int dtype, const ActionParams& p, int keep_reference,
                           double* S, double* sq, double* ell, const double* beta, uint64_t seed,
                           uint64_t stream_id, uint32_t step, uint32_t sweep, uint32_t* acc_count,
-                          uint32_t* status, cudaStream_t s);
+                          uint32_t* status, cudaStream_t s, const double* irmh_zz = nullptr,
+                          double* irmh_r = nullptr);
+// SMC-IRMH (kernels_irmh.cu): r_n = |L^{-1}(phi_n - mu)|^2 (L: D x D lower, row pitch ld;
+// D <= 1024) and zz_n = |Z_n|^2, FP64
+cudaError_t launch_whitened_sq_norm(const double* phi, const double* mu, const double* Lf, int ld, int N, int D,
+                                    double* r, cudaStream_t s);
+cudaError_t launch_row_sq_norm(const double* Z, int N, int D, double* zz, cudaStream_t s);
 // float fields, proposal = phi + delta (fp16 increment), L % 4 == 0
 cudaError_t launch_accept_delta(float* phi, const void* delta_f16, const ActionParams& p, int keep_reference,
                                 double* S, double* sq, double* ell, const double* beta, uint64_t seed,
@@ -136,8 +144,9 @@ cudaError_t launch_factor_convert_f32(const float* Lc, int D, float* out, cudaSt
 cudaError_t launch_factor_convert(const double* Lc, int D, int dtype, void* out, int ld, cudaStream_t s);
 
 // kernels_gemm_simt.cu
+// prop = phi + scale Z L^T; phi_ld = 0 adds the one row `phi` to every row (SMC-IRMH: mu)
 cudaError_t launch_propose_simt(const void* phi, void* prop, const void* Z, const void* Lf, int dtype, int N,
-                                int D, double scale, cudaStream_t s);
+                                int D, double scale, cudaStream_t s, int phi_ld = -1);
 cudaError_t launch_syrk_simt(const void* XcT, int dtype, int D, int N, int ldx, double inv_nm1, double* sigma,
                              cudaStream_t s);
 

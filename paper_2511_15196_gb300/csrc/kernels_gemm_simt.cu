@@ -1,6 +1,7 @@
 // SIMT register-blocked GEMM, C = A B^T with both operands K-contiguous
 // (A: M x K rows, B: Nn x K rows), for the FP32 and FP64 forms of the sampler:
-//   EPI_PROPOSE: prop[m][n] = phi[m][n] + scale * sum_{k <= n} Z[m][k] L[n][k]
+//   EPI_PROPOSE: prop[m][n] = phi[m][n] + scale * sum_{k <= n} Z[m][k] L[n][k] (phi's row
+//                pitch phi_ld; 0 adds one row, the SMC-IRMH mean, to every row)
 //                (L lower triangular; a tile of columns [n0, n0+BN) stops at k = n0+BN);
 //   EPI_SYRK:    sigma[m][n] = inv * sum_k XcT[m][k] XcT[n][k] for n <= m only
 //                (tiles strictly above the diagonal are skipped).
@@ -14,7 +15,8 @@ enum { EPI_PROPOSE = 0, EPI_SYRK = 1 };
 template <typename T, int BM, int BN, int BK, int TM, int TN, int EPI>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     simt_gemm_kernel(const T* __restrict__ A, int lda, const T* __restrict__ B, int ldb, int M, int Nn, int K,
-                     const T* __restrict__ phi, T* __restrict__ out, double* __restrict__ sigma, double scale) {
+                     const T* __restrict__ phi, int phi_ld, T* __restrict__ out, double* __restrict__ sigma,
+                     double scale) {
   constexpr int NT = (BM / TM) * (BN / TN);
   constexpr int TX = BN / TN;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -71,8 +73,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
       const int gn = n0 + cc[j];
       if (gn >= Nn) continue;
       if (EPI == EPI_PROPOSE) {
-        const size_t o = (size_t)gm * Nn + gn;
-        out[o] = phi[o] + (T)scale * acc[i][j];
+        out[(size_t)gm * Nn + gn] = phi[(size_t)gm * phi_ld + gn] + (T)scale * acc[i][j];
       } else {
         if (gn <= gm) sigma[(size_t)gm * Nn + gn] = (double)acc[i][j] * scale;
       }
@@ -81,22 +82,23 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 }
 
 template <typename T, int BM, int BN, int TM, int TN, int EPI>
-static cudaError_t run_gemm(const T* A, int lda, const T* B, int ldb, int M, int Nn, int K, const T* phi, T* out,
-                            double* sigma, double scale, cudaStream_t s) {
+static cudaError_t run_gemm(const T* A, int lda, const T* B, int ldb, int M, int Nn, int K, const T* phi, int phi_ld,
+                            T* out, double* sigma, double scale, cudaStream_t s) {
   dim3 grid((Nn + BN - 1) / BN, (M + BM - 1) / BM);
   simt_gemm_kernel<T, BM, BN, 16, TM, TN, EPI>
-      <<<grid, (BM / TM) * (BN / TN), 0, s>>>(A, lda, B, ldb, M, Nn, K, phi, out, sigma, scale);
+      <<<grid, (BM / TM) * (BN / TN), 0, s>>>(A, lda, B, ldb, M, Nn, K, phi, phi_ld, out, sigma, scale);
   return cudaGetLastError();
 }
 
 cudaError_t launch_propose_simt(const void* phi, void* prop, const void* Z, const void* Lf, int dtype, int N, int D,
-                                double scale, cudaStream_t s) {
+                                double scale, cudaStream_t s, int phi_ld) {
+  if (phi_ld < 0) phi_ld = D;
   if (dtype == 0)
     return run_gemm<double, 64, 64, 4, 4, EPI_PROPOSE>((const double*)Z, D, (const double*)Lf, D, N, D, D,
-                                                       (const double*)phi, (double*)prop, nullptr, scale, s);
+                                                       (const double*)phi, phi_ld, (double*)prop, nullptr, scale, s);
   if (dtype == 1)
     return run_gemm<float, 128, 128, 8, 8, EPI_PROPOSE>((const float*)Z, D, (const float*)Lf, D, N, D, D,
-                                                        (const float*)phi, (float*)prop, nullptr, scale, s);
+                                                        (const float*)phi, phi_ld, (float*)prop, nullptr, scale, s);
   return cudaErrorInvalidValue;
 }
 
@@ -104,10 +106,10 @@ cudaError_t launch_syrk_simt(const void* XcT, int dtype, int D, int N, int ldx, 
                              cudaStream_t s) {
   if (dtype == 0)
     return run_gemm<double, 64, 64, 4, 4, EPI_SYRK>((const double*)XcT, ldx, (const double*)XcT, ldx, D, D, N,
-                                                    nullptr, nullptr, sigma, inv_nm1, s);
+                                                    nullptr, 0, nullptr, sigma, inv_nm1, s);
   if (dtype == 1)
     return run_gemm<float, 128, 128, 8, 8, EPI_SYRK>((const float*)XcT, ldx, (const float*)XcT, ldx, D, D, N,
-                                                     nullptr, nullptr, sigma, inv_nm1, s);
+                                                     nullptr, 0, nullptr, sigma, inv_nm1, s);
   return cudaErrorInvalidValue;
 }
 

@@ -99,7 +99,9 @@ __global__ void __launch_bounds__(PPB* TPP) accept_kernel(T* __restrict__ phi, c
                                                           const double* __restrict__ beta_ptr, PhiloxKey key,
                                                           uint32_t w0, uint32_t sweep,
                                                           uint32_t* __restrict__ acc_count,
-                                                          uint32_t* __restrict__ status) {
+                                                          uint32_t* __restrict__ status,
+                                                          const double* __restrict__ irmh_zz,
+                                                          double* __restrict__ irmh_r) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[64];
   __shared__ int accept_flag[PPB];
@@ -116,7 +118,8 @@ __global__ void __launch_bounds__(PPB* TPP) accept_kernel(T* __restrict__ phi, c
   if (i < p.N && t == 0) {
     const double beta = *beta_ptr;
     const double dS = s - S[i], dq = q - sq[i];
-    const double log_alpha = keep_ref ? (-beta * dS - 0.5 * dq) : (-beta * dS - (1.0 - beta) * 0.5 * dq);
+    double log_alpha = keep_ref ? (-beta * dS - 0.5 * dq) : (-beta * dS - (1.0 - beta) * 0.5 * dq);
+    if (irmh_zz) log_alpha += 0.5 * (irmh_zz[i] - irmh_r[i]);  // log q(phi) - log q(phi')
     const uint4 w = philox4x32_10(make_uint4(w0, sweep, (uint32_t)i, 0u), key);
     const double u = uniform53(w.x, w.y);
     int acc = log(u) < log_alpha;
@@ -129,6 +132,7 @@ __global__ void __launch_bounds__(PPB* TPP) accept_kernel(T* __restrict__ phi, c
       S[i] = s;
       sq[i] = q;
       ell[i] = keep_ref ? -s : (-s + 0.5 * q + p.half_d_log2pi);
+      if (irmh_zz) irmh_r[i] = irmh_zz[i];
       atomicAdd(acc_count, 1u);
     }
   }
@@ -361,19 +365,20 @@ cudaError_t launch_action(const void* phi, int dtype, const ActionParams& p, dou
 template <typename T>
 static cudaError_t accept_t(T* phi, const T* prop, const ActionParams& p, int keep_ref, double* S, double* sq,
                             double* ell, const double* beta, PhiloxKey key, uint32_t w0, uint32_t sweep,
-                            uint32_t* acc, uint32_t* status, cudaStream_t s) {
+                            uint32_t* acc, uint32_t* status, cudaStream_t s, const double* irmh_zz = nullptr,
+                            double* irmh_r = nullptr) {
   if (p.D >= kBigD) {
     const size_t sm = (size_t)p.D * sizeof(T);
     cudaError_t e = set_smem(accept_kernel<T, 1, 256>, sm);
     if (e != cudaSuccess) return e;
     accept_kernel<T, 1, 256><<<p.N, 256, sm, s>>>(phi, prop, p, keep_ref, S, sq, ell, beta, key, w0, sweep, acc,
-                                                  status);
+                                                  status, irmh_zz, irmh_r);
   } else {
     const size_t sm = (size_t)8 * p.D * sizeof(T);
     cudaError_t e = set_smem(accept_kernel<T, 8, 32>, sm);
     if (e != cudaSuccess) return e;
     accept_kernel<T, 8, 32><<<(p.N + 7) / 8, 256, sm, s>>>(phi, prop, p, keep_ref, S, sq, ell, beta, key, w0,
-                                                           sweep, acc, status);
+                                                           sweep, acc, status, irmh_zz, irmh_r);
   }
   return cudaGetLastError();
 }
@@ -422,10 +427,16 @@ cudaError_t launch_accept_delta(float* phi, const void* delta_f16, const ActionP
 
 cudaError_t launch_accept(void* phi, const void* prop, int dtype, const ActionParams& p, int keep_reference,
                           double* S, double* sq, double* ell, const double* beta, uint64_t seed, uint64_t stream_id,
-                          uint32_t step, uint32_t sweep, uint32_t* acc_count, uint32_t* status, cudaStream_t s) {
+                          uint32_t step, uint32_t sweep, uint32_t* acc_count, uint32_t* status, cudaStream_t s,
+                          const double* irmh_zz, double* irmh_r) {
   if (p.N <= 0) return cudaSuccess;
   const PhiloxKey key = philox_key(seed, stream_id);
   const uint32_t w0 = counter_word0(RNG_ACCEPT, step);
+  if (irmh_zz) {
+    if (dtype != 0) return cudaErrorInvalidValue;
+    return accept_t<double>((double*)phi, (const double*)prop, p, keep_reference, S, sq, ell, beta, key, w0, sweep,
+                            acc_count, status, s, irmh_zz, irmh_r);
+  }
   if (dtype == 1 && vec_ok(p))
     return accept_vec<false>((float*)phi, (const float*)prop, nullptr, p, keep_reference, S, sq, ell, beta, key, w0,
                              sweep, acc_count, status, s);

@@ -9,7 +9,7 @@ The library's log Z in this mode is log E_{N(0,I)}[exp(-S_E)]; the values the pa
 (Tables 1, 3 and 4: about -65.3 at L = 10, -146 at 15, -210 at 18) equal it minus
 (V/4) log(pi) at all three sizes, so `logz_paper_convention` reports that difference too.
 
-    python -m paper_2511_15196_gb300.ess_sweep [--ess 0.9 0.99 0.999] [--seeds 4] [--n-mcmc 300]
+    python -m paper_2511_15196_gb300.ess_sweep [--ess 0.9 0.99 0.999] [--seeds 4] [--n-mcmc 300] [--L 10] [--irmh]
 """
 import argparse
 import json
@@ -17,10 +17,11 @@ import math
 import time
 
 
-def paper_config(ess, seed, n_mcmc=300, N=5000, precision=None):
-    from . import FP64, Config
-    return Config(L=10, N=N, m2=-4.0, lam=1.0, c_kin=0.5, c_mass=0.5, keep_reference=True,
-                  precision=FP64 if precision is None else precision, n_mcmc=n_mcmc, ess_target=ess, seed=seed)
+def paper_config(ess, seed, n_mcmc=300, N=5000, precision=None, L=10, kind=None):
+    from . import FP64, SMC_RW, Config
+    return Config(L=L, N=N, m2=-4.0, lam=1.0, c_kin=0.5, c_mass=0.5, keep_reference=True,
+                  precision=FP64 if precision is None else precision, n_mcmc=n_mcmc, ess_target=ess, seed=seed,
+                  kind=SMC_RW if kind is None else kind)
 
 
 def run_one(cfg):
@@ -37,15 +38,19 @@ def run_one(cfg):
     return obs, ms
 
 
-def sweep(ess_targets, seeds, n_mcmc=300, N=5000):
+def sweep(ess_targets, seeds, n_mcmc=None, N=5000, L=10, kind=None):
+    """n_mcmc defaults to 3 V (App. A); kind: SMC_RW (default) or SMC_IRMH."""
+    if n_mcmc is None:
+        n_mcmc = 3 * L * L
     rows = []
     for ess in ess_targets:
-        res = [run_one(paper_config(ess, s, n_mcmc=n_mcmc, N=N)) for s in range(seeds)]
+        res = [run_one(paper_config(ess, s, n_mcmc=n_mcmc, N=N, L=L, kind=kind)) for s in range(seeds)]
         lz = [o["logz"] for o, _ in res]
         m = sum(lz) / len(lz)
         sd = math.sqrt(sum((x - m) ** 2 for x in lz) / max(len(lz) - 1, 1))
         rows.append({"ess_target": ess, "seeds": seeds, "logz_mean": m, "logz_sd": sd,
-                     "logz_paper_convention": m - 100 / 4 * math.log(math.pi),
+                     "L": L, "kind": "irmh" if kind == 2 else "rw",
+                     "logz_paper_convention": m - L * L / 4 * math.log(math.pi),
                      "temperatures": sum(o["n_steps"] for o, _ in res) / len(res),
                      "likelihood_evals": sum(o["n_likelihood_evals"] for o, _ in res) / len(res),
                      "acc_rate": sum(o["acc_rate"] for o, _ in res) / len(res),
@@ -58,10 +63,12 @@ def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--ess", type=float, nargs="+", default=[0.9, 0.99, 0.999])
     ap.add_argument("--seeds", type=int, default=4)
-    ap.add_argument("--n-mcmc", type=int, default=300)
+    ap.add_argument("--n-mcmc", type=int, default=None, help="sweeps per temperature (default 3 V)")
     ap.add_argument("--N", type=int, default=5000)
+    ap.add_argument("--L", type=int, default=10)
+    ap.add_argument("--irmh", action="store_true", help="independent Metropolis-Hastings sweeps (SMC-IRMH)")
     a = ap.parse_args()
-    for row in sweep(a.ess, a.seeds, n_mcmc=a.n_mcmc, N=a.N):
+    for row in sweep(a.ess, a.seeds, n_mcmc=a.n_mcmc, N=a.N, L=a.L, kind=2 if a.irmh else None):
         print(json.dumps(row))
 
 

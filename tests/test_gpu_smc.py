@@ -81,6 +81,32 @@ def test_z2_flip_balances_the_modes_mixed():
     run.close()
 
 
+@pytest.mark.parametrize("L,N", [(4, 512), (8, 1024), (2, 300)])
+def test_irmh_fp64_steps_match_oracle(L, N):
+    # SMC-IRMH: the same proposals (mean + L z), Hastings terms and decisions as the oracle
+    run = p.Run(gpu_cfg(L=L, N=N, n_mcmc=3, seed=9, kind=p.SMC_IRMH))
+    ref = SMC(oracle_cfg(L=L, N=N, n_mcmc=3, seed=9, inner="irmh"))
+    for _ in range(3):
+        if ref.done:
+            break
+        beta = run.temper_step()
+        rec = ref.temper_step()
+        assert beta == pytest.approx(rec["beta"], rel=1e-10, abs=1e-13)
+        lz, _ = run.log_evidence()
+        assert lz == pytest.approx(rec["logz"], rel=1e-10, abs=1e-9)
+        phi = run.particles().cpu().numpy()
+        assert np.abs(phi - ref.phi).max() < 1e-8
+        assert run.observables()["acc_rate"] == pytest.approx(rec["acc_rate"], abs=1e-12)
+    run.close()
+
+
+def test_irmh_configuration_checks():
+    with pytest.raises(RuntimeError):
+        p.Run(gpu_cfg(L=8, N=64, kind=p.SMC_IRMH, precision=p.MIXED_BF16))
+    with pytest.raises(RuntimeError):
+        p.Run(gpu_cfg(L=40, N=64, kind=p.SMC_IRMH))
+
+
 def test_flags_are_checked():
     with pytest.raises(RuntimeError):
         p.Run(gpu_cfg(L=4, N=64, flags=2))
