@@ -10,7 +10,8 @@ Outer step at temperature index t (t = 1, 2, ...), in the paper's order:
   4. re-estimate the particle covariance and its Cholesky factor (ridge level
      carried over from the previous step);
   5. n_mcmc random-walk Metropolis sweeps targeting gamma_{beta + dbeta} (or, with
-     inner = "irmh", independent Metropolis-Hastings sweeps, oracle.irmh);
+     inner = "irmh", independent Metropolis-Hastings sweeps, oracle.irmh; with inner = "hmc",
+     HMC transitions with the covariance diagonal as inverse mass, oracle.hmc);
   5'. optionally (z2_flip) the global move phi -> -phi per particle with a Philox bit
      (KIND_FLIP, t, 0, particle, 0), bit 0 of word 0;
   6. refresh ell from the cached S and |phi|^2.
@@ -21,7 +22,7 @@ import math
 
 import numpy as np
 
-from . import covariance, irmh, lattice, mutation, observables, philox, resample, tempering
+from . import covariance, hmc, irmh, lattice, mutation, observables, philox, resample, tempering
 
 
 @dataclasses.dataclass
@@ -43,7 +44,9 @@ class SMCConfig:
     normal_bits: int = 32          # 32: double-precision draws; 24: single-precision draws
     max_steps: int = 100000
     z2_flip: bool = False          # global phi -> -phi move after each temperature's sweeps
-    inner: str = "rw"              # "rw": random-walk sweeps; "irmh": independent MH sweeps (oracle.irmh)
+    inner: str = "rw"              # "rw": random-walk sweeps; "irmh": independent MH sweeps (oracle.irmh);
+                                   # "hmc": HMC transitions (oracle.hmc)
+    hmc_step: float = 0.0          # <= 0: oracle.hmc.default_step(D)
 
     @property
     def D(self):
@@ -108,7 +111,15 @@ class SMC:
         Lc, delta, _, self.ridge_level = covariance.regularised_cholesky(Sigma, c.jitter_rel,
                                                                          start_level=self.ridge_level)
         n_acc = 0
-        if c.inner == "irmh":
+        if c.inner == "hmc":
+            v = np.diag(Sigma) + delta
+            eps = c.hmc_step if c.hmc_step > 0 else hmc.default_step(c.D)
+            for s in range(c.n_mcmc):
+                self.phi, self.S, self.sq, acc, _ = hmc.hmc_sweep(
+                    self.phi, self.S, self.sq, v, eps, beta_new, c.L, c.m2, c.lam, c.c_kin, c.c_mass,
+                    c.keep_reference, c.seed, c.stream, t, s)
+                n_acc += int(acc.sum())
+        elif c.inner == "irmh":
             r = irmh.whitened_sq_norm(self.phi, mu, Lc)
             for s in range(c.n_mcmc):
                 self.phi, self.S, self.sq, r, acc, _ = irmh.irmh_sweep(
