@@ -60,8 +60,12 @@ typedef enum {
  * (sampler (iv)). SMC_IRMH: the same tempered SMC with independent Metropolis-Hastings
  * sweeps (sampler (ii)): each particle proposes mu + L z from the Gaussian of the
  * population's mean mu and covariance L L^T, accepted with the tempered-target ratio
- * times q(phi) / q(phi'); FP64 form, D <= 1024. */
-typedef enum { PHI4_SMC_RW = 0, PHI4_NS_SLICE = 1, PHI4_SMC_IRMH = 2 } phi4_kind;
+ * times q(phi) / q(phi'); FP64 form, D <= 1024. SMC_HMC: the same tempered SMC with
+ * Hamiltonian Monte Carlo transitions (sampler (iii)): 20 leapfrog steps (App. A) per
+ * transition with the refit's covariance diagonal plus the ridge as inverse mass and
+ * step size rw_scale (<= 0 selects 0.8 D^(-1/4)); n_mcmc transitions per temperature;
+ * FP64 form, D <= 4096. */
+typedef enum { PHI4_SMC_RW = 0, PHI4_NS_SLICE = 1, PHI4_SMC_IRMH = 2, PHI4_SMC_HMC = 3 } phi4_kind;
 
 /* Arithmetic forms of a run.
  * FP64:      fields, proposal GEMM, covariance and everything else in double.
@@ -94,7 +98,8 @@ typedef struct {
                                 1: path N(0,I) e^{-beta S}, i.e. exp(-[U0 + beta S]) of Sec. 2 */
   int32_t n_mcmc;            /* random-walk sweeps per temperature (SMC) */
   double ess_target;         /* rho in (0,1): next beta keeps ESS = rho N (SMC) */
-  double rw_scale;           /* proposal scale on the Cholesky factor; <= 0 selects 2.38/sqrt(D) (App. A) */
+  double rw_scale;           /* proposal scale on the Cholesky factor; <= 0 selects 2.38/sqrt(D) (App. A);
+                                SMC_HMC: the leapfrog step size, <= 0 selects 0.8 D^(-1/4) */
   int32_t ns_n_delete;       /* live points deleted per nested-sampling iteration (1 <= k < N) */
   int32_t ns_slice_steps;    /* slice steps per new point; <= 0 selects 3*D */
   double ns_stop_frac;       /* stop when remaining evidence < ns_stop_frac * Z */

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libphi4smc.so")
 
 PHI4_OK, PHI4_ERR_ARG, PHI4_ERR_CUDA, PHI4_ERR_NOT_PD, PHI4_ERR_NONFINITE, PHI4_ERR_DONE, PHI4_ERR_WORKSPACE, \
     PHI4_ERR_TIMEOUT, PHI4_ERR_UNSUPPORTED = range(9)
-SMC_RW, NS_SLICE, SMC_IRMH = 0, 1, 2
+SMC_RW, NS_SLICE, SMC_IRMH, SMC_HMC = 0, 1, 2, 3
 FP64, FP32, MIXED_BF16 = 0, 1, 2
 DT_F64, DT_F32, DT_BF16 = 0, 1, 2
 RNG_INIT, RNG_RESAMPLE, RNG_PROPOSE, RNG_ACCEPT, RNG_NS_START, RNG_NS_DIRECTION, RNG_NS_SLICE, RNG_FLIP = range(1, 9)

@@ -141,6 +141,103 @@ __global__ void __launch_bounds__(PPB* TPP) accept_kernel(T* __restrict__ phi, c
     for (int x = t; x < p.D; x += TPP) phi[(size_t)i * p.D + x] = row[x];
 }
 
+// SMC-HMC transition (Sec. 2 sampler (iii), FP64), one particle per 256-thread CTA with
+// its field x, momentum p and inverse mass v in shared memory. v_s = Sigma_ss + ridge
+// (the refit's covariance diagonal), p = z / sqrt(v) from the sweep's normals Z; leapfrog
+// with the tempered target's gradient
+//   g_s = -beta (c_kin (8 x_s - 2 sum of neighbours) + 2 c_mass m2 x_s + 4 lam x_s^3) - a x_s,
+// a = 1 - beta (1 with the reference kept): p += eps/2 g, then n times {x += eps v p;
+// p += eps g} with a half step last; accept when log u < H(start) - H(end),
+// H = beta S + a |x|^2 / 2 + sum_s v_s p_s^2 / 2.
+__global__ void __launch_bounds__(256) hmc_kernel(double* __restrict__ phi, const double* __restrict__ Z,
+                                                  const double* __restrict__ sigma, const double* __restrict__ ridge,
+                                                  ActionParams p, int keep_ref, double* __restrict__ S,
+                                                  double* __restrict__ sq, double* __restrict__ ell,
+                                                  const double* __restrict__ beta_ptr, double eps, int n_leap,
+                                                  PhiloxKey key, uint32_t w0, uint32_t sweep,
+                                                  uint32_t* __restrict__ acc_count, uint32_t* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[64];
+  __shared__ int accept_flag;
+  double* x = reinterpret_cast<double*>(smem_raw);
+  double* pm = x + p.D;
+  double* v = pm + p.D;
+  const int i = blockIdx.x, t = threadIdx.x, L = p.L, D = p.D;
+  const double beta = *beta_ptr, a = keep_ref ? 1.0 : 1.0 - beta, dl = *ridge;
+  const SiteCoef<double> k = coefs<double>(p);
+  double kin0 = 0.0;
+  for (int s = t; s < D; s += 256) {
+    x[s] = phi[(size_t)i * D + s];
+    v[s] = sigma[(size_t)s * D + s] + dl;
+    const double q = Z[(size_t)i * D + s] / sqrt(v[s]);
+    pm[s] = q;
+    kin0 += v[s] * q * q;
+  }
+  __syncthreads();
+  auto grad = [&](int s) {
+    const int r = s / L, c = s - (s / L) * L;
+    const int cl = c == 0 ? L - 1 : c - 1, cr = c == L - 1 ? 0 : c + 1;
+    const int ru = r == 0 ? L - 1 : r - 1, rd = r == L - 1 ? 0 : r + 1;
+    const double f = x[s];
+    const double nb = x[r * L + cl] + x[r * L + cr] + x[ru * L + c] + x[rd * L + c];
+    const double gs = k.ck * (8.0 * f - 2.0 * nb) + 2.0 * k.cm * f + 4.0 * k.lm * (f * f * f);
+    return -beta * gs - a * f;
+  };
+  for (int s = t; s < D; s += 256) pm[s] += 0.5 * eps * grad(s);
+  __syncthreads();
+  for (int l = 0; l < n_leap; ++l) {
+    for (int s = t; s < D; s += 256) x[s] += eps * v[s] * pm[s];
+    __syncthreads();
+    const double h = l + 1 < n_leap ? eps : 0.5 * eps;
+    for (int s = t; s < D; s += 256) pm[s] += h * grad(s);
+    __syncthreads();
+  }
+  double s_new = 0.0, q_new = 0.0, kin1 = 0.0;
+  site_sums<double, 256>(x, L, D, t, k, s_new, q_new);
+  for (int s = t; s < D; s += 256) kin1 += v[s] * pm[s] * pm[s];
+  s_new = block_sum(s_new, red);
+  q_new = block_sum(q_new, red);
+  kin0 = block_sum(kin0, red);
+  kin1 = block_sum(kin1, red);
+  if (t == 0) {
+    const double dS = s_new - S[i], dq = q_new - sq[i];
+    const double log_alpha = (keep_ref ? (-beta * dS - 0.5 * dq) : (-beta * dS - (1.0 - beta) * 0.5 * dq)) -
+                             0.5 * (kin1 - kin0);
+    const uint4 w = philox4x32_10(make_uint4(w0, sweep, (uint32_t)i, 0u), key);
+    int acc = log(uniform53(w.x, w.y)) < log_alpha;
+    if (!isfinite(s_new) || !isfinite(q_new)) {
+      atomicOr(status, ST_NONFINITE);
+      acc = 0;
+    }
+    accept_flag = acc;
+    if (acc) {
+      S[i] = s_new;
+      sq[i] = q_new;
+      ell[i] = keep_ref ? -s_new : (-s_new + 0.5 * q_new + p.half_d_log2pi);
+      atomicAdd(acc_count, 1u);
+    }
+  }
+  __syncthreads();
+  if (accept_flag)
+    for (int s = t; s < D; s += 256) phi[(size_t)i * D + s] = x[s];
+}
+
+cudaError_t launch_hmc(double* phi, const double* Z, const double* sigma, const double* ridge, const ActionParams& p,
+                       int keep_reference, double* S, double* sq, double* ell, const double* beta, double eps,
+                       int n_leap, uint64_t seed, uint64_t stream_id, uint32_t step, uint32_t sweep,
+                       uint32_t* acc_count, uint32_t* status, cudaStream_t s) {
+  if (p.N <= 0) return cudaSuccess;
+  const size_t sm = (size_t)3 * p.D * sizeof(double);
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(hmc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  hmc_kernel<<<p.N, 256, sm, s>>>(phi, Z, sigma, ridge, p, keep_reference, S, sq, ell, beta, eps, n_leap,
+                                 philox_key(seed, stream_id), counter_word0(RNG_ACCEPT, step), sweep, acc_count,
+                                 status);
+  return cudaGetLastError();
+}
+
 // Metropolis decision log u < log alpha for u in (0, 1] (53-bit), taken exactly as in
 // double precision but mostly without the double log: log u lies in [log 2^-53, 0],
 // so log alpha > 0 accepts and log alpha < -40 rejects; otherwise logf of the

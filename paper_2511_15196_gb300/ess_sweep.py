@@ -9,7 +9,8 @@ The library's log Z in this mode is log E_{N(0,I)}[exp(-S_E)]; the values the pa
 (Tables 1, 3 and 4: about -65.3 at L = 10, -146 at 15, -210 at 18) equal it minus
 (V/4) log(pi) at all three sizes, so `logz_paper_convention` reports that difference too.
 
-    python -m paper_2511_15196_gb300.ess_sweep [--ess 0.9 0.99 0.999] [--seeds 4] [--n-mcmc 300] [--L 10] [--irmh]
+    python -m paper_2511_15196_gb300.ess_sweep [--ess 0.9 0.99 0.999] [--seeds 4] [--n-mcmc 300] [--L 10]
+                                               [--irmh | --hmc]
 """
 import argparse
 import json
@@ -39,7 +40,7 @@ def run_one(cfg):
 
 
 def sweep(ess_targets, seeds, n_mcmc=None, N=5000, L=10, kind=None):
-    """n_mcmc defaults to 3 V (App. A); kind: SMC_RW (default) or SMC_IRMH."""
+    """n_mcmc defaults to 3 V (App. A); kind: SMC_RW (default), SMC_IRMH or SMC_HMC."""
     if n_mcmc is None:
         n_mcmc = 3 * L * L
     rows = []
@@ -49,7 +50,7 @@ def sweep(ess_targets, seeds, n_mcmc=None, N=5000, L=10, kind=None):
         m = sum(lz) / len(lz)
         sd = math.sqrt(sum((x - m) ** 2 for x in lz) / max(len(lz) - 1, 1))
         rows.append({"ess_target": ess, "seeds": seeds, "logz_mean": m, "logz_sd": sd,
-                     "L": L, "kind": "irmh" if kind == 2 else "rw",
+                     "L": L, "kind": {2: "irmh", 3: "hmc"}.get(kind, "rw"),
                      "logz_paper_convention": m - L * L / 4 * math.log(math.pi),
                      "temperatures": sum(o["n_steps"] for o, _ in res) / len(res),
                      "likelihood_evals": sum(o["n_likelihood_evals"] for o, _ in res) / len(res),
@@ -67,8 +68,10 @@ def main():
     ap.add_argument("--N", type=int, default=5000)
     ap.add_argument("--L", type=int, default=10)
     ap.add_argument("--irmh", action="store_true", help="independent Metropolis-Hastings sweeps (SMC-IRMH)")
+    ap.add_argument("--hmc", action="store_true", help="HMC transitions, 20 leapfrog steps (SMC-HMC)")
     a = ap.parse_args()
-    for row in sweep(a.ess, a.seeds, n_mcmc=a.n_mcmc, N=a.N, L=a.L, kind=2 if a.irmh else None):
+    kind = 2 if a.irmh else 3 if a.hmc else None
+    for row in sweep(a.ess, a.seeds, n_mcmc=a.n_mcmc, N=a.N, L=a.L, kind=kind):
         print(json.dumps(row))
 
 

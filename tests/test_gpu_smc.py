@@ -107,6 +107,33 @@ def test_irmh_configuration_checks():
         p.Run(gpu_cfg(L=40, N=64, kind=p.SMC_IRMH))
 
 
+@pytest.mark.parametrize("L,N,keep", [(4, 512, False), (8, 1024, False), (3, 300, True), (16, 256, False)])
+def test_hmc_fp64_steps_match_oracle(L, N, keep):
+    # SMC-HMC: the same momenta, leapfrog trajectories (20 steps, covariance-diagonal inverse
+    # mass), energies and decisions as the oracle
+    run = p.Run(gpu_cfg(L=L, N=N, n_mcmc=2, seed=5, kind=p.SMC_HMC, keep_reference=keep))
+    ref = SMC(oracle_cfg(L=L, N=N, n_mcmc=2, seed=5, inner="hmc", keep_reference=keep))
+    for _ in range(3):
+        if ref.done:
+            break
+        beta = run.temper_step()
+        rec = ref.temper_step()
+        assert beta == pytest.approx(rec["beta"], rel=1e-10, abs=1e-13)
+        lz, _ = run.log_evidence()
+        assert lz == pytest.approx(rec["logz"], rel=1e-10, abs=1e-9)
+        phi = run.particles().cpu().numpy()
+        assert np.abs(phi - ref.phi).max() < 1e-8
+        assert run.observables()["acc_rate"] == pytest.approx(rec["acc_rate"], abs=1e-12)
+    run.close()
+
+
+def test_hmc_configuration_checks():
+    with pytest.raises(RuntimeError):
+        p.Run(gpu_cfg(L=8, N=64, kind=p.SMC_HMC, precision=p.FP32))
+    with pytest.raises(RuntimeError):
+        p.Run(gpu_cfg(L=72, N=64, kind=p.SMC_HMC))
+
+
 def test_flags_are_checked():
     with pytest.raises(RuntimeError):
         p.Run(gpu_cfg(L=4, N=64, flags=2))
