@@ -64,7 +64,7 @@ typedef enum {
  * Hamiltonian Monte Carlo transitions (sampler (iii)): 20 leapfrog steps (App. A) per
  * transition with the refit's covariance diagonal plus the ridge as inverse mass and
  * step size rw_scale (<= 0 selects 0.8 D^(-1/4)); n_mcmc transitions per temperature;
- * FP64 form, D <= 4096. */
+ * FP64 or FP32 form (float trajectories, energies summed in double), D <= 4096. */
 typedef enum { PHI4_SMC_RW = 0, PHI4_NS_SLICE = 1, PHI4_SMC_IRMH = 2, PHI4_SMC_HMC = 3 } phi4_kind;
 
 /* Arithmetic forms of a run.

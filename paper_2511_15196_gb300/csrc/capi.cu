@@ -48,8 +48,8 @@ phi4_status check_config(const phi4_config* c) {
             "kind = %d unknown", c->kind);
   ARG_CHECK(c->kind != PHI4_SMC_IRMH || (c->precision == PHI4_FP64 && c->L * c->L <= 1024),
             "SMC-IRMH runs in the FP64 form with D <= 1024");
-  ARG_CHECK(c->kind != PHI4_SMC_HMC || (c->precision == PHI4_FP64 && c->L * c->L <= 4096),
-            "SMC-HMC runs in the FP64 form with D <= 4096");
+  ARG_CHECK(c->kind != PHI4_SMC_HMC || (c->precision != PHI4_MIXED_BF16 && c->L * c->L <= 4096),
+            "SMC-HMC runs in the FP64 or FP32 form with D <= 4096");
   ARG_CHECK(c->precision >= PHI4_FP64 && c->precision <= PHI4_MIXED_BF16, "precision = %d unknown", c->precision);
   ARG_CHECK(isfinite(c->m2) && isfinite(c->lambda) && c->lambda >= 0.0, "m2/lambda invalid");
   ARG_CHECK(isfinite(c->c_kin) && isfinite(c->c_mass) && c->c_kin >= 0.0, "c_kin/c_mass invalid");
@@ -381,13 +381,13 @@ static phi4_status step_sweeps(phi4_run* r) {
     for (int sweep = 0; sweep < c.n_mcmc; ++sweep) {
       {
         StageScope sc(r, STG_NORMALS);
-        CUDA_TRY(launch_normals(c.seed, c.stream_id, RNG_PROPOSE, t, (uint32_t)sweep, 0, N, D, D, PHI4_DT_F64, r->Z,
+        CUDA_TRY(launch_normals(c.seed, c.stream_id, RNG_PROPOSE, t, (uint32_t)sweep, 0, N, D, D, r->zdtype, r->Z,
                                 s));
       }
       StageScope sc(r, STG_ACCEPT);
-      CUDA_TRY(launch_hmc((double*)r->phi, (const double*)r->Z, r->sigma, r->scal + SC_RIDGE, ap, c.keep_reference,
-                          r->S, r->sq, r->ell, r->scal + SC_BETA, eps, kHmcLeapfrog, c.seed, c.stream_id, t,
-                          (uint32_t)sweep, r->acc_count, r->status, s));
+      CUDA_TRY(launch_hmc(r->phi, r->Z, r->zdtype, r->sigma, r->scal + SC_RIDGE, ap, c.keep_reference, r->S, r->sq,
+                          r->ell, r->scal + SC_BETA, eps, kHmcLeapfrog, c.seed, c.stream_id, t, (uint32_t)sweep,
+                          r->acc_count, r->status, s));
       r->kernel_launches += 2;
     }
     r->n_evals += (int64_t)N * c.n_mcmc * (kHmcLeapfrog + 1);

@@ -141,65 +141,106 @@ __global__ void __launch_bounds__(PPB* TPP) accept_kernel(T* __restrict__ phi, c
     for (int x = t; x < p.D; x += TPP) phi[(size_t)i * p.D + x] = row[x];
 }
 
-// SMC-HMC transition (Sec. 2 sampler (iii), FP64), one particle per 256-thread CTA with
-// its field x, momentum p and inverse mass v in shared memory. v_s = Sigma_ss + ridge
-// (the refit's covariance diagonal), p = z / sqrt(v) from the sweep's normals Z; leapfrog
-// with the tempered target's gradient
-//   g_s = -beta (c_kin (8 x_s - 2 sum of neighbours) + 2 c_mass m2 x_s + 4 lam x_s^3) - a x_s,
-// a = 1 - beta (1 with the reference kept): p += eps/2 g, then n times {x += eps v p;
-// p += eps g} with a half step last; accept when log u < H(start) - H(end),
-// H = beta S + a |x|^2 / 2 + sum_s v_s p_s^2 / 2.
-__global__ void __launch_bounds__(256) hmc_kernel(double* __restrict__ phi, const double* __restrict__ Z,
+// SMC-HMC transition (Sec. 2 sampler (iii)). Inverse mass v_s = Sigma_ss + ridge (the
+// refit's covariance diagonal), momenta p = z / sqrt(v). The kernel integrates in the
+// whitened momentum y = sqrt(v) p (y = z at the start, kinetic energy |y|^2 / 2), so with
+// e_s = eps sqrt(v_s) a leapfrog step is x += e y, y += e g(x) and the first and last
+// momentum steps are half steps. g is the gradient of the tempered log target,
+//   g_s = -beta (c_kin (8 x_s - 2 sum of neighbours) + 2 c_mass m2 x_s + 4 lam x_s^3) - a x_s
+//       = A x_s + B nb_s + C x_s^3,
+// a = 1 - beta (1 with the reference kept). Accept when log u < H(start) - H(end) with
+// H = beta S + a |x|^2 / 2 + |y|^2 / 2, the sums in double.
+// TPP threads per particle (256 / TPP particles per CTA); thread t of a group owns sites
+// t + k TPP (k < K) in registers: its field, y and e, and the four neighbour indices. The
+// field also lives in a double-buffered shared row so neighbours can read it: one barrier
+// per leapfrog step (the buffer written at step l was last read at step l - 2, before the
+// barrier of step l - 1).
+template <typename T, int TPP, int K>
+__global__ void __launch_bounds__(256) hmc_kernel(T* __restrict__ phi, const T* __restrict__ Z,
                                                   const double* __restrict__ sigma, const double* __restrict__ ridge,
                                                   ActionParams p, int keep_ref, double* __restrict__ S,
                                                   double* __restrict__ sq, double* __restrict__ ell,
                                                   const double* __restrict__ beta_ptr, double eps, int n_leap,
                                                   PhiloxKey key, uint32_t w0, uint32_t sweep,
                                                   uint32_t* __restrict__ acc_count, uint32_t* __restrict__ status) {
+  constexpr int PPB = 256 / TPP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[64];
-  __shared__ int accept_flag;
-  double* x = reinterpret_cast<double*>(smem_raw);
-  double* pm = x + p.D;
-  double* v = pm + p.D;
-  const int i = blockIdx.x, t = threadIdx.x, L = p.L, D = p.D;
+  __shared__ int accept_flag[PPB];
+  const int L = p.L, D = p.D;
+  const int g = threadIdx.x / TPP, t = threadIdx.x % TPP;
+  const int i = blockIdx.x * PPB + g;
+  const bool live = i < p.N;
+  T* buf0 = reinterpret_cast<T*>(smem_raw) + (size_t)g * 2 * D;
+  T* buf1 = buf0 + D;
   const double beta = *beta_ptr, a = keep_ref ? 1.0 : 1.0 - beta, dl = *ridge;
-  const SiteCoef<double> k = coefs<double>(p);
+  const T A = (T)(-beta * (8.0 * p.c_kin + 2.0 * p.c_mass * p.m2) - a);
+  const T B = (T)(2.0 * beta * p.c_kin);
+  const T C = (T)(-4.0 * beta * p.lam);
+  T x[K], y[K], e[K];
+  uint32_t lr[K], ud[K];
   double kin0 = 0.0;
-  for (int s = t; s < D; s += 256) {
-    x[s] = phi[(size_t)i * D + s];
-    v[s] = sigma[(size_t)s * D + s] + dl;
-    const double q = Z[(size_t)i * D + s] / sqrt(v[s]);
-    pm[s] = q;
-    kin0 += v[s] * q * q;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int s = t + k * TPP;
+    x[k] = y[k] = e[k] = T(0);
+    lr[k] = ud[k] = 0u;
+    if (live && s < D) {
+      const int r = s / L, c = s - r * L;
+      const int cl = c == 0 ? L - 1 : c - 1, cr = c == L - 1 ? 0 : c + 1;
+      const int ru = r == 0 ? L - 1 : r - 1, rd = r == L - 1 ? 0 : r + 1;
+      lr[k] = (uint32_t)(r * L + cl) | ((uint32_t)(r * L + cr) << 16);
+      ud[k] = (uint32_t)(ru * L + c) | ((uint32_t)(rd * L + c) << 16);
+      x[k] = phi[(size_t)i * D + s];
+      buf0[s] = x[k];
+      y[k] = Z[(size_t)i * D + s];
+      e[k] = (T)(eps * sqrt(sigma[(size_t)s * D + s] + dl));
+      kin0 += (double)y[k] * (double)y[k];
+    }
   }
-  __syncthreads();
-  auto grad = [&](int s) {
-    const int r = s / L, c = s - (s / L) * L;
-    const int cl = c == 0 ? L - 1 : c - 1, cr = c == L - 1 ? 0 : c + 1;
-    const int ru = r == 0 ? L - 1 : r - 1, rd = r == L - 1 ? 0 : r + 1;
-    const double f = x[s];
-    const double nb = x[r * L + cl] + x[r * L + cr] + x[ru * L + c] + x[rd * L + c];
-    const double gs = k.ck * (8.0 * f - 2.0 * nb) + 2.0 * k.cm * f + 4.0 * k.lm * (f * f * f);
-    return -beta * gs - a * f;
+  auto sync = [&]() {
+    if constexpr (TPP == 32) __syncwarp();
+    else __syncthreads();
   };
-  for (int s = t; s < D; s += 256) pm[s] += 0.5 * eps * grad(s);
-  __syncthreads();
+  // y += h e g(x) over the own sites, neighbours from the row `cur`
+  auto kick = [&](const T* __restrict__ cur, T h) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (k * TPP < D) {
+        const int s = t + k * TPP;
+        if (live && s < D) {
+          const T nb = (cur[lr[k] & 0xffffu] + cur[lr[k] >> 16]) + (cur[ud[k] & 0xffffu] + cur[ud[k] >> 16]);
+          const T f = x[k];
+          const T gr = fma(C, f * f * f, fma(A, f, B * nb));
+          y[k] = fma(h * e[k], gr, y[k]);
+        }
+      }
+    }
+  };
+  sync();
+  kick(buf0, T(0.5));
+  T* cur = buf0;
   for (int l = 0; l < n_leap; ++l) {
-    for (int s = t; s < D; s += 256) x[s] += eps * v[s] * pm[s];
-    __syncthreads();
-    const double h = l + 1 < n_leap ? eps : 0.5 * eps;
-    for (int s = t; s < D; s += 256) pm[s] += h * grad(s);
-    __syncthreads();
+    T* nxt = cur == buf0 ? buf1 : buf0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int s = t + k * TPP;
+      if (k * TPP < D && live && s < D) {
+        x[k] = fma(e[k], y[k], x[k]);
+        nxt[s] = x[k];
+      }
+    }
+    sync();
+    cur = nxt;
+    kick(cur, l + 1 < n_leap ? T(1) : T(0.5));
   }
   double s_new = 0.0, q_new = 0.0, kin1 = 0.0;
-  site_sums<double, 256>(x, L, D, t, k, s_new, q_new);
-  for (int s = t; s < D; s += 256) kin1 += v[s] * pm[s] * pm[s];
-  s_new = block_sum(s_new, red);
-  q_new = block_sum(q_new, red);
-  kin0 = block_sum(kin0, red);
-  kin1 = block_sum(kin1, red);
-  if (t == 0) {
+  if (live) site_sums<T, TPP>(cur, L, D, t, coefs<T>(p), s_new, q_new);
+#pragma unroll
+  for (int k = 0; k < K; ++k) kin1 += (double)y[k] * (double)y[k];
+  group_sum2<TPP>(s_new, q_new, red);
+  group_sum2<TPP>(kin0, kin1, red);
+  if (live && t == 0) {
     const double dS = s_new - S[i], dq = q_new - sq[i];
     const double log_alpha = (keep_ref ? (-beta * dS - 0.5 * dq) : (-beta * dS - (1.0 - beta) * 0.5 * dq)) -
                              0.5 * (kin1 - kin0);
@@ -209,7 +250,7 @@ __global__ void __launch_bounds__(256) hmc_kernel(double* __restrict__ phi, cons
       atomicOr(status, ST_NONFINITE);
       acc = 0;
     }
-    accept_flag = acc;
+    accept_flag[g] = acc;
     if (acc) {
       S[i] = s_new;
       sq[i] = q_new;
@@ -217,25 +258,64 @@ __global__ void __launch_bounds__(256) hmc_kernel(double* __restrict__ phi, cons
       atomicAdd(acc_count, 1u);
     }
   }
-  __syncthreads();
-  if (accept_flag)
-    for (int s = t; s < D; s += 256) phi[(size_t)i * D + s] = x[s];
+  sync();
+  if (live && accept_flag[g]) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int s = t + k * TPP;
+      if (k * TPP < D && s < D) phi[(size_t)i * D + s] = x[k];
+    }
+  }
 }
 
-cudaError_t launch_hmc(double* phi, const double* Z, const double* sigma, const double* ridge, const ActionParams& p,
-                       int keep_reference, double* S, double* sq, double* ell, const double* beta, double eps,
-                       int n_leap, uint64_t seed, uint64_t stream_id, uint32_t step, uint32_t sweep,
-                       uint32_t* acc_count, uint32_t* status, cudaStream_t s) {
-  if (p.N <= 0) return cudaSuccess;
-  const size_t sm = (size_t)3 * p.D * sizeof(double);
+namespace {
+template <typename T, int TPP, int K>
+cudaError_t hmc_go(T* phi, const T* Z, const double* sigma, const double* ridge, const ActionParams& p, int keep,
+                   double* S, double* sq, double* ell, const double* beta, double eps, int n_leap, PhiloxKey key,
+                   uint32_t w0, uint32_t sweep, uint32_t* acc_count, uint32_t* status, cudaStream_t s) {
+  constexpr int PPB = 256 / TPP;
+  const size_t sm = (size_t)PPB * 2 * p.D * sizeof(T);
   if (sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(hmc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(hmc_kernel<T, TPP, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
-  hmc_kernel<<<p.N, 256, sm, s>>>(phi, Z, sigma, ridge, p, keep_reference, S, sq, ell, beta, eps, n_leap,
-                                 philox_key(seed, stream_id), counter_word0(RNG_ACCEPT, step), sweep, acc_count,
-                                 status);
+  hmc_kernel<T, TPP, K><<<(unsigned)((p.N + PPB - 1) / PPB), 256, sm, s>>>(
+      phi, Z, sigma, ridge, p, keep, S, sq, ell, beta, eps, n_leap, key, w0, sweep, acc_count, status);
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t hmc_t(T* phi, const T* Z, const double* sigma, const double* ridge, const ActionParams& p, int keep,
+                  double* S, double* sq, double* ell, const double* beta, double eps, int n_leap, PhiloxKey key,
+                  uint32_t w0, uint32_t sweep, uint32_t* acc_count, uint32_t* status, cudaStream_t s) {
+  const int D = p.D;
+#define PHI4_HMC_GO(TPP, K) \
+  return hmc_go<T, TPP, K>(phi, Z, sigma, ridge, p, keep, S, sq, ell, beta, eps, n_leap, key, w0, sweep, acc_count, \
+                           status, s)
+  if (D <= 128) PHI4_HMC_GO(32, 4);
+  if (D <= 256) PHI4_HMC_GO(32, 8);
+  if (D <= 512) PHI4_HMC_GO(32, 16);
+  if (D <= 2048) PHI4_HMC_GO(256, 8);
+  if (D <= 4096) PHI4_HMC_GO(256, 16);
+#undef PHI4_HMC_GO
+  return cudaErrorInvalidValue;
+}
+}  // namespace
+
+cudaError_t launch_hmc(void* phi, const void* Z, int dtype, const double* sigma, const double* ridge,
+                       const ActionParams& p, int keep_reference, double* S, double* sq, double* ell,
+                       const double* beta, double eps, int n_leap, uint64_t seed, uint64_t stream_id, uint32_t step,
+                       uint32_t sweep, uint32_t* acc_count, uint32_t* status, cudaStream_t s) {
+  if (p.N <= 0) return cudaSuccess;
+  const PhiloxKey key = philox_key(seed, stream_id);
+  const uint32_t w0 = counter_word0(RNG_ACCEPT, step);
+  if (dtype == 0)
+    return hmc_t<double>((double*)phi, (const double*)Z, sigma, ridge, p, keep_reference, S, sq, ell, beta, eps,
+                         n_leap, key, w0, sweep, acc_count, status, s);
+  if (dtype == 1)
+    return hmc_t<float>((float*)phi, (const float*)Z, sigma, ridge, p, keep_reference, S, sq, ell, beta, eps, n_leap,
+                        key, w0, sweep, acc_count, status, s);
+  return cudaErrorInvalidValue;
 }
 
 // Metropolis decision log u < log alpha for u in (0, 1] (53-bit), taken exactly as in

@@ -10,7 +10,7 @@ The library's log Z in this mode is log E_{N(0,I)}[exp(-S_E)]; the values the pa
 (V/4) log(pi) at all three sizes, so `logz_paper_convention` reports that difference too.
 
     python -m paper_2511_15196_gb300.ess_sweep [--ess 0.9 0.99 0.999] [--seeds 4] [--n-mcmc 300] [--L 10]
-                                               [--irmh | --hmc]
+                                               [--irmh | --hmc] [--fp32]
 """
 import argparse
 import json
@@ -39,18 +39,21 @@ def run_one(cfg):
     return obs, ms
 
 
-def sweep(ess_targets, seeds, n_mcmc=None, N=5000, L=10, kind=None):
-    """n_mcmc defaults to 3 V (App. A); kind: SMC_RW (default), SMC_IRMH or SMC_HMC."""
+def sweep(ess_targets, seeds, n_mcmc=None, N=5000, L=10, kind=None, precision=None):
+    """n_mcmc defaults to 3 V (App. A); kind: SMC_RW (default), SMC_IRMH or SMC_HMC;
+    precision: FP64 (default), FP32 or MIXED_BF16."""
     if n_mcmc is None:
         n_mcmc = 3 * L * L
     rows = []
     for ess in ess_targets:
-        res = [run_one(paper_config(ess, s, n_mcmc=n_mcmc, N=N, L=L, kind=kind)) for s in range(seeds)]
+        res = [run_one(paper_config(ess, s, n_mcmc=n_mcmc, N=N, L=L, kind=kind, precision=precision))
+               for s in range(seeds)]
         lz = [o["logz"] for o, _ in res]
         m = sum(lz) / len(lz)
         sd = math.sqrt(sum((x - m) ** 2 for x in lz) / max(len(lz) - 1, 1))
         rows.append({"ess_target": ess, "seeds": seeds, "logz_mean": m, "logz_sd": sd,
                      "L": L, "kind": {2: "irmh", 3: "hmc"}.get(kind, "rw"),
+                     "precision": {1: "fp32", 2: "mixed_bf16"}.get(precision, "fp64"),
                      "logz_paper_convention": m - L * L / 4 * math.log(math.pi),
                      "temperatures": sum(o["n_steps"] for o, _ in res) / len(res),
                      "likelihood_evals": sum(o["n_likelihood_evals"] for o, _ in res) / len(res),
@@ -69,9 +72,10 @@ def main():
     ap.add_argument("--L", type=int, default=10)
     ap.add_argument("--irmh", action="store_true", help="independent Metropolis-Hastings sweeps (SMC-IRMH)")
     ap.add_argument("--hmc", action="store_true", help="HMC transitions, 20 leapfrog steps (SMC-HMC)")
+    ap.add_argument("--fp32", action="store_true", help="the float arithmetic form")
     a = ap.parse_args()
     kind = 2 if a.irmh else 3 if a.hmc else None
-    for row in sweep(a.ess, a.seeds, n_mcmc=a.n_mcmc, N=a.N, L=a.L, kind=kind):
+    for row in sweep(a.ess, a.seeds, n_mcmc=a.n_mcmc, N=a.N, L=a.L, kind=kind, precision=1 if a.fp32 else None):
         print(json.dumps(row))
 
 

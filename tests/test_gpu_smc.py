@@ -107,7 +107,8 @@ def test_irmh_configuration_checks():
         p.Run(gpu_cfg(L=40, N=64, kind=p.SMC_IRMH))
 
 
-@pytest.mark.parametrize("L,N,keep", [(4, 512, False), (8, 1024, False), (3, 300, True), (16, 256, False)])
+@pytest.mark.parametrize("L,N,keep", [(4, 512, False), (8, 1024, False), (3, 300, True), (16, 256, False),
+                                      (24, 128, False), (46, 64, True)])
 def test_hmc_fp64_steps_match_oracle(L, N, keep):
     # SMC-HMC: the same momenta, leapfrog trajectories (20 steps, covariance-diagonal inverse
     # mass), energies and decisions as the oracle
@@ -127,9 +128,38 @@ def test_hmc_fp64_steps_match_oracle(L, N, keep):
     run.close()
 
 
+@pytest.mark.parametrize("L,N", [(8, 1024), (18, 300), (24, 256)], ids=["warp_per_particle", "D324", "cta_per_particle"])
+def test_hmc_fp32_step_close_to_oracle(L, N):
+    # the float form of the same transition: float leapfrog trajectories, energies summed in
+    # double. Against the double oracle on the same streams, particles whose decisions and
+    # ancestors agree match to float rounding; a decision at the threshold may flip
+    run = p.Run(gpu_cfg(L=L, N=N, n_mcmc=2, seed=5, kind=p.SMC_HMC, precision=p.FP32))
+    ref = SMC(oracle_cfg(L=L, N=N, n_mcmc=2, seed=5, inner="hmc"))
+    beta = run.temper_step()
+    rec = ref.temper_step()
+    assert beta == pytest.approx(rec["beta"], rel=1e-5)
+    phi = run.particles().cpu().numpy().astype(np.float64)
+    close = np.abs(phi - ref.phi).max(axis=1) < 1e-3
+    assert close.mean() >= 0.99, close.mean()
+    assert abs(run.observables()["acc_rate"] - rec["acc_rate"]) <= 0.01
+    run.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", [p.FP64, p.FP32], ids=["fp64", "fp32"])
+def test_broken_phase_hmc_16_seeds(precision):
+    # L = 8, N = 1024, m2 = -4, lambda = 8: SMC-HMC runs to beta = 1 agree with the oracle's
+    # in log Z, <|M|> and chi within three standard errors of the seed-to-seed spread
+    g = _gpu_runs(16, kind=p.SMC_HMC, n_mcmc=3, precision=precision)
+    o = _oracle_runs(16, inner="hmc", n_mcmc=3)
+    _within_3se(g, o)
+    if precision == p.FP64:
+        assert np.abs(g[:, 0] - o[:, 0]).max() < 1e-6
+
+
 def test_hmc_configuration_checks():
     with pytest.raises(RuntimeError):
-        p.Run(gpu_cfg(L=8, N=64, kind=p.SMC_HMC, precision=p.FP32))
+        p.Run(gpu_cfg(L=8, N=64, kind=p.SMC_HMC, precision=p.MIXED_BF16))
     with pytest.raises(RuntimeError):
         p.Run(gpu_cfg(L=72, N=64, kind=p.SMC_HMC))
 
