@@ -15,6 +15,7 @@ proposals, normals: about 320 MiB per sweep) is larger than L2, so no flush is
 needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp32|fp64]
+  python bench.py --sampler hmc --precision fp32   # SMC-HMC steps (20 leapfrog steps per transition)
   python bench.py --impl reference     # the FP64 CPU oracle on a bounded sample
 
 With --gpus N > 1 (torchrun) each rank advances its own independent replica
@@ -52,6 +53,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=2048, help="particles in the oracle's bounded sample")
+    ap.add_argument("--sampler", default="rw", choices=["rw", "hmc"],
+                    help="rw: random-walk sweeps (default); hmc: HMC transitions (fp32 or fp64)")
     ap.add_argument("--workload", default="single", choices=["single", "batch", "kernels"],
                     help="single: one L=64 run; batch: 64 independent runs of mixed lattice sizes")
     ap.add_argument("--batch-runs", type=int, default=64)
@@ -159,8 +162,28 @@ def run_kernels(a):
     return 0
 
 
+HMC_LEAPFROG = 20
+# algorithmic work of one HMC transition per site: 21 momentum kicks (gradient: 3 adds for
+# the neighbour sum, 2 multiplies for x^3, A x + B nb + C x^3 as a multiply and 2 FMAs, then
+# the FMA y += h e g: 12 flop) and 20 drifts (one FMA: 2 flop); shared-memory traffic: 4
+# neighbour loads per kick and one store per drift
+HMC_FLOP_PER_SITE = (HMC_LEAPFROG + 1) * 12 + HMC_LEAPFROG * 2
+
+
+def hmc_smem_bytes_per_site(prec):
+    return ((HMC_LEAPFROG + 1) * 4 + HMC_LEAPFROG) * (8 if prec == 0 else 4)
+
+
 def workload(a):
     D = a.L * a.L
+    if a.sampler == "hmc":
+        return {"workload": "SMC-HMC tempering step, broken-phase phi^4 L=%d (D=%d), N=%d, m2=-4, lambda=8, "
+                            "%d HMC transitions/temperature (%d leapfrog steps, covariance-diagonal inverse mass), "
+                            "ESS 0.5N, %s" % (a.L, D, a.N, a.n_mcmc, HMC_LEAPFROG, a.precision),
+                "sampler": "hmc", "L": a.L, "D": D, "N": a.N, "n_mcmc": a.n_mcmc, "m2": -4.0, "lambda": 8.0,
+                "ess_target": 0.5, "precision": a.precision,
+                "l2": "inputs larger than L2 (fields %d MiB + normals per transition)"
+                      % (a.N * D * (8 if a.precision == "fp64" else 4) >> 20)}
     return {"workload": "SMC-RW tempering step, broken-phase phi^4 L=%d (D=%d), N=%d, m2=-4, lambda=8, "
                         "%d RWM sweeps/temperature, ESS 0.5N, %s" % (a.L, D, a.N, a.n_mcmc, a.precision),
             "L": a.L, "D": D, "N": a.N, "n_mcmc": a.n_mcmc, "m2": -4.0, "lambda": 8.0, "ess_target": 0.5,
@@ -263,13 +286,20 @@ def kernel_traffic(kernel):
     return d["bytes_per_launch"]
 
 
+def cpu_sample(a):
+    """Particles in the oracle's bounded sample (an HMC transition costs about 21 gradient
+    evaluations, so its sample is smaller)."""
+    return a.cpu_sample if a.sampler == "rw" else min(a.cpu_sample, 128)
+
+
 def cpu_baseline(a, sample):
     """The FP64 oracle (test infrastructure, untuned) on a bounded sample of the workload:
     one temperature step from beta = 0 with `sample` particles of the same lattice."""
     import numpy as np
     from oracle.smc import SMC, SMCConfig
     cfg = SMCConfig(L=a.L, N=sample, m2=-4.0, lam=8.0, rho=0.5, n_mcmc=a.n_mcmc, seed=0,
-                    normal_bits=32 if a.precision == "fp64" else 24)
+                    normal_bits=32 if a.precision == "fp64" else 24,
+                    inner="hmc" if a.sampler == "hmc" else "rw")
     smc = SMC(cfg)
     t0 = time.perf_counter()
     smc.temper_step()
@@ -283,8 +313,8 @@ def cpu_baseline(a, sample):
     del np
     return {"value": sample * D * a.n_mcmc / dt, "unit": "site-updates/s", "cores": cores, "kind": "oracle",
             "sample": "one temperature step (ESS bisection, resampling, covariance + Cholesky of the D x D "
-                      "covariance, %d RWM sweeps) with N=%d of the %d particles, L=%d; %.1f s"
-                      % (a.n_mcmc, sample, a.N, a.L, dt)}
+                      "covariance, %d %s) with N=%d of the %d particles, L=%d; %.1f s"
+                      % (a.n_mcmc, "HMC transitions" if a.sampler == "hmc" else "RWM sweeps", sample, a.N, a.L, dt)}
 
 
 def run_reference(a):
@@ -295,12 +325,12 @@ def run_reference(a):
     for _ in range(a.warmup):
         pass
     for _ in range(max(1, a.steps)):
-        res.append(cpu_baseline(a, a.cpu_sample))
+        res.append(cpu_baseline(a, cpu_sample(a)))
     v = statistics.median(r["value"] for r in res)
     cb = dict(res[0])
     cb["value"] = v
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "site-updates/s", "n_gpus": a.gpus,
-            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * a.cpu_sample * a.L ** 2 * a.n_mcmc / v,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * cpu_sample(a) * a.L ** 2 * a.n_mcmc / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp64",
             "data": "synthetic (Philox N(0,I) initial fields)", "config": workload(a), "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -323,8 +353,11 @@ def main():
     torch.cuda.set_device(local)
     D = a.L * a.L
     prec = PREC[a.precision]
+    hmc = a.sampler == "hmc"
+    if hmc and prec == 2:
+        raise SystemExit("--sampler hmc runs in the fp32 or fp64 form")
     cfg = p.Config(L=a.L, N=a.N, m2=-4.0, lam=8.0, precision=prec, n_mcmc=a.n_mcmc, ess_target=0.5,
-                   seed=1000 + rank)
+                   seed=1000 + rank, kind=p.SMC_HMC if hmc else p.SMC_RW)
     stream = torch.cuda.current_stream()
 
     def fresh():
@@ -401,6 +434,16 @@ def main():
         work = ("tensor", units, "TFLOP/s")
         extra = {"fp64_equivalent_tflops": 2 * 64 * elems * n_fact / (ms_tot * 1e-3) / 1e12,
                  "factorizations": n_fact}
+    elif hmc and dom == "accept":
+        # the HMC transition kernel (timed as the accept stage): FMA-unit work of the
+        # leapfrog trajectory; its shared-memory traffic against the derived shared-memory
+        # bandwidth (128 B per SM per cycle) is reported beside it
+        work = ("alu", a.N * D * HMC_FLOP_PER_SITE, "TFLOP/s")
+        smem = a.N * D * hmc_smem_bytes_per_site(prec)
+        smem_peak = 152 * 2070e6 * 128 / 1e9
+        extra = {"kernel_name": "hmc_kernel", "smem_bytes_per_launch": smem,
+                 "smem_gbs": smem / avg_s / 1e9, "smem_peak_gbs": smem_peak,
+                 "smem_frac": smem / avg_s / 1e9 / smem_peak}
     else:
         work = {
             # the mixed form's proposal runs on the tensor cores, the FP32 / FP64 forms' on the
@@ -477,7 +520,7 @@ def main():
         del lz
         r2.close()
     if rank == 0 and not a.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(a, a.cpu_sample)
+        line["cpu_baseline"] = cpu_baseline(a, cpu_sample(a))
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:

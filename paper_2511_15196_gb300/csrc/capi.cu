@@ -138,6 +138,7 @@ void lay_out(phi4_run* r, Layout& L) {
   r->cov_scratch = L.take(r->cov_scratch_bytes);
   r->bisect_scratch = L.take(bisect_scratch_bytes(N));
   r->resample_scratch = L.take(resample_scratch_bytes(N));
+  if (c.kind == PHI4_SMC_HMC) r->hmc_e = (double*)L.take((size_t)D * 8);
   if (c.kind == PHI4_SMC_IRMH) {
     r->irmh_r = (double*)L.take(N * 8);
     r->irmh_zz = (double*)L.take(N * 8);
@@ -378,6 +379,11 @@ static phi4_status step_sweeps(phi4_run* r) {
   if (c.kind == PHI4_SMC_HMC) {
     // HMC transitions with the refit's covariance diagonal (plus the ridge) as inverse mass
     const double eps = c.rw_scale > 0.0 ? c.rw_scale : 0.8 * pow((double)D, -0.25);
+    {
+      StageScope sc(r, STG_OTHER);
+      CUDA_TRY(launch_hmc_scale(r->sigma, D, r->scal + SC_RIDGE, eps, r->hmc_e, s));
+      r->kernel_launches += 1;
+    }
     for (int sweep = 0; sweep < c.n_mcmc; ++sweep) {
       {
         StageScope sc(r, STG_NORMALS);
@@ -385,9 +391,9 @@ static phi4_status step_sweeps(phi4_run* r) {
                                 s));
       }
       StageScope sc(r, STG_ACCEPT);
-      CUDA_TRY(launch_hmc(r->phi, r->Z, r->zdtype, r->sigma, r->scal + SC_RIDGE, ap, c.keep_reference, r->S, r->sq,
-                          r->ell, r->scal + SC_BETA, eps, kHmcLeapfrog, c.seed, c.stream_id, t, (uint32_t)sweep,
-                          r->acc_count, r->status, s));
+      CUDA_TRY(launch_hmc(r->phi, r->Z, r->zdtype, r->hmc_e, ap, c.keep_reference, r->S, r->sq, r->ell,
+                          r->scal + SC_BETA, kHmcLeapfrog, c.seed, c.stream_id, t, (uint32_t)sweep, r->acc_count,
+                          r->status, s));
       r->kernel_launches += 2;
     }
     r->n_evals += (int64_t)N * c.n_mcmc * (kHmcLeapfrog + 1);

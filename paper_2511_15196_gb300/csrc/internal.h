@@ -36,15 +36,18 @@ cudaError_t launch_accept(void* phi, const void* prop, int dtype, const ActionPa
 cudaError_t launch_whitened_sq_norm(const double* phi, const double* mu, const double* Lf, int ld, int N, int D,
                                     double* r, cudaStream_t s);
 cudaError_t launch_row_sq_norm(const double* Z, int N, int D, double* zz, cudaStream_t s);
-// SMC-HMC (kernels_lattice.cu): one HMC transition per particle, D <= 4096, fields and Z
-// of `dtype` (F64 or F32; the energies in double): inverse mass v_s = sigma_ss + *ridge,
-// momenta Z / sqrt(v), n_leap leapfrog steps of size eps on the tempered target at *beta,
-// accept on the Philox RNG_ACCEPT uniform of (step, sweep)
+// SMC-HMC (kernels_lattice.cu): escale_s = eps sqrt(sigma_ss + *ridge) (D doubles), once per
+// temperature; then one HMC transition per particle, D <= 4096, fields and Z of `dtype`
+// (F64 or F32; the energies in double): momenta Z / sqrt(v) with inverse mass
+// v_s = sigma_ss + ridge, n_leap leapfrog steps of size eps on the tempered target at
+// *beta, accept on the Philox RNG_ACCEPT uniform of (step, sweep)
 constexpr int kHmcLeapfrog = 20;  // App. A
-cudaError_t launch_hmc(void* phi, const void* Z, int dtype, const double* sigma, const double* ridge,
-                       const ActionParams& p, int keep_reference, double* S, double* sq, double* ell,
-                       const double* beta, double eps, int n_leap, uint64_t seed, uint64_t stream_id, uint32_t step,
-                       uint32_t sweep, uint32_t* acc_count, uint32_t* status, cudaStream_t s);
+cudaError_t launch_hmc_scale(const double* sigma, int D, const double* ridge, double eps, double* escale,
+                             cudaStream_t s);
+cudaError_t launch_hmc(void* phi, const void* Z, int dtype, const double* escale, const ActionParams& p,
+                       int keep_reference, double* S, double* sq, double* ell, const double* beta, int n_leap,
+                       uint64_t seed, uint64_t stream_id, uint32_t step, uint32_t sweep, uint32_t* acc_count,
+                       uint32_t* status, cudaStream_t s);
 // float fields, proposal = phi + delta (fp16 increment), L % 4 == 0
 cudaError_t launch_accept_delta(float* phi, const void* delta_f16, const ActionParams& p, int keep_reference,
                                 double* S, double* sq, double* ell, const double* beta, uint64_t seed,

@@ -150,20 +150,52 @@ __global__ void __launch_bounds__(PPB* TPP) accept_kernel(T* __restrict__ phi, c
 //       = A x_s + B nb_s + C x_s^3,
 // a = 1 - beta (1 with the reference kept). Accept when log u < H(start) - H(end) with
 // H = beta S + a |x|^2 / 2 + |y|^2 / 2, the sums in double.
-// TPP threads per particle (256 / TPP particles per CTA); thread t of a group owns sites
+
+// e_s = eps sqrt(Sigma_ss + ridge), once per temperature
+__global__ void hmc_scale_kernel(const double* __restrict__ sigma, int D, const double* __restrict__ ridge,
+                                 double eps, double* __restrict__ e) {
+  const double dl = *ridge;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < D; s += gridDim.x * blockDim.x)
+    e[s] = eps * sqrt(sigma[(size_t)s * D + s] + dl);
+}
+
+// Sum (a, b) over the TPP threads of each particle's group; valid in the group's thread 0.
+template <int TPP>
+PHI4_DEV void hmc_group_sum2(double& a, double& b, double* red) {
+  a = warp_sum(a);
+  b = warp_sum(b);
+  if constexpr (TPP > 32) {
+    constexpr int WPG = TPP / 32;
+    const int w = threadIdx.x >> 5, g = threadIdx.x / TPP;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+      red[2 * w] = a;
+      red[2 * w + 1] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x % TPP == 0) {
+      a = b = 0.0;
+      for (int k = 0; k < WPG; ++k) {
+        a += red[2 * (g * WPG + k)];
+        b += red[2 * (g * WPG + k) + 1];
+      }
+    }
+  }
+}
+
+// TPP threads per particle, max(TPP, 256) threads per CTA; thread t of a group owns sites
 // t + k TPP (k < K) in registers: its field, y and e, and the four neighbour indices. The
 // field also lives in a double-buffered shared row so neighbours can read it: one barrier
 // per leapfrog step (the buffer written at step l was last read at step l - 2, before the
 // barrier of step l - 1).
 template <typename T, int TPP, int K>
-__global__ void __launch_bounds__(256) hmc_kernel(T* __restrict__ phi, const T* __restrict__ Z,
-                                                  const double* __restrict__ sigma, const double* __restrict__ ridge,
-                                                  ActionParams p, int keep_ref, double* __restrict__ S,
-                                                  double* __restrict__ sq, double* __restrict__ ell,
-                                                  const double* __restrict__ beta_ptr, double eps, int n_leap,
-                                                  PhiloxKey key, uint32_t w0, uint32_t sweep,
-                                                  uint32_t* __restrict__ acc_count, uint32_t* __restrict__ status) {
-  constexpr int PPB = 256 / TPP;
+__global__ void __launch_bounds__(TPP < 256 ? 256 : TPP)
+    hmc_kernel(T* __restrict__ phi, const T* __restrict__ Z, const double* __restrict__ escale, ActionParams p,
+               int keep_ref, double* __restrict__ S, double* __restrict__ sq, double* __restrict__ ell,
+               const double* __restrict__ beta_ptr, int n_leap, PhiloxKey key, uint32_t w0, uint32_t sweep,
+               uint32_t* __restrict__ acc_count, uint32_t* __restrict__ status) {
+  constexpr int NT = TPP < 256 ? 256 : TPP;
+  constexpr int PPB = NT / TPP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[64];
   __shared__ int accept_flag[PPB];
@@ -173,7 +205,7 @@ __global__ void __launch_bounds__(256) hmc_kernel(T* __restrict__ phi, const T* 
   const bool live = i < p.N;
   T* buf0 = reinterpret_cast<T*>(smem_raw) + (size_t)g * 2 * D;
   T* buf1 = buf0 + D;
-  const double beta = *beta_ptr, a = keep_ref ? 1.0 : 1.0 - beta, dl = *ridge;
+  const double beta = *beta_ptr, a = keep_ref ? 1.0 : 1.0 - beta;
   const T A = (T)(-beta * (8.0 * p.c_kin + 2.0 * p.c_mass * p.m2) - a);
   const T B = (T)(2.0 * beta * p.c_kin);
   const T C = (T)(-4.0 * beta * p.lam);
@@ -194,12 +226,12 @@ __global__ void __launch_bounds__(256) hmc_kernel(T* __restrict__ phi, const T* 
       x[k] = phi[(size_t)i * D + s];
       buf0[s] = x[k];
       y[k] = Z[(size_t)i * D + s];
-      e[k] = (T)(eps * sqrt(sigma[(size_t)s * D + s] + dl));
+      e[k] = (T)escale[s];
       kin0 += (double)y[k] * (double)y[k];
     }
   }
   auto sync = [&]() {
-    if constexpr (TPP == 32) __syncwarp();
+    if constexpr (NT == 32) __syncwarp();
     else __syncthreads();
   };
   // y += h e g(x) over the own sites, neighbours from the row `cur`
@@ -238,8 +270,8 @@ __global__ void __launch_bounds__(256) hmc_kernel(T* __restrict__ phi, const T* 
   if (live) site_sums<T, TPP>(cur, L, D, t, coefs<T>(p), s_new, q_new);
 #pragma unroll
   for (int k = 0; k < K; ++k) kin1 += (double)y[k] * (double)y[k];
-  group_sum2<TPP>(s_new, q_new, red);
-  group_sum2<TPP>(kin0, kin1, red);
+  hmc_group_sum2<TPP>(s_new, q_new, red);
+  hmc_group_sum2<TPP>(kin0, kin1, red);
   if (live && t == 0) {
     const double dS = s_new - S[i], dq = q_new - sq[i];
     const double log_alpha = (keep_ref ? (-beta * dS - 0.5 * dq) : (-beta * dS - (1.0 - beta) * 0.5 * dq)) -
@@ -270,51 +302,56 @@ __global__ void __launch_bounds__(256) hmc_kernel(T* __restrict__ phi, const T* 
 
 namespace {
 template <typename T, int TPP, int K>
-cudaError_t hmc_go(T* phi, const T* Z, const double* sigma, const double* ridge, const ActionParams& p, int keep,
-                   double* S, double* sq, double* ell, const double* beta, double eps, int n_leap, PhiloxKey key,
-                   uint32_t w0, uint32_t sweep, uint32_t* acc_count, uint32_t* status, cudaStream_t s) {
-  constexpr int PPB = 256 / TPP;
+cudaError_t hmc_go(T* phi, const T* Z, const double* escale, const ActionParams& p, int keep, double* S, double* sq,
+                   double* ell, const double* beta, int n_leap, PhiloxKey key, uint32_t w0, uint32_t sweep,
+                   uint32_t* acc_count, uint32_t* status, cudaStream_t s) {
+  constexpr int NT = TPP < 256 ? 256 : TPP;
+  constexpr int PPB = NT / TPP;
   const size_t sm = (size_t)PPB * 2 * p.D * sizeof(T);
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(hmc_kernel<T, TPP, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
-  hmc_kernel<T, TPP, K><<<(unsigned)((p.N + PPB - 1) / PPB), 256, sm, s>>>(
-      phi, Z, sigma, ridge, p, keep, S, sq, ell, beta, eps, n_leap, key, w0, sweep, acc_count, status);
+  hmc_kernel<T, TPP, K><<<(unsigned)((p.N + PPB - 1) / PPB), NT, sm, s>>>(
+      phi, Z, escale, p, keep, S, sq, ell, beta, n_leap, key, w0, sweep, acc_count, status);
   return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t hmc_t(T* phi, const T* Z, const double* sigma, const double* ridge, const ActionParams& p, int keep,
-                  double* S, double* sq, double* ell, const double* beta, double eps, int n_leap, PhiloxKey key,
-                  uint32_t w0, uint32_t sweep, uint32_t* acc_count, uint32_t* status, cudaStream_t s) {
-  const int D = p.D;
-#define PHI4_HMC_GO(TPP, K) \
-  return hmc_go<T, TPP, K>(phi, Z, sigma, ridge, p, keep, S, sq, ell, beta, eps, n_leap, key, w0, sweep, acc_count, \
-                           status, s)
-  if (D <= 128) PHI4_HMC_GO(32, 4);
-  if (D <= 256) PHI4_HMC_GO(32, 8);
-  if (D <= 512) PHI4_HMC_GO(32, 16);
-  if (D <= 2048) PHI4_HMC_GO(256, 8);
-  if (D <= 4096) PHI4_HMC_GO(256, 16);
-#undef PHI4_HMC_GO
-  return cudaErrorInvalidValue;
 }
 }  // namespace
 
-cudaError_t launch_hmc(void* phi, const void* Z, int dtype, const double* sigma, const double* ridge,
-                       const ActionParams& p, int keep_reference, double* S, double* sq, double* ell,
-                       const double* beta, double eps, int n_leap, uint64_t seed, uint64_t stream_id, uint32_t step,
-                       uint32_t sweep, uint32_t* acc_count, uint32_t* status, cudaStream_t s) {
+cudaError_t launch_hmc_scale(const double* sigma, int D, const double* ridge, double eps, double* escale,
+                             cudaStream_t s) {
+  hmc_scale_kernel<<<(unsigned)((D + 255) / 256), 256, 0, s>>>(sigma, D, ridge, eps, escale);
+  return cudaGetLastError();
+}
+
+// Layouts: each thread owns at most 4 sites (float) or 8 (double), so the float form keeps
+// about 64 registers and 1024-thread CTAs at D = 4096 (32 warps per SM).
+cudaError_t launch_hmc(void* phi, const void* Z, int dtype, const double* escale, const ActionParams& p,
+                       int keep_reference, double* S, double* sq, double* ell, const double* beta, int n_leap,
+                       uint64_t seed, uint64_t stream_id, uint32_t step, uint32_t sweep, uint32_t* acc_count,
+                       uint32_t* status, cudaStream_t s) {
   if (p.N <= 0) return cudaSuccess;
   const PhiloxKey key = philox_key(seed, stream_id);
   const uint32_t w0 = counter_word0(RNG_ACCEPT, step);
-  if (dtype == 0)
-    return hmc_t<double>((double*)phi, (const double*)Z, sigma, ridge, p, keep_reference, S, sq, ell, beta, eps,
-                         n_leap, key, w0, sweep, acc_count, status, s);
-  if (dtype == 1)
-    return hmc_t<float>((float*)phi, (const float*)Z, sigma, ridge, p, keep_reference, S, sq, ell, beta, eps, n_leap,
-                        key, w0, sweep, acc_count, status, s);
+  const int D = p.D;
+#define PHI4_HMC_GO(T, TPP, K)                                                                                   \
+  return hmc_go<T, TPP, K>((T*)phi, (const T*)Z, escale, p, keep_reference, S, sq, ell, beta, n_leap, key, w0, \
+                           sweep, acc_count, status, s)
+  if (dtype == 0) {
+    if (D <= 256) PHI4_HMC_GO(double, 32, 8);
+    if (D <= 512) PHI4_HMC_GO(double, 64, 8);
+    if (D <= 1024) PHI4_HMC_GO(double, 128, 8);
+    if (D <= 2048) PHI4_HMC_GO(double, 256, 8);
+    if (D <= 4096) PHI4_HMC_GO(double, 512, 8);
+  } else if (dtype == 1) {
+    if (D <= 128) PHI4_HMC_GO(float, 32, 4);
+    if (D <= 256) PHI4_HMC_GO(float, 64, 4);
+    if (D <= 512) PHI4_HMC_GO(float, 128, 4);
+    if (D <= 1024) PHI4_HMC_GO(float, 256, 4);
+    if (D <= 2048) PHI4_HMC_GO(float, 512, 4);
+    if (D <= 4096) PHI4_HMC_GO(float, 1024, 4);
+  }
+#undef PHI4_HMC_GO
   return cudaErrorInvalidValue;
 }
 

@@ -29,6 +29,7 @@ struct phi4_run {
   double *w = nullptr, *M = nullptr, *sigma = nullptr, *chol = nullptr, *scal = nullptr;
   int32_t* anc = nullptr;
   double *irmh_r = nullptr, *irmh_zz = nullptr;  // SMC-IRMH: whitened |L^-1 (phi - mu)|^2, |z|^2
+  double* hmc_e = nullptr;                        // SMC-HMC: leapfrog scales eps sqrt(Sigma_ss + ridge)
   uint32_t *status = nullptr, *acc_count = nullptr;
   void *cov_scratch = nullptr, *bisect_scratch = nullptr, *resample_scratch = nullptr;
   size_t cov_scratch_bytes = 0;
