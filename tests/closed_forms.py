@@ -72,6 +72,22 @@ def free_field_sample(L, m2, beta, n, rng, c_kin=1.0, c_mass=1.0):
     return (xi / np.sqrt(2.0 * evals)) @ evecs.T
 
 
+def free_field_covariance(L, m2, beta, keep_reference=False, c_kin=1.0, c_mass=1.0):
+    """Covariance of gamma_beta for the free field, from the quadratic form written out site
+    by site: precision a I + 2 beta A with a = 1 - beta (1 with the reference kept) and
+    S = phi^T A phi."""
+    D = L * L
+    A = np.zeros((D, D))
+    for r in range(L):
+        for c in range(L):
+            x = r * L + c
+            A[x, x] += c_kin * 4.0 + c_mass * m2
+            for (rr, cc) in ((r, (c + 1) % L), (r, (c - 1) % L), ((r + 1) % L, c), ((r - 1) % L, c)):
+                A[x, rr * L + cc] -= c_kin
+    a = 1.0 if keep_reference else 1.0 - beta
+    return np.linalg.inv(a * np.eye(D) + 2.0 * beta * A)
+
+
 def one_site_logz(m2, lam, c_mass=1.0):
     f = lambda c: math.exp(-c_mass * m2 * c * c - lam * c ** 4)
     val, err = integrate.quad(f, -np.inf, np.inf, epsabs=0, epsrel=1e-13, limit=200)

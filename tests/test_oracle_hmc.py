@@ -1,6 +1,7 @@
 """Pins for the HMC transition (SMC-HMC): the gradient against finite differences of the
 independently written action, leapfrog reversibility and its second-order energy error,
-near-certain acceptance for small steps, and the free-field evidence."""
+near-certain acceptance for small steps, invariance of the tempered free field under the
+transition, and the free-field evidence."""
 import math
 
 import numpy as np
@@ -59,3 +60,30 @@ def test_hmc_free_field_evidence():
     ref = cf.free_field_logz(2, 1.0)
     se = lz.std(ddof=1) / math.sqrt(len(lz))
     assert abs(lz.mean() + 0.5 * lz.var(ddof=1) - ref) < 4.0 * se + 0.01
+
+
+@pytest.mark.parametrize("keep_reference", [False, True])
+def test_invariance_free_field(keep_reference):
+    # exact draws from gamma_beta of the free field stay distributed as gamma_beta under HMC
+    # transitions with an inverse mass deliberately off the exact variances: a wrong kinetic
+    # or potential term in the Hamiltonian of the accept test moves E|phi|^2 and Var M (or
+    # starves the acceptance), and a wrong gradient starves the acceptance
+    L, m2, beta, N = 4, 1.0, 0.6, 20000
+    D = L * L
+    g = np.random.default_rng(21)
+    C = cf.free_field_covariance(L, m2, beta, keep_reference)
+    phi = g.standard_normal((N, D)) @ np.linalg.cholesky(C).T
+    want_sq, want_varM = float(np.trace(C)), float(C.sum()) / D ** 2
+    S, sq = lattice.action(phi, L, m2, 0.0), lattice.sq_norm(phi)
+    v = np.diag(C) * (0.5 + g.random(D))
+    accs = []
+    for s in range(4):
+        phi, S, sq, acc, _ = hmc.hmc_sweep(phi, S, sq, v, hmc.default_step(D), beta, L, m2, 0.0, 1.0, 1.0,
+                                           keep_reference, 3, 0, 1, s)
+        accs.append(acc.mean())
+    assert min(accs) > 0.6, accs
+    assert abs(sq.mean() - want_sq) < 4 * math.sqrt(np.var(sq) / N), (sq.mean(), want_sq)
+    varM = phi.mean(axis=1).var()
+    assert abs(varM - want_varM) < 4 * want_varM * math.sqrt(2.0 / N), (varM, want_varM)
+    np.testing.assert_allclose(S, lattice.action(phi, L, m2, 0.0), rtol=1e-12)
+    np.testing.assert_allclose(sq, lattice.sq_norm(phi), rtol=1e-12)

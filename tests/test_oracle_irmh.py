@@ -1,6 +1,7 @@
 """Pins for the independent Metropolis-Hastings sweep (SMC-IRMH): its acceptance ratio
 against the densities written out with scipy, exact acceptance when the proposal is the
-target, the whitened norm against a direct solve, and the free-field evidence."""
+target, the whitened norm against a direct solve, invariance of the tempered free field
+under sweeps with a mismatched proposal, and the free-field evidence."""
 import math
 
 import numpy as np
@@ -75,3 +76,30 @@ def test_irmh_free_field_evidence():
     ref = cf.free_field_logz(2, 1.0)
     se = lz.std(ddof=1) / math.sqrt(len(lz))
     assert abs(lz.mean() + 0.5 * lz.var(ddof=1) - ref) < 4.0 * se + 0.01
+
+
+@pytest.mark.parametrize("keep_reference", [False, True])
+def test_invariance_free_field(keep_reference):
+    # exact draws from gamma_beta of the free field stay distributed as gamma_beta under
+    # independence sweeps whose Gaussian proposal is shifted and 1.5 x too wide: only the
+    # Hastings factor q(phi) / q(phi') keeps E|phi|^2 and Var M where they are
+    L, m2, beta, N = 3, 1.0, 0.6, 20000
+    D = L * L
+    g = np.random.default_rng(22)
+    C = cf.free_field_covariance(L, m2, beta, keep_reference)
+    phi = g.standard_normal((N, D)) @ np.linalg.cholesky(C).T
+    want_sq, want_varM = float(np.trace(C)), float(C.sum()) / D ** 2
+    S, sq = lattice.action(phi, L, m2, 0.0), lattice.sq_norm(phi)
+    mu = 0.1 * np.ones(D)
+    Lc = np.linalg.cholesky(1.5 * C)
+    r = irmh.whitened_sq_norm(phi, mu, Lc)
+    accs = []
+    for s in range(6):
+        phi, S, sq, r, acc, _ = irmh.irmh_sweep(phi, S, sq, r, Lc, mu, beta, L, m2, 0.0, 1.0, 1.0, keep_reference,
+                                                4, 0, 1, s)
+        accs.append(acc.mean())
+    assert 0.2 < min(accs) and max(accs) < 0.95, accs
+    assert abs(sq.mean() - want_sq) < 4 * math.sqrt(np.var(sq) / N), (sq.mean(), want_sq)
+    varM = phi.mean(axis=1).var()
+    assert abs(varM - want_varM) < 4 * want_varM * math.sqrt(2.0 / N), (varM, want_varM)
+    np.testing.assert_allclose(r, irmh.whitened_sq_norm(phi, mu, Lc), rtol=1e-10)
