@@ -61,3 +61,15 @@ def test_reference_arm_prints_one_line_from_rank_0():
     line = json.loads(lines[0])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_reference_arm_hmc_workload():
+    # the HMC workload's reference arm: the oracle's HMC transitions on a bounded sample
+    cmd = [sys.executable, "bench.py", "--impl", "reference", "--sampler", "hmc", "--precision", "fp32", "--steps",
+           "1", "--warmup", "0", "--L", "4", "--N", "64", "--n-mcmc", "2", "--cpu-sample", "32"]
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=300,
+                       env=dict(os.environ, OMP_NUM_THREADS="1"))
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
+    line = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][-1])
+    assert line["config"]["sampler"] == "hmc" and line["value"] > 0
+    assert "HMC transitions" in line["cpu_baseline"]["sample"]
