@@ -57,3 +57,23 @@ def test_workspace_sizing_and_argument_checks(built):
     with pytest.raises(p.Phi4Error):
         p.workspace_bytes(p.Config(L=8, N=16, kind=p.NS_SLICE, ns_n_delete=16))
     assert b"ns_n_delete" in p.lib().phi4_last_error()
+
+
+def test_inner_kernel_configuration_rules_and_workspace(built):
+    # SMC-IRMH: FP64, D <= 1024; SMC-HMC: FP64 or FP32, D <= 4096; both SMC moves, so the Z2
+    # flag is accepted. Their extra buffers (whitened norms, leapfrog scales) are in the
+    # workspace.
+    import paper_2511_15196_gb300 as p
+    rw = p.workspace_bytes(p.Config(L=8, N=1024))
+    assert p.workspace_bytes(p.Config(L=8, N=1024, kind=p.SMC_IRMH)) >= rw + 2 * 1024 * 8
+    assert p.workspace_bytes(p.Config(L=8, N=1024, kind=p.SMC_HMC)) >= rw + 64 * 8
+    assert p.workspace_bytes(p.Config(L=64, N=64, kind=p.SMC_HMC, precision=p.FP32)) > 0
+    assert p.workspace_bytes(p.Config(L=32, N=64, kind=p.SMC_IRMH, flags=p.FLAG_Z2_FLIP)) > 0
+    for bad, word in ((p.Config(L=8, N=64, kind=p.SMC_IRMH, precision=p.FP32), b"SMC-IRMH"),
+                      (p.Config(L=33, N=64, kind=p.SMC_IRMH), b"SMC-IRMH"),
+                      (p.Config(L=8, N=64, kind=p.SMC_HMC, precision=p.MIXED_BF16), b"SMC-HMC"),
+                      (p.Config(L=65, N=64, kind=p.SMC_HMC), b"SMC-HMC"),
+                      (p.Config(L=8, N=64, kind=4), b"kind")):
+        with pytest.raises(p.Phi4Error):
+            p.workspace_bytes(bad)
+        assert word in p.lib().phi4_last_error()
