@@ -1,5 +1,6 @@
 """Pins for the nested-sampling oracle: the exact prior bracket, evidence on
-one site against quadrature and the error bar against the spread."""
+one site against quadrature and on the 2 x 2 torus against its transfer matrix, and the
+error bar sqrt(H / N) against the seed-to-seed spread."""
 import math
 
 import numpy as np
@@ -39,3 +40,15 @@ def test_volume_bookkeeping_single_deletion():
     assert s.logX == pytest.approx(-10.0 / 16, rel=1e-14)
     w = np.exp(np.array(s.dead_logw))
     assert w.sum() == pytest.approx(1.0 - math.exp(s.logX), rel=1e-12)
+
+
+def test_two_by_two_torus_evidence_and_error_bar():
+    # the interacting 2 x 2 torus (the kinetic term a 4-cycle with coupling 2): log Z from
+    # the transfer matrix, tr T^4; the error bar sqrt(H / N) matches the spread of 8 seeds
+    ref = cf.two_by_two_logz(-4.0, 8.0)
+    res = [ns.NS(ns.NSConfig(L=2, N=64, m2=-4.0, lam=8.0, n_delete=32, seed=100 + s)).run() for s in range(8)]
+    lz = np.array([r["logz"] for r in res])
+    err = np.mean([r["logz_err"] for r in res])
+    assert abs(lz.mean() - ref) < 4.0 * err / math.sqrt(len(lz)) + 0.02, (lz.mean(), ref, err)
+    assert 0.4 < lz.std(ddof=1) / err < 2.5
+    assert all(r["capped"] == 0 for r in res)
