@@ -13,9 +13,14 @@ It is a plain, slow, obviously correct restatement of the method, in float64:
                   the tempering log-weight and the magnetisation (Sec. 2);
 * ``tempering``   adaptive tempering: ESS, bisection for the next beta, reweighting
                   and the running log Z (Sec. 2 (i), App. A);
-* ``resample``    systematic resampling in fixed point (paper silent; see DESIGN);
+* ``resample``    systematic resampling in exact fixed point (the paper names no
+                  scheme; the reading is stated in the module);
 * ``covariance``  particle covariance and its Cholesky factor (App. A);
 * ``mutation``    covariance-preconditioned random-walk Metropolis (App. A);
+* ``irmh``        independent Metropolis-Hastings sweep from the population's Gaussian
+                  (Sec. 2 sampler (ii));
+* ``hmc``         Hamiltonian Monte Carlo transition, 20 leapfrog steps with a
+                  diagonal mass matrix (Sec. 2 sampler (iii), App. A);
 * ``smc``         the adaptive tempered SMC driver (Sec. 2 (i), App. A);
 * ``ns``          nested sampling with slice-sampling rejuvenation (Sec. 2 (iv), App. A);
 * ``observables`` magnetisation moments, susceptibility, mode balance (Sec. 2, App. F).
