@@ -1,5 +1,6 @@
-"""Pins for the HMC transition (SMC-HMC): the gradient against finite differences of the
-independently written action, leapfrog reversibility and its second-order energy error,
+"""Pins for the HMC transition (SMC-HMC): the gradients of the action and of the tempered
+log-target against finite differences of the independently written action and target,
+leapfrog reversibility and its second-order energy error,
 near-certain acceptance for small steps, invariance of the tempered free field under the
 transition, and the free-field evidence."""
 import math
@@ -22,6 +23,24 @@ def test_gradient_matches_finite_differences(L, c):
         e = np.zeros(L * L)
         e[x] = h
         fd = (lattice.action(phi + e, L, -4.0, 8.0, *c) - lattice.action(phi - e, L, -4.0, 8.0, *c)) / (2 * h)
+        np.testing.assert_allclose(grad[:, x], fd, rtol=1e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("keep_reference", [False, True])
+def test_target_gradient_matches_finite_differences(keep_reference):
+    # the force of the leapfrog map is the gradient of the tempered log-target as a whole,
+    # reference term included: -beta grad S - a phi with a = 1 - beta (1 with the reference kept)
+    L, beta = 3, 0.37
+    phi = np.random.default_rng(4).standard_normal((2, L * L))
+    grad = hmc.grad_log_target(phi, beta, L, -4.0, 8.0, 1.0, 1.0, keep_reference)
+
+    def log_gamma(q):
+        return lattice.log_target(lattice.action(q, L, -4.0, 8.0), lattice.sq_norm(q), beta, keep_reference)
+    h = 1e-6
+    for x in range(L * L):
+        e = np.zeros(L * L)
+        e[x] = h
+        fd = (log_gamma(phi + e) - log_gamma(phi - e)) / (2 * h)
         np.testing.assert_allclose(grad[:, x], fd, rtol=1e-6, atol=1e-6)
 
 
@@ -67,7 +86,8 @@ def test_invariance_free_field(keep_reference):
     # exact draws from gamma_beta of the free field stay distributed as gamma_beta under HMC
     # transitions with an inverse mass deliberately off the exact variances: a wrong kinetic
     # or potential term in the Hamiltonian of the accept test moves E|phi|^2 and Var M (or
-    # starves the acceptance), and a wrong gradient starves the acceptance
+    # starves the acceptance); a wrong force leaves the transition exact and only lowers the
+    # acceptance, which the gradient pins above cover
     L, m2, beta, N = 4, 1.0, 0.6, 20000
     D = L * L
     g = np.random.default_rng(21)
