@@ -73,9 +73,11 @@ typedef enum { PHI4_SMC_RW = 0, PHI4_NS_SLICE = 1, PHI4_SMC_IRMH = 2, PHI4_SMC_H
  *            covariance and Cholesky; float per-site action terms with compensated
  *            float partial sums; the per-particle sums, log-weights and log Z stay
  *            double (a few operations per particle).
- * MIXED_BF16: float fields; proposal and covariance GEMMs on the tcgen05 tensor
- *            cores with bf16 operands and fp32 accumulation; double Cholesky,
- *            acceptance test, log-weights and compensated log Z. */
+ * MIXED_BF16: float fields; proposal GEMM on the tcgen05 tensor cores with bf16
+ *            operands and fp32 accumulation; covariance as the exact Gram matrix of
+ *            fixed-point digits of the centred fields, also on the tensor cores (see
+ *            phi4_covariance); double Cholesky, acceptance test, log-weights and
+ *            compensated log Z. */
 typedef enum { PHI4_FP64 = 0, PHI4_FP32 = 1, PHI4_MIXED_BF16 = 2 } phi4_precision;
 
 /* Element types of the kernel-level entry points. */
@@ -317,8 +319,14 @@ size_t phi4_covariance_scratch_bytes(int32_t N, int32_t D, int32_t precision);
 /* Particle covariance (App. A): Sigma = Xc^T Xc / (N-1), Xc = phi - mean, lower
  * triangle (j <= i) of the row-major D x D double matrix `sigma` (device); the
  * strictly upper part is left untouched. precision FP64 / FP32: SIMT GEMM in that
- * type (phi dtype F64 / F32); MIXED_BF16: Xc rounded to bf16, tcgen05 GEMM with
- * fp32 accumulation (phi F32). */
+ * type (phi dtype F64 / F32). MIXED_BF16 (phi F32): site j's centred fields are
+ * rounded to integers v = rint(x 2^s_j) with s_j set by the site's largest deviation
+ * so that |v| <= 2^B, B = min(14, 23 - ceil(log2 N)); each v is split into two
+ * digits held exactly in bf16, and the digit planes' Gram matrices are formed on the
+ * tcgen05 tensor cores, whose fp32 sums of integer digit products stay within the
+ * integers fp32 holds exactly, then combined and scaled in double: sigma is the covariance of the
+ * rounded fields, positive semi-definite by construction. A device-side anomaly is
+ * returned as a status code; the call synchronises `stream`. */
 phi4_status phi4_covariance(const void* phi, int32_t precision, int32_t N, int32_t D, double* sigma,
                             void* scratch, size_t scratch_bytes, void* stream);
 
