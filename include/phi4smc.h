@@ -91,14 +91,14 @@ typedef enum {
 
 typedef struct {
   int32_t L;                 /* lattice side, D = L*L sites (1 <= L <= 128) */
-  int32_t N;                 /* particles (SMC) or live points (NS), 1 <= N <= 131072 */
+  int32_t N;                 /* particles (SMC) or live points (NS), 2 <= N <= 131072 (NS: N <= 8192) */
   int32_t kind;              /* phi4_kind */
   int32_t precision;         /* phi4_precision */
   double m2, lambda;         /* bare mass^2 and quartic coupling */
   double c_kin, c_mass;      /* action coefficients, 1.0 / 1.0 = unhalved form, 0.5 / 0.5 = Eq. (1) */
   int32_t keep_reference;    /* 0: tempering path N(0,I)^(1-beta) e^{-beta S}, target e^{-S} at beta=1;
                                 1: path N(0,I) e^{-beta S}, i.e. exp(-[U0 + beta S]) of Sec. 2 */
-  int32_t n_mcmc;            /* random-walk sweeps per temperature (SMC) */
+  int32_t n_mcmc;            /* inner-kernel sweeps (SMC_HMC: transitions) per temperature (SMC) */
   double ess_target;         /* rho in (0,1): next beta keeps ESS = rho N (SMC) */
   double rw_scale;           /* proposal scale on the Cholesky factor; <= 0 selects 2.38/sqrt(D) (App. A);
                                 SMC_HMC: the leapfrog step size, <= 0 selects 0.8 D^(-1/4) */
@@ -165,8 +165,10 @@ phi4_status smc_init(const phi4_config* cfg, void* d_workspace, size_t workspace
 
 /* One SMC temperature (Sec. 2 (i); App. A): ESS bisection for the next beta,
  * reweighting with Kahan-compensated log Z, systematic resampling and particle
- * gather, covariance and FP64 Cholesky refit, n_mcmc random-walk Metropolis
- * sweeps at the new beta. Synchronises the run's stream and writes the new beta
+ * gather, covariance and Cholesky refit (double; float in the FP32 form), n_mcmc
+ * sweeps of the run's inner kernel at the new beta (random-walk Metropolis,
+ * independent Metropolis-Hastings or HMC transitions, by phi4_config.kind), then
+ * the global flip move when PHI4_FLAG_Z2_FLIP is set. Synchronises the run's stream and writes the new beta
  * to *beta_out (may be NULL). PHI4_ERR_DONE once beta == 1; PHI4_ERR_ARG on an NS run. */
 phi4_status smc_temper_step(phi4_run* run, double* beta_out);
 
