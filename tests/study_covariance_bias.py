@@ -1,0 +1,88 @@
+"""Bias of the SMC evidence from the population-estimated proposal covariance (oracle study).
+
+Test infrastructure, like the rest of ``tests/``: it runs the FP64 oracle only. The
+random-walk kernel of a temperature uses the covariance of the population it is about
+to move (App. A). On the free field (lam = 0, m2 = 1), where log Z has a closed form,
+this prints log Zhat - log Z over a few seeds
+
+* against the number of sweeps per temperature and the target ESS (population
+  covariance),
+* against the number of particles at the workload's 10 sweeps and ESS 0.5 N,
+* with the exact covariance of the tempered free field in place of the population's
+  (the control: the driver is then exact and only the usual -Var/2 remains),
+* optionally (--L32) one run of the 32 x 32 precision-check workload
+  (N = 4096, 10 sweeps, ESS 0.5 N).
+
+    python tests/study_covariance_bias.py [--L32]
+"""
+import argparse
+import math
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+for p in (os.path.dirname(HERE), HERE):
+    if p not in sys.path:
+        sys.path.insert(0, p)
+
+import numpy as np  # noqa: E402
+
+import closed_forms as cf  # noqa: E402
+from oracle import covariance, tempering  # noqa: E402
+from oracle.smc import SMC, SMCConfig  # noqa: E402
+
+
+def logz_seeds(L, N, rho, n_mcmc, seeds, exact_covariance=False):
+    """log Zhat of the free field for seeds 0..seeds-1; with ``exact_covariance`` the
+    kernel covariance at each new temperature is the tempered free field's own."""
+    saved = (tempering.bisect_dbeta, covariance.sample_covariance)
+    if exact_covariance:
+        state = {}
+
+        def recording_bisect(ell, beta, rho_, iters=64):
+            d, used = saved[0](ell, beta, rho_, iters)
+            state["beta"] = min(1.0, beta + d)
+            return d, used
+        tempering.bisect_dbeta = recording_bisect
+        covariance.sample_covariance = lambda X: (X.mean(axis=0), cf.free_field_covariance(L, 1.0, state["beta"]))
+    try:
+        return np.array([SMC(SMCConfig(L=L, N=N, m2=1.0, lam=0.0, rho=rho, n_mcmc=n_mcmc, seed=s)).run()["logz"]
+                         for s in range(seeds)])
+    finally:
+        tempering.bisect_dbeta, covariance.sample_covariance = saved
+
+
+def report(label, L, lz, t0):
+    ref = cf.free_field_logz(L, 1.0)
+    sd = lz.std(ddof=1) if len(lz) > 1 else float("nan")
+    print("%-46s log Zhat - log Z = %+8.3f  (sd %.3f, %d seeds, %.0f s)"
+          % (label, lz.mean() - ref, sd, len(lz), time.time() - t0), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--L32", action="store_true", help="also run the 32 x 32, N = 4096 workload once (minutes)")
+    ap.add_argument("--seeds", type=int, default=4)
+    a = ap.parse_args()
+    L = 8
+    for n_mcmc in (10, 50, 200):
+        for rho in (0.5, 0.9):
+            t0 = time.time()
+            report("L=8 N=1024 sweeps=%d ESS=%.1fN" % (n_mcmc, rho), L, logz_seeds(L, 1024, rho, n_mcmc, a.seeds), t0)
+    for N in (256, 4096):
+        t0 = time.time()
+        report("L=8 N=%d sweeps=10 ESS=0.5N" % N, L, logz_seeds(L, N, 0.5, 10, a.seeds), t0)
+    t0 = time.time()
+    lz = logz_seeds(L, 1024, 0.5, 10, a.seeds, exact_covariance=True)
+    report("L=8 N=1024 sweeps=10 ESS=0.5N exact covariance", L, lz, t0)
+    print("%-46s mean + var/2 - log Z = %+.3f" % ("", lz.mean() + 0.5 * lz.var(ddof=1) - cf.free_field_logz(L, 1.0)))
+    if a.L32:
+        t0 = time.time()
+        report("L=32 N=4096 sweeps=10 ESS=0.5N", 32, logz_seeds(32, 4096, 0.5, 10, 1), t0)
+    print("closed forms: L=8 %.10f  L=32 %.10f" % (cf.free_field_logz(8, 1.0), cf.free_field_logz(32, 1.0)))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
