@@ -77,3 +77,43 @@ def test_inner_kernel_configuration_rules_and_workspace(built):
         with pytest.raises(p.Phi4Error):
             p.workspace_bytes(bad)
         assert word in p.lib().phi4_last_error()
+
+
+def _imports_of(tree):
+    """Absolute module names imported anywhere under an AST node."""
+    import ast
+    out = []
+    for n in ast.walk(tree):
+        if isinstance(n, ast.Import):
+            out += [a.name for a in n.names]
+        elif isinstance(n, ast.ImportFrom) and n.level == 0:
+            out.append(n.module or "")
+    return [m.split(".")[0] for m in out]
+
+
+def test_product_and_oracle_are_separate():
+    # the product (the package and its CUDA sources) never imports or names the oracle;
+    # the oracle imports nothing of the product; bench.py reaches the oracle only inside
+    # its CPU-baseline function (the reference arm and the cpu_baseline leg)
+    import ast
+
+    def parsed(path):
+        return ast.parse(open(path).read())
+    pkg = os.path.join(ROOT, "paper_2511_15196_gb300")
+    for name in sorted(os.listdir(pkg)):
+        if name.endswith(".py"):
+            assert "oracle" not in _imports_of(parsed(os.path.join(pkg, name))), name
+    csrc = os.path.join(pkg, "csrc")
+    for name in sorted(os.listdir(csrc)):
+        assert "oracle" not in open(os.path.join(csrc, name)).read().lower(), name
+    odir = os.path.join(ROOT, "oracle")
+    for name in sorted(os.listdir(odir)):
+        if name.endswith(".py"):
+            mods = _imports_of(parsed(os.path.join(odir, name)))
+            assert not {"paper_2511_15196_gb300", "torch", "ctypes"} & set(mods), name
+    bench = parsed(os.path.join(ROOT, "bench.py"))
+    for node in bench.body:
+        if isinstance(node, ast.FunctionDef) and "oracle" in _imports_of(node):
+            assert node.name == "cpu_baseline", node.name
+        elif not isinstance(node, ast.FunctionDef):
+            assert "oracle" not in _imports_of(node)
