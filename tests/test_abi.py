@@ -117,3 +117,34 @@ def test_product_and_oracle_are_separate():
             assert node.name == "cpu_baseline", node.name
         elif not isinstance(node, ast.FunctionDef):
             assert "oracle" not in _imports_of(node)
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    # the ctypes mirrors of phi4_config and phi4_obs have the C compiler's size and field
+    # offsets (a field added, dropped or reordered on one side only would shift the rest)
+    import shutil
+    import subprocess
+    import paper_2511_15196_gb300 as p
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"phi4_config": p.CConfig, "phi4_obs": p.CObs}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "phi4smc.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in cls._fields_:
+            cf = "lambda" if f == "lambda_" else f
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, cf))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        s, f, v = line.split()
+        got[(s, f)] = int(v)
+    for cname, cls in structs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
