@@ -179,11 +179,14 @@ phi4_status smc_temper_step(phi4_run* run, double* beta_out);
  * rule holds. PHI4_ERR_DONE if already stopped; PHI4_ERR_ARG on an SMC run. */
 phi4_status ns_replace_step(phi4_run* run, int32_t* done_out);
 
-/* Running log-evidence and its error bar (NS: sqrt(H/N) including the live
- * points; SMC: NaN). Synchronises the run's stream. */
+/* Running log-evidence (Sec. 2: SMC accumulates the log mean incremental weight of
+ * each temperature; NS sums dead and live points' prior-volume weights, App. A) and its
+ * error bar (NS: sqrt(H/N) including the live points; SMC: NaN). Synchronises the
+ * run's stream. */
 phi4_status smc_log_evidence(const phi4_run* run, double* logz, double* logz_err);
 
-/* Population observables (uniform weights over the current population).
+/* Population observables (uniform weights over the current population): moments of
+ * the magnetisation M (Sec. 2), susceptibility, mode balance (App. F).
  * Synchronises the run's stream. */
 phi4_status smc_observables(const phi4_run* run, phi4_obs* out);
 
@@ -310,7 +313,8 @@ phi4_status phi4_resample_systematic(const double* w, int32_t N, uint32_t U, int
 #define PHI4_RESAMPLE_STATIC_MAX_N 65536
 phi4_status phi4_resample_systematic_static(const double* w, int32_t N, uint32_t U, int32_t* anc, void* stream);
 
-/* dst row i = src row anc[i] for i < N, rows of `row_bytes` (device buffers;
+/* Particle gather after resampling (Sec. 2 (i)):
+ * dst row i = src row anc[i] for i < N, rows of `row_bytes` (device buffers;
  * dst and src must not overlap). */
 phi4_status phi4_gather_rows(const void* src, void* dst, size_t row_bytes, int32_t N, const int32_t* anc,
                              void* stream);
@@ -332,7 +336,8 @@ size_t phi4_covariance_scratch_bytes(int32_t N, int32_t D, int32_t precision);
 phi4_status phi4_covariance(const void* phi, int32_t precision, int32_t N, int32_t D, double* sigma,
                             void* scratch, size_t scratch_bytes, void* stream);
 
-/* In-place Cholesky A = L L^T (+ ridge): on entry the lower triangle of the
+/* Cholesky factor of the particle covariance, which scales the random-walk proposal
+ * (App. A). In-place A = L L^T (+ ridge): on entry the lower triangle of the
  * row-major D x D double matrix `a` (device) holds Sigma; `*d_ridge` (device
  * double) is added to its diagonal; on exit the lower triangle holds L and the
  * strictly upper triangle is zeroed. A non-positive pivot sets bit 2 of
