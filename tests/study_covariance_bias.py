@@ -11,9 +11,11 @@ this prints log Zhat - log Z over a few seeds
 * with the exact covariance of the tempered free field in place of the population's
   (the control: the driver is then exact and only the usual -Var/2 remains),
 * optionally (--L32) one run of the 32 x 32 precision-check workload
-  (N = 4096, 10 sweeps, ESS 0.5 N).
+  (N = 4096, 10 sweeps, ESS 0.5 N),
+* optionally (--broken) the interacting 8 x 8 workload (m2 = -4, lam = 8, N = 1024),
+  which has no closed form, as the sweeps per temperature grow.
 
-    python tests/study_covariance_bias.py [--L32]
+    python tests/study_covariance_bias.py [--L32] [--broken]
 """
 import argparse
 import math
@@ -31,6 +33,18 @@ import numpy as np  # noqa: E402
 import closed_forms as cf  # noqa: E402
 from oracle import covariance, tempering  # noqa: E402
 from oracle.smc import SMC, SMCConfig  # noqa: E402
+
+
+def broken_phase(seeds):
+    # (sweeps, ESS target, seeds) in increasing cost
+    for n_mcmc, rho, ns in ((10, 0.5, seeds), (50, 0.9, seeds), (200, 0.9, 2), (800, 0.9, 1)):
+        t0 = time.time()
+        lz = np.array([SMC(SMCConfig(L=8, N=1024, m2=-4.0, lam=8.0, rho=rho, n_mcmc=n_mcmc, seed=s)).run()["logz"]
+                       for s in range(ns)])
+        sd = lz.std(ddof=1) if ns > 1 else float("nan")
+        print("%-46s log Zhat = %8.3f  (sd %.3f, %d seeds, %.0f s)"
+              % ("L=8 m2=-4 lam=8 N=1024 sweeps=%d ESS=%.1fN" % (n_mcmc, rho), lz.mean(), sd, ns, time.time() - t0),
+              flush=True)
 
 
 def logz_seeds(L, N, rho, n_mcmc, seeds, exact_covariance=False):
@@ -63,6 +77,7 @@ def report(label, L, lz, t0):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--L32", action="store_true", help="also run the 32 x 32, N = 4096 workload once (minutes)")
+    ap.add_argument("--broken", action="store_true", help="also the interacting 8 x 8 workload (minutes)")
     ap.add_argument("--seeds", type=int, default=4)
     a = ap.parse_args()
     L = 8
@@ -77,6 +92,8 @@ def main():
     lz = logz_seeds(L, 1024, 0.5, 10, a.seeds, exact_covariance=True)
     report("L=8 N=1024 sweeps=10 ESS=0.5N exact covariance", L, lz, t0)
     print("%-46s mean + var/2 - log Z = %+.3f" % ("", lz.mean() + 0.5 * lz.var(ddof=1) - cf.free_field_logz(L, 1.0)))
+    if a.broken:
+        broken_phase(a.seeds)
     if a.L32:
         t0 = time.time()
         report("L=32 N=4096 sweeps=10 ESS=0.5N", 32, logz_seeds(32, 4096, 0.5, 10, 1), t0)
