@@ -10,6 +10,9 @@ this prints log Zhat - log Z over a few seeds
 * against the number of particles at the workload's 10 sweeps and ESS 0.5 N,
 * with the exact covariance of the tempered free field in place of the population's
   (the control: the driver is then exact and only the usual -Var/2 remains),
+* with two other estimates of the covariance: each half of the resampled population
+  moved with the other half's covariance, and the importance-weighted covariance of the
+  population before resampling,
 * optionally (--L32) one run of the 32 x 32 precision-check workload
   (N = 4096, 10 sweeps, ESS 0.5 N),
 * optionally (--broken) the interacting 8 x 8 workload (m2 = -4, lam = 8, N = 1024),
@@ -31,7 +34,7 @@ for p in (os.path.dirname(HERE), HERE):
 import numpy as np  # noqa: E402
 
 import closed_forms as cf  # noqa: E402
-from oracle import covariance, tempering  # noqa: E402
+from oracle import covariance, lattice, mutation, philox, resample, tempering  # noqa: E402
 from oracle.smc import SMC, SMCConfig  # noqa: E402
 
 
@@ -45,6 +48,44 @@ def broken_phase(seeds):
         print("%-46s log Zhat = %8.3f  (sd %.3f, %d seeds, %.0f s)"
               % ("L=8 m2=-4 lam=8 N=1024 sweeps=%d ESS=%.1fN" % (n_mcmc, rho), lz.mean(), sd, ns, time.time() - t0),
               flush=True)
+
+
+def variant_logz(L, N, seed, mode, rho=0.5, n_mcmc=10):
+    """The SMC driver's temperature step written out with another covariance estimate:
+    mode "split" moves each half of the resampled population with the covariance of the
+    other half; mode "weighted" uses the importance-weighted covariance of the population
+    before resampling."""
+    c = SMCConfig(L=L, N=N, m2=1.0, lam=0.0, rho=rho, n_mcmc=n_mcmc, seed=seed)
+    s = SMC(c)
+    while not s.done:
+        s.t += 1
+        t = s.t
+        dbeta = s.choose_dbeta()
+        beta_new = 1.0 if dbeta >= 1.0 - s.beta else s.beta + dbeta
+        w, inc = tempering.reweight(s.ell, dbeta)
+        s.logz.add(inc)
+        if mode == "weighted":
+            wn = w / w.sum()
+            Xc = s.phi - wn @ s.phi
+            Sig = (Xc * wn[:, None]).T @ Xc / (1.0 - (wn * wn).sum())
+        anc = resample.systematic(w, philox.word32(c.seed, c.stream, philox.KIND_RESAMPLE, t))
+        s.phi, s.S, s.sq = s.phi[anc], s.S[anc], s.sq[anc]
+        if mode == "weighted":
+            groups = [(np.arange(N), Sig, 0)]
+        else:
+            perm = np.random.default_rng([seed, t]).permutation(N)
+            A, B = perm[: N // 2], perm[N // 2:]
+            groups = [(A, covariance.sample_covariance(s.phi[B])[1], 0), (B, covariance.sample_covariance(s.phi[A])[1], 1)]
+        for own, Sig_g, stream in groups:
+            Lc = covariance.regularised_cholesky(Sig_g, c.jitter_rel)[0]
+            ph, S, sq = s.phi[own], s.S[own], s.sq[own]
+            for k in range(n_mcmc):
+                ph, S, sq, _ = mutation.rw_sweep(ph, S, sq, Lc, c.scale, beta_new, L, 1.0, 0.0, 1.0, 1.0, False,
+                                                 seed, stream, t, k)
+            s.phi[own], s.S[own], s.sq[own] = ph, S, sq
+        s.ell = lattice.tempering_loglik(s.S, s.sq, c.D)
+        s.beta = beta_new
+    return s.logz.s
 
 
 def logz_seeds(L, N, rho, n_mcmc, seeds, exact_covariance=False):
@@ -92,6 +133,10 @@ def main():
     lz = logz_seeds(L, 1024, 0.5, 10, a.seeds, exact_covariance=True)
     report("L=8 N=1024 sweeps=10 ESS=0.5N exact covariance", L, lz, t0)
     print("%-46s mean + var/2 - log Z = %+.3f" % ("", lz.mean() + 0.5 * lz.var(ddof=1) - cf.free_field_logz(L, 1.0)))
+    for mode in ("split", "weighted"):
+        t0 = time.time()
+        report("L=8 N=1024 sweeps=10 ESS=0.5N %s" % mode, L,
+               np.array([variant_logz(L, 1024, s, mode) for s in range(a.seeds)]), t0)
     if a.broken:
         broken_phase(a.seeds)
     if a.L32:
