@@ -21,7 +21,6 @@ this prints log Zhat - log Z over a few seeds
     python tests/study_covariance_bias.py [--L32] [--broken]
 """
 import argparse
-import math
 import os
 import sys
 import time
