@@ -10,6 +10,7 @@ this prints log Zhat - log Z over a few seeds
 * against the number of particles at the workload's 10 sweeps and ESS 0.5 N,
 * with the exact covariance of the tempered free field in place of the population's
   (the control: the driver is then exact and only the usual -Var/2 remains),
+* the final population's mean |phi|^2 against its exact value (the contraction),
 * with two other estimates of the covariance: each half of the resampled population
   moved with the other half's covariance, and the importance-weighted covariance of the
   population before resampling,
@@ -132,6 +133,12 @@ def main():
     lz = logz_seeds(L, 1024, 0.5, 10, a.seeds, exact_covariance=True)
     report("L=8 N=1024 sweeps=10 ESS=0.5N exact covariance", L, lz, t0)
     print("%-46s mean + var/2 - log Z = %+.3f" % ("", lz.mean() + 0.5 * lz.var(ddof=1) - cf.free_field_logz(L, 1.0)))
+    for n_mcmc in (10, 200):
+        r = SMC(SMCConfig(L=L, N=1024, m2=1.0, lam=0.0, rho=0.5, n_mcmc=n_mcmc, seed=0))
+        r.run()
+        print("%-46s mean |phi|^2 of the final population %.3f (exact %.3f)"
+              % ("L=8 N=1024 sweeps=%d ESS=0.5N seed 0" % n_mcmc, float((r.phi ** 2).sum(axis=1).mean()),
+                 cf.free_field_sq_mean(L, 1.0)), flush=True)
     for mode in ("split", "weighted"):
         t0 = time.time()
         report("L=8 N=1024 sweeps=10 ESS=0.5N %s" % mode, L,
