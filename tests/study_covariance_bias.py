@@ -15,11 +15,12 @@ this prints log Zhat - log Z over a few seeds
   moved with the other half's covariance, and the importance-weighted covariance of the
   population before resampling,
 * optionally (--L32) one run of the 32 x 32 precision-check workload
-  (N = 4096, 10 sweeps, ESS 0.5 N),
+  (N = 4096, ESS 0.5 N, 10 sweeps or --L32-sweeps) with each covariance (about 10
+  minutes at 10 sweeps, two hours at 100),
 * optionally (--broken) the interacting 8 x 8 workload (m2 = -4, lam = 8, N = 1024),
   which has no closed form, as the sweeps per temperature grow.
 
-    python tests/study_covariance_bias.py [--L32] [--broken]
+    python tests/study_covariance_bias.py [--L32 [--L32-sweeps 100]] [--broken]
 """
 import argparse
 import os
@@ -119,6 +120,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--L32", action="store_true", help="also run the 32 x 32, N = 4096 workload once (minutes)")
     ap.add_argument("--broken", action="store_true", help="also the interacting 8 x 8 workload (minutes)")
+    ap.add_argument("--L32-sweeps", type=int, default=10, help="sweeps per temperature of the --L32 runs")
     ap.add_argument("--seeds", type=int, default=4)
     a = ap.parse_args()
     L = 8
@@ -146,8 +148,12 @@ def main():
     if a.broken:
         broken_phase(a.seeds)
     if a.L32:
+        m = a.L32_sweeps
         t0 = time.time()
-        report("L=32 N=4096 sweeps=10 ESS=0.5N", 32, logz_seeds(32, 4096, 0.5, 10, 1), t0)
+        report("L=32 N=4096 sweeps=%d ESS=0.5N" % m, 32, logz_seeds(32, 4096, 0.5, m, 1), t0)
+        t0 = time.time()
+        report("L=32 N=4096 sweeps=%d ESS=0.5N exact covariance" % m, 32,
+               logz_seeds(32, 4096, 0.5, m, 1, exact_covariance=True), t0)
     print("closed forms: L=8 %.10f  L=32 %.10f" % (cf.free_field_logz(8, 1.0), cf.free_field_logz(32, 1.0)))
     return 0
 
