@@ -18,3 +18,21 @@ def test_kappa_config_reproduces_the_kappa_form_and_its_log_z_shift():
     s_cfg = lattice.action(phi, L, cfg.m2, cfg.lam, cfg.c_kin, cfg.c_mass)
     # Z_kappa = exp(-lam V) Z_cfg, so S_kappa = S_cfg - kappa_logz_shift
     np.testing.assert_allclose(s_cfg - p.kappa_logz_shift(lam, L * L), s_kappa, rtol=1e-13)
+
+
+def test_batched_workload_assignment():
+    # 64 runs: L round-robin over {8, 12, 16, 24, 32}, N = {1024, 2048, 4096}[seed mod 3],
+    # lambda = {4, 8, 16}[(r div 3) mod 3] so that every lambda meets every N, m2 = -4,
+    # float fields with bf16 tensor-core GEMMs, seed = run index
+    import itertools
+
+    import bench
+    cfgs = bench.batch_configs(p, 64, 10)
+    assert len(cfgs) == 64
+    assert [c.L for c in cfgs[:6]] == [8, 12, 16, 24, 32, 8]
+    assert all(c.seed == r and c.N == [1024, 2048, 4096][r % 3] for r, c in enumerate(cfgs))
+    assert {(c.lam, c.N) for c in cfgs} == set(itertools.product([4.0, 8.0, 16.0], [1024, 2048, 4096]))
+    assert {c.L for c in cfgs} == {8, 12, 16, 24, 32}
+    assert all(c.m2 == -4.0 and c.precision == p.MIXED_BF16 and c.n_mcmc == 10 for c in cfgs)
+    total = sum(p.workspace_bytes(c) for c in cfgs)
+    assert total < 64 * 2 ** 30
