@@ -94,6 +94,17 @@ def one_site_logz(m2, lam, c_mass=1.0):
     return math.log(val)
 
 
+def one_site_information(m2, lam, c_mass=1.0):
+    """Information H = E_post[log L] - log Z of the one-site problem as nested sampling
+    sets it up: prior N(0, 1), likelihood L(c) = exp(-S(c)) / N(c; 0, 1), posterior
+    exp(-S) / Z (adaptive quadrature)."""
+    logz = one_site_logz(m2, lam, c_mass)
+    S = lambda c: c_mass * m2 * c * c + lam * c ** 4  # noqa: E731
+    f = lambda c: math.exp(-S(c) - logz) * (-S(c) + 0.5 * c * c + 0.5 * math.log(2.0 * math.pi))  # noqa: E731
+    val, _ = integrate.quad(f, -np.inf, np.inf, epsabs=0, epsrel=1e-12, limit=200)
+    return val - logz
+
+
 def two_by_two_logz(m2, lam, c_kin=1.0, c_mass=1.0, half_width=8.0, n=4001):
     """log Z of the 2 x 2 torus by the transfer matrix on a uniform grid
     (trapezoid rule; the integrand decays like a Gaussian or faster)."""

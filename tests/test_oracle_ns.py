@@ -1,6 +1,8 @@
 """Pins for the nested-sampling oracle: the exact prior bracket, evidence on
-one site against quadrature and on the 2 x 2 torus against its transfer matrix, and the
-error bar sqrt(H / N) against the seed-to-seed spread."""
+one site against quadrature and on the 2 x 2 torus against its transfer matrix, the
+error bar sqrt(H / N) against the seed-to-seed spread, the information H against
+quadrature, the evidence with the live points at any stopping point, and the stopping
+rule."""
 import math
 
 import numpy as np
@@ -52,3 +54,37 @@ def test_two_by_two_torus_evidence_and_error_bar():
     assert abs(lz.mean() - ref) < 4.0 * err / math.sqrt(len(lz)) + 0.02, (lz.mean(), ref, err)
     assert 0.4 < lz.std(ddof=1) / err < 2.5
     assert all(r["capped"] == 0 for r in res)
+
+
+def test_evidence_with_the_live_points_at_any_stopping_point():
+    # dead points' weights plus X times the mean live likelihood estimate Z after any
+    # number of iterations; after 3 deletions of half the points the live points still
+    # carry most of the mass, so their weight X / N is what this checks
+    ref = cf.one_site_logz(-4.0, 8.0)
+    lz = []
+    for s in range(6):
+        run = ns.NS(ns.NSConfig(L=1, N=64, m2=-4.0, lam=8.0, n_delete=32, seed=20 + s))
+        for _ in range(3):
+            run.replace_step()
+        lz.append(run.final()[0])
+    lz = np.array(lz)
+    assert abs(lz.mean() - ref) < 4.0 * lz.std(ddof=1) / math.sqrt(len(lz)) + 0.02, (lz.mean(), ref)
+
+
+def test_information_and_stopping_rule():
+    # H = E_post[log L] - log Z against quadrature; the run stops at the first iteration
+    # whose remaining evidence X mean(L_live) is below stop_frac of the accumulated Z
+    H_ref = cf.one_site_information(-4.0, 8.0)
+    Hs = []
+    for s in range(4):
+        run = ns.NS(ns.NSConfig(L=1, N=64, m2=-4.0, lam=8.0, n_delete=32, seed=s))
+        prev = []
+        while not run.done:
+            prev.append(run.remaining_log_evidence() - run.logZ)
+            run.replace_step()
+        assert run.remaining_log_evidence() - run.logZ < math.log(1e-3)
+        assert all(g >= math.log(1e-3) for g in prev[1:]), prev
+        assert run.it >= 2
+        Hs.append(run.result()["H"])
+    Hs = np.array(Hs)
+    assert abs(Hs.mean() - H_ref) < 4.0 * Hs.std(ddof=1) / math.sqrt(len(Hs)) + 0.02, (Hs.mean(), H_ref)

@@ -211,6 +211,49 @@ CASES = [
      [P(t_ns.test_one_site_evidence_and_error_bar)],
      # the live points collapse onto a few and the run stops at a singular covariance
      (AssertionError, np.linalg.LinAlgError)),
+    ("deletion threshold at the lowest deleted point", "oracle.ns",
+     [("lstar = float(self.logl[dead[-1]])", "lstar = float(self.logl[dead[0]])")],
+     [P(t_ns.test_one_site_evidence_and_error_bar)]),
+    ("replacement started from any point, deleted ones included", "oracle.ns",
+     [("start = int(survivors[int(math.floor(u * (N - k)))])", "start = int(order[int(math.floor(u * N))])")],
+     [P(t_ns.test_one_site_evidence_and_error_bar)]),
+    ("live points weighted X instead of X / N", "oracle.ns",
+     [("logw_live = self.logX - math.log(c.N)", "logw_live = self.logX")],
+     [P(t_ns.test_evidence_with_the_live_points_at_any_stopping_point)]),
+    ("stopping rule reversed", "oracle.ns",
+     [("- self.logZ < math.log(c.stop_frac)", "- self.logZ > math.log(c.stop_frac)")],
+     [P(t_ns.test_information_and_stopping_rule)]),
+    ("information without the -log Z", "oracle.ns",
+     [("H = float((p * all_l).sum()) - logZ", "H = float((p * all_l).sum())")],
+     [P(t_ns.test_information_and_stopping_rule)]),
+    # ---- more of the same modules ----
+    ("Box-Muller with the cosine twice", "oracle.philox",
+     [("    ang = 2.0 * np.pi * u2\n    return r * np.cos(ang), r * np.sin(ang)\n\n\ndef box_muller_24",
+       "    ang = 2.0 * np.pi * u2\n    return r * np.cos(ang), r * np.cos(ang)\n\n\ndef box_muller_24")],
+     [P(t_philox.test_box_muller_special_points), P(t_philox.test_normals_moments)]),
+    ("Box-Muller radius uniform without the +1 (u1 may be 0)", "oracle.philox",
+     [("u1 = (wa.astype(np.float64) + 1.0) * 2.0 ** -32", "u1 = wa.astype(np.float64) * 2.0 ** -32")],
+     [P(t_philox.test_box_muller_special_points)]),
+    ("independence proposal without the population mean", "oracle.irmh",
+     [("prop = np.asarray(mu, np.float64)[None, :] + Z @ np.asarray(Lchol, np.float64).T",
+       "prop = Z @ np.asarray(Lchol, np.float64).T")],
+     [P(t_irmh.test_log_alpha_is_the_metropolis_hastings_ratio, keep_reference=False)]),
+    ("leapfrog drift without the inverse mass", "oracle.hmc",
+     [("phi = phi + eps * v * p", "phi = phi + eps * p")],
+     [P(t_hmc.test_leapfrog_is_reversible_and_second_order), P(t_hmc.test_invariance_free_field, keep_reference=False)]),
+    ("ridge without the 1/D of the mean diagonal", "oracle.covariance",
+     [("delta = jitter_rel * np.trace(Sigma) / D", "delta = jitter_rel * np.trace(Sigma)")],
+     [P(t_cov.test_regularised_cholesky_rank_deficient)]),
+    ("<|M|> without the absolute value", "oracle.observables",
+     [("mean_absM = float((w * np.abs(M)).sum())", "mean_absM = float((w * M).sum())")],
+     [P(t_obs.test_weighted_moments_by_hand), P(t_obs.test_free_field_moments_from_exact_draws)]),
+    ("magnetisation as the sum over sites", "oracle.lattice",
+     [("return phi.mean(axis=-1)", "return phi.sum(axis=-1)")],
+     [P(t_obs.test_weighted_moments_by_hand), P(t_obs.test_free_field_moments_from_exact_draws)]),
+    ("paper-mode weight keeps the reference term", "oracle.lattice",
+     [("        return -np.asarray(S, dtype=np.float64)\n",
+       "        return -np.asarray(S, dtype=np.float64) + 0.5 * np.asarray(sq, dtype=np.float64)\n")],
+     [P(t_action.test_loglik_and_target), P(t_smc.test_paper_mode_free_field)]),
 ]
 
 
