@@ -11,9 +11,10 @@ this prints log Zhat - log Z over a few seeds
 * with the exact covariance of the tempered free field in place of the population's
   (the control: the driver is then exact and only the usual -Var/2 remains),
 * the final population's mean |phi|^2 against its exact value (the contraction),
-* with two other estimates of the covariance: each half of the resampled population
-  moved with the other half's covariance, and the importance-weighted covariance of the
-  population before resampling,
+* with three other estimates of the covariance: each half of the resampled population
+  moved with the other half's covariance, the importance-weighted covariance of the
+  population before resampling, and the covariance of an independent replica population
+  on the same temperature schedule,
 * optionally (--L32) one run of the 32 x 32 precision-check workload
   (N = 4096, ESS 0.5 N, 10 sweeps or --L32-sweeps) with each covariance (about 10
   minutes at 10 sweeps, two hours at 100),
@@ -89,6 +90,34 @@ def variant_logz(L, N, seed, mode, rho=0.5, n_mcmc=10):
     return s.logz.s
 
 
+def replica_logz(L, N, seed, rho=0.5, n_mcmc=10):
+    """Two independent populations on one temperature schedule (the first's adaptive
+    one): each is moved with the covariance of the other, so no kernel depends on the
+    particles it moves or on their copies. Returns the first population's log Zhat."""
+    cA = SMCConfig(L=L, N=N, m2=1.0, lam=0.0, rho=rho, n_mcmc=n_mcmc, seed=seed)
+    cB = SMCConfig(L=L, N=N, m2=1.0, lam=0.0, rho=rho, n_mcmc=n_mcmc, seed=seed + 7919)
+    A, B = SMC(cA), SMC(cB)
+    while not A.done:
+        A.t += 1
+        B.t += 1
+        dbeta = A.choose_dbeta()
+        beta_new = 1.0 if dbeta >= 1.0 - A.beta else A.beta + dbeta
+        for r, c in ((A, cA), (B, cB)):
+            w, inc = tempering.reweight(r.ell, dbeta)
+            r.logz.add(inc)
+            anc = resample.systematic(w, philox.word32(c.seed, c.stream, philox.KIND_RESAMPLE, r.t))
+            r.phi, r.S, r.sq = r.phi[anc], r.S[anc], r.sq[anc]
+        LA = covariance.regularised_cholesky(covariance.sample_covariance(B.phi)[1], cA.jitter_rel)[0]
+        LB = covariance.regularised_cholesky(covariance.sample_covariance(A.phi)[1], cB.jitter_rel)[0]
+        for r, c, Lc in ((A, cA, LA), (B, cB, LB)):
+            for k in range(n_mcmc):
+                r.phi, r.S, r.sq, _ = mutation.rw_sweep(r.phi, r.S, r.sq, Lc, c.scale, beta_new, L, 1.0, 0.0, 1.0,
+                                                        1.0, False, c.seed, c.stream, r.t, k)
+            r.ell = lattice.tempering_loglik(r.S, r.sq, c.D)
+            r.beta = beta_new
+    return A.logz.s
+
+
 def logz_seeds(L, N, rho, n_mcmc, seeds, exact_covariance=False):
     """log Zhat of the free field for seeds 0..seeds-1; with ``exact_covariance`` the
     kernel covariance at each new temperature is the tempered free field's own."""
@@ -131,10 +160,14 @@ def main():
     for N in (256, 4096):
         t0 = time.time()
         report("L=8 N=%d sweeps=10 ESS=0.5N" % N, L, logz_seeds(L, N, 0.5, 10, a.seeds), t0)
+    # the controls have a large spread: 12 seeds
+    n_ctl = max(a.seeds, 12)
     t0 = time.time()
-    lz = logz_seeds(L, 1024, 0.5, 10, a.seeds, exact_covariance=True)
+    lz = logz_seeds(L, 1024, 0.5, 10, n_ctl, exact_covariance=True)
     report("L=8 N=1024 sweeps=10 ESS=0.5N exact covariance", L, lz, t0)
     print("%-46s mean + var/2 - log Z = %+.3f" % ("", lz.mean() + 0.5 * lz.var(ddof=1) - cf.free_field_logz(L, 1.0)))
+    t0 = time.time()
+    report("L=8 N=1024 sweeps=10 ESS=0.5N replica", L, np.array([replica_logz(L, 1024, s) for s in range(n_ctl)]), t0)
     for n_mcmc in (10, 200):
         r = SMC(SMCConfig(L=L, N=1024, m2=1.0, lam=0.0, rho=0.5, n_mcmc=n_mcmc, seed=0))
         r.run()
