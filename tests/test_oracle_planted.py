@@ -254,6 +254,25 @@ CASES = [
      [("        return -np.asarray(S, dtype=np.float64)\n",
        "        return -np.asarray(S, dtype=np.float64) + 0.5 * np.asarray(sq, dtype=np.float64)\n")],
      [P(t_action.test_loglik_and_target), P(t_smc.test_paper_mode_free_field)]),
+    ("bisection halves the wrong side", "oracle.tempering",
+     [("            lo = mid\n        else:\n            hi = mid", "            hi = mid\n        else:\n            lo = mid")],
+     [P(t_temp.test_bisection_matches_independent_root_finder), P(t_temp.test_bisection_brute_force_grid_tiny)]),
+    ("ESS target rho (N - 1)", "oracle.tempering",
+     [("target = rho * n\n", "target = rho * (n - 1)\n")],
+     [P(t_temp.test_bisection_matches_independent_root_finder)]),
+    ("sweeps at the previous temperature", "oracle.smc",
+     [("self.phi, self.S, self.sq, Lc, c.scale, beta_new,", "self.phi, self.S, self.sq, Lc, c.scale, self.beta,")],
+     [P(t_smc.test_every_stage_of_free_field_path),
+      P(t_smc.test_evidence_matches_exact, kind="free", L=2, m2=1.0, lam=0.0)]),
+    ("paper-mode accept ignores the kept reference", "oracle.mutation",
+     [("        return -beta * dS - 0.5 * dsq\n", "        return -beta * dS - (1.0 - beta) * 0.5 * dsq\n")],
+     [P(t_mut.test_invariance_free_field, keep_reference=True)]),
+    ("HMC accept with the kinetic difference's sign flipped", "oracle.hmc",
+     [("- (kin1 - kin0)", "+ (kin1 - kin0)")],
+     [P(t_hmc.test_small_steps_are_accepted), P(t_hmc.test_invariance_free_field, keep_reference=False)]),
+    ("whitened norm with the upper triangle", "oracle.irmh",
+     [("X, lower=True)", "X, lower=False)")],
+     [P(t_irmh.test_whitened_norm_is_the_mahalanobis_distance)]),
 ]
 
 
