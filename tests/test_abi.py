@@ -148,3 +148,16 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
         for f, _ in cls._fields_:
             assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+
+
+def test_static_resampling_array_holds_the_scratch_of_its_largest_call(built):
+    # the allocation-free resampler's built-in array (PHI4_RESAMPLE_STATIC_MAX_N 64-bit
+    # words) is exactly the scratch the allocating entry point asks for at that N
+    import paper_2511_15196_gb300 as p
+    text = open(HEADER).read()
+    max_n = int(re.search(r"#define PHI4_RESAMPLE_STATIC_MAX_N (\d+)", text).group(1))
+    lib = p.lib()
+    assert lib.phi4_resample_scratch_bytes(max_n) == 8 * max_n == 512 * 1024
+    for n in (1, 2, 1000, 8192, 131072):
+        assert lib.phi4_resample_scratch_bytes(n) == 8 * n
+    assert lib.phi4_bisect_scratch_bytes(8192) > 0
