@@ -160,8 +160,8 @@ def main():
     for N in (256, 4096):
         t0 = time.time()
         report("L=8 N=%d sweeps=10 ESS=0.5N" % N, L, logz_seeds(L, N, 0.5, 10, a.seeds), t0)
-    # the controls have a large spread: 12 seeds
-    n_ctl = max(a.seeds, 12)
+    # the controls have a large spread: 32 seeds
+    n_ctl = max(a.seeds, 32)
     t0 = time.time()
     lz = logz_seeds(L, 1024, 0.5, 10, n_ctl, exact_covariance=True)
     report("L=8 N=1024 sweeps=10 ESS=0.5N exact covariance", L, lz, t0)
