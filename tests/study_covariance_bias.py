@@ -18,10 +18,12 @@ this prints log Zhat - log Z over a few seeds
 * optionally (--L32) one run of the 32 x 32 precision-check workload
   (N = 4096, ESS 0.5 N, 10 sweeps or --L32-sweeps) with each covariance (about 10
   minutes at 10 sweeps, two hours at 100),
+* optionally (--L16) the 16 x 16 free field at the same D/N = 1/4 as the 32 x 32 run
+  (N = 1024, 10 and 100 sweeps, two seeds),
 * optionally (--broken) the interacting 8 x 8 workload (m2 = -4, lam = 8, N = 1024),
   which has no closed form, as the sweeps per temperature grow.
 
-    python tests/study_covariance_bias.py [--L32 [--L32-sweeps 100]] [--broken]
+    python tests/study_covariance_bias.py [--L16] [--L32 [--L32-sweeps 100]] [--broken]
 """
 import argparse
 import os
@@ -148,6 +150,7 @@ def report(label, L, lz, t0):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--L32", action="store_true", help="also run the 32 x 32, N = 4096 workload once (minutes)")
+    ap.add_argument("--L16", action="store_true", help="also the 16 x 16 free field at N = 1024, 10 and 100 sweeps")
     ap.add_argument("--broken", action="store_true", help="also the interacting 8 x 8 workload (minutes)")
     ap.add_argument("--L32-sweeps", type=int, default=10, help="sweeps per temperature of the --L32 runs")
     ap.add_argument("--seeds", type=int, default=4)
@@ -178,6 +181,10 @@ def main():
         t0 = time.time()
         report("L=8 N=1024 sweeps=10 ESS=0.5N %s" % mode, L,
                np.array([variant_logz(L, 1024, s, mode) for s in range(a.seeds)]), t0)
+    if a.L16:
+        for n_mcmc in (10, 100):
+            t0 = time.time()
+            report("L=16 N=1024 sweeps=%d ESS=0.5N" % n_mcmc, 16, logz_seeds(16, 1024, 0.5, n_mcmc, 2), t0)
     if a.broken:
         broken_phase(a.seeds)
     if a.L32:
