@@ -22,6 +22,7 @@ With --gpus N > 1 (torchrun) each rank advances its own independent replica
 (the sampler has no data-parallel exchange at this size: "replicas only").
 """
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -58,6 +59,8 @@ def parse():
     ap.add_argument("--workload", default="single", choices=["single", "batch", "kernels"],
                     help="single: one L=64 run; batch: 64 independent runs of mixed lattice sizes")
     ap.add_argument("--batch-runs", type=int, default=64)
+    ap.add_argument("--fp32-steps", type=int, default=3,
+                    help="temperatures of the plain FP32 comparator timed after the mixed form (0: skip)")
     return ap.parse_args()
 
 
@@ -338,6 +341,78 @@ def run_reference(a):
     return 0
 
 
+def time_steps(p, cfg, steps, warmup, stream, dist, local):
+    """Times `steps` temperatures of a run of `cfg` after `warmup` untimed ones (CUDA events on
+    the run's stream, barrier and synchronize on both sides). A run that reaches beta = 1
+    is continued by a fresh replica of the same configuration. Returns the elapsed device
+    milliseconds, the stage timers, the kernel launches, the last run, the sampler's state
+    over the timed temperatures and the clock sampler."""
+    import torch
+
+    def fresh():
+        r = p.Run(cfg)
+        r.set_stage_timing(True)
+        return r
+
+    run = fresh()
+    for _ in range(warmup):
+        if run.temper_step() >= 1.0:
+            run = fresh()
+    run.stage_times(reset=True)
+    l0 = run.kernel_launches()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stage_acc = {}
+    launches = 0
+    betas, accs, esss, replicas = [], [], [], 1
+
+    def bank(r):
+        for k, (ms, n) in r.stage_times(reset=True).items():
+            s = stage_acc.setdefault(k, [0.0, 0])
+            s[0] += ms
+            s[1] += n
+
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(steps):
+            b = run.temper_step()
+            betas.append(b)
+            if b >= 1.0:
+                # the run reached beta = 1: account and continue on a fresh replica
+                bank(run)
+                launches += run.kernel_launches() - l0
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                partial = ev0.elapsed_time(ev1)
+                o = run.observables()  # outside the timed interval
+                accs.append(o["acc_rate"])
+                esss.append(o["ess"])
+                run = fresh()
+                replicas += 1
+                l0 = run.kernel_launches()
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                stage_acc.setdefault("_partial_ms", [0.0, 0])[0] += partial
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    elapsed_ms = ev0.elapsed_time(ev1) + stage_acc.pop("_partial_ms", [0.0, 0])[0]
+    if dist is not None:
+        dist.barrier()
+    launches += run.kernel_launches() - l0
+    bank(run)
+    if betas and betas[-1] < 1.0:
+        o = run.observables()
+        accs.append(o["acc_rate"])
+        esss.append(o["ess"])
+    finite = [x for x in accs if x == x]
+    telemetry = {"temperatures_timed": steps, "replicas": replicas, "beta_after_each_step": betas,
+                 "acc_rate_last_step_per_replica": accs, "ess_last_step_per_replica": esss,
+                 "acc_rate_mean": sum(finite) / len(finite) if finite else float("nan")}
+    return elapsed_ms, stage_acc, launches, run, telemetry, clk
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -360,53 +435,9 @@ def main():
                    seed=1000 + rank, kind=p.SMC_HMC if hmc else p.SMC_RW)
     stream = torch.cuda.current_stream()
 
-    def fresh():
-        r = p.Run(cfg)
-        r.set_stage_timing(True)
-        return r
-
-    run = fresh()
-    for _ in range(a.warmup):
-        if run.temper_step() >= 1.0:
-            run = fresh()
-    run.stage_times(reset=True)
-    l0 = run.kernel_launches()
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    stage_acc = {}
-    launches = 0
-    with Clocks(local) as clk:
-        ev0.record(stream)
-        for _ in range(a.steps):
-            if run.temper_step() >= 1.0:
-                # the run reached beta = 1: account and continue on a fresh replica
-                for k, (ms, n) in run.stage_times(reset=True).items():
-                    s = stage_acc.setdefault(k, [0.0, 0])
-                    s[0] += ms
-                    s[1] += n
-                launches += run.kernel_launches() - l0
-                ev1.record(stream)
-                torch.cuda.synchronize()
-                partial = ev0.elapsed_time(ev1)
-                run = fresh()
-                l0 = run.kernel_launches()
-                ev0 = torch.cuda.Event(enable_timing=True)
-                ev0.record(stream)
-                stage_acc.setdefault("_partial_ms", [0.0, 0])[0] += partial
-        ev1.record(stream)
-        torch.cuda.synchronize()
-    elapsed_ms = ev0.elapsed_time(ev1) + stage_acc.pop("_partial_ms", [0.0, 0])[0]
-    if dist is not None:
-        dist.barrier()
-    launches += run.kernel_launches() - l0
-    for k, (ms, n) in run.stage_times(reset=True).items():
-        s = stage_acc.setdefault(k, [0.0, 0])
-        s[0] += ms
-        s[1] += n
+    elapsed_ms, stage_acc, launches, run, telemetry, clk = time_steps(p, cfg, a.steps, a.warmup, stream, dist,
+                                                                      local)
     elapsed_ms = max_over_ranks(elapsed_ms, dist)
-    obs = run.observables()
     units_per_step = a.N * D * a.n_mcmc
     value = world * units_per_step * a.steps / (elapsed_ms * 1e-3)
     # wall time of the sweeps (their normals, proposal and accept overlap on three streams)
@@ -419,7 +450,7 @@ def main():
     dom = max(("chol_update", "propose", "accept", "normals"), key=lambda k: stage_acc.get(k, [0, 0])[0])
     ms_tot, n_l = stage_acc[dom]
     avg_s = ms_tot / max(n_l, 1) * 1e-3
-    acc = obs["acc_rate"] if obs["acc_rate"] == obs["acc_rate"] else 0.25
+    acc = telemetry["acc_rate_mean"] if telemetry["acc_rate_mean"] == telemetry["acc_rate_mean"] else 0.25
     extra = {}
     if dom == "chol_update":
         # exact digit emulation of the FP64 update A22 -= P P^T: 36 bf16 digit-plane products
@@ -481,21 +512,34 @@ def main():
             "config": workload(a), "gpu_launches": launches,
             "mutation_only": {"value": world * units_per_step * a.steps / (mutation_ms * 1e-3) if mutation_ms else None,
                               "unit": "site-updates/s", "ms_per_step": mutation_ms / a.steps},
-            "roofline": roofline, "stages": stages, "clocks": clk.summary(),
-            "sampler": {"beta": obs["beta"], "acc_rate": obs["acc_rate"], "ess": obs["ess"],
-                        "n_steps": obs["n_steps"]}}
+            "roofline": roofline, "stages": stages, "clocks": clk.summary(), "sampler": telemetry}
     run.close()
+    if prec == 2 and not hmc and a.fp32_steps > 0:
+        # the plain FP32 form (SIMT float GEMMs, float covariance and Cholesky, FP64 log Z)
+        # on the same workload and seed, timed the same way: the comparator of the metric
+        cfg32 = dataclasses.replace(cfg, precision=p.FP32)
+        ms32, acc32, l32, r32, tel32, clk32 = time_steps(p, cfg32, a.fp32_steps, 3, stream, dist, local)
+        ms32 = max_over_ranks(ms32, dist)
+        mut32 = acc32.get("mutation", [0, 0])[0] or \
+            sum(acc32.get(k, [0, 0])[0] for k in ("normals", "propose", "accept"))
+        r32.close()
+        line["fp32_comparator"] = {
+            "value": world * units_per_step * a.fp32_steps / (ms32 * 1e-3), "unit": "site-updates/s",
+            "steps": a.fp32_steps, "warmup": 3, "ms_per_step": ms32 / a.fp32_steps,
+            "mutation_only": world * units_per_step * a.fp32_steps / (mut32 * 1e-3) if mut32 else None,
+            "dtype": PREC_DTYPE["fp32"], "gpu_launches": l32, "sampler": tel32, "clocks": clk32.summary(),
+            "stages": {k: {"ms_per_step": v[0] / a.fp32_steps, "launches": v[1]} for k, v in acc32.items() if v[1]},
+            "speedup_of_mixed": (ms32 / a.fp32_steps) / (elapsed_ms / a.steps)}
 
     if not a.no_e2e:
         # the same metric through the public API with the population held in pinned host
         # memory: the same run (seed, warm-up steps) as the device-timed one, and every
         # timed step copies the population in (H2D), advances one temperature, copies the
         # new population out (D2H) and reads log Z back
-        r2 = fresh()
-        r2.set_stage_timing(False)
+        r2 = p.Run(cfg)
         for _ in range(a.warmup):
             if r2.temper_step() >= 1.0:
-                r2 = fresh()
+                r2 = p.Run(cfg)
         host = torch.empty((a.N, D), dtype=torch.float64 if prec == 0 else torch.float32).pin_memory()
         r2.copy_particles(host)
         torch.cuda.synchronize()

@@ -148,6 +148,18 @@ const char* phi4_last_error(void);
 /* Number of streaming multiprocessors of the current device (host query). */
 phi4_status phi4_device_sm_count(int32_t* out);
 
+/* Limit, in SM clock cycles, of the library's software waits on the current device:
+ * the grid barrier of the ESS bisection, the flags between the diagonal-block CTA and
+ * the CTAs of its streamed inverse, and the hand-offs between the diagonal block's
+ * warps. A wait that reaches the limit gives up: its kernel sets the timeout bit of
+ * the run's device status word and returns, and the next synchronising call of the
+ * run returns PHI4_ERR_TIMEOUT. cycles <= 0 restores the default (2e9, about one
+ * second). Waits on TMA copies and tensor-core commits keep the default: they wait for
+ * hardware that completes by itself. Synchronous; affects every later launch on the
+ * device, so set it while no run is in flight. Failure detection (no counterpart in the
+ * paper): a short limit lets a test see a wait give up without hanging anything. */
+phi4_status phi4_set_spin_limit(int64_t cycles);
+
 /* ------------------------------------------------------------------------ */
 /* Run-level API: a population advanced one outer step per call.             */
 /* ------------------------------------------------------------------------ */
@@ -307,11 +319,23 @@ phi4_status phi4_resample_systematic(const double* w, int32_t N, uint32_t U, int
  * N > PHI4_RESAMPLE_STATIC_MAX_N returns PHI4_ERR_ARG (use phi4_resample_systematic).
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress
  * with that device current) and caches it; make that first call before any stream
- * capture. All calls share the one array and it keeps the last call's contents (each
+ * capture. A cudaDeviceReset of that device discards the array and with it the cached
+ * address: do not call this entry point on the device after such a reset. All calls share the one array and it keeps the last call's contents (each
  * launch writes every entry it reads, so nothing needs clearing): calls that overlap
  * on the GPU, e.g. on two streams, race and must be serialised by the caller. */
 #define PHI4_RESAMPLE_STATIC_MAX_N 65536
 phi4_status phi4_resample_systematic_static(const double* w, int32_t N, uint32_t U, int32_t* anc, void* stream);
+
+/* Population observables on the device (Sec. 2: magnetisation M = (1/D) sum_x phi_x;
+ * App. F: mode balance): M[i] (device double[N]) of each field of phi (device [N][D],
+ * D = L*L, dtype F64 or F32), then, with weights w (device double[N], >= 0, positive
+ * sum; NULL for uniform weights) normalised by their sum, out (device double[6]):
+ * out[0] = <M>, out[1] = <|M|>, out[2] = <M^2>, out[3] = chi = D (<M^2> - <M>^2),
+ * out[4] = mode balance = weight of M > 0 over weight of M < 0 (zeros ignored; +inf
+ * when no M < 0, NaN when neither side has weight), out[5] = the sum of the weights.
+ * FP64 sums in a fixed order (deterministic). smc_observables uses this reduction. */
+phi4_status phi4_observables(const void* phi, int32_t dtype, int32_t N, int32_t L, const double* w, double* M,
+                             double* out, void* stream);
 
 /* Particle gather after resampling (Sec. 2 (i)):
  * dst row i = src row anc[i] for i < N, rows of `row_bytes` (device buffers;

@@ -93,6 +93,7 @@ _I32, _U32, _U64, _F64, _SZ = ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64, 
 _SIGS = {
     "phi4_last_error": ([], ctypes.c_char_p),
     "phi4_device_sm_count": ([ctypes.POINTER(_I32)], _I32),
+    "phi4_set_spin_limit": ([ctypes.c_int64], _I32),
     "phi4_workspace_bytes": ([ctypes.POINTER(CConfig), ctypes.POINTER(_SZ)], _I32),
     "smc_init": ([ctypes.POINTER(CConfig), _P, _SZ, _P, ctypes.POINTER(_P)], _I32),
     "smc_temper_step": ([_P, ctypes.POINTER(_F64)], _I32),
@@ -118,6 +119,7 @@ _SIGS = {
     "phi4_resample_systematic": ([_P, _I32, _U32, _P, _P, _SZ, _P], _I32),
     "phi4_resample_systematic_static": ([_P, _I32, _U32, _P, _P], _I32),
     "phi4_gather_rows": ([_P, _P, _SZ, _I32, _P, _P], _I32),
+    "phi4_observables": ([_P, _I32, _I32, _I32, _P, _P, _P, _P], _I32),
     "phi4_covariance_scratch_bytes": ([_I32, _I32, _I32], _SZ),
     "phi4_covariance": ([_P, _I32, _I32, _I32, _P, _P, _SZ, _P], _I32),
     "phi4_cholesky_scratch_bytes": ([_I32], _SZ),
@@ -392,6 +394,23 @@ def resample_systematic_static(w, U, stream=None):
     anc = torch.empty(N, dtype=torch.int32, device=w.device)
     _check(lib().phi4_resample_systematic_static(_ptr(w), N, U, _ptr(anc), _stream(stream)))
     return anc
+
+
+def observables(phi, L, w=None, stream=None):
+    """Device FP64 moments of the magnetisation: returns (M, out) with
+    out = [<M>, <|M|>, <M^2>, chi, mode balance, total weight] (device tensors)."""
+    import torch
+    N = phi.shape[0]
+    dt = DT_F64 if phi.dtype == torch.float64 else DT_F32
+    M = torch.empty(N, dtype=torch.float64, device=phi.device)
+    out = torch.empty(6, dtype=torch.float64, device=phi.device)
+    _check(lib().phi4_observables(_ptr(phi), dt, N, L, _ptr(w), _ptr(M), _ptr(out), _stream(stream)))
+    return M, out
+
+
+def set_spin_limit(cycles):
+    """Limit (SM clock cycles) of the library's software waits; <= 0 restores the default."""
+    _check(lib().phi4_set_spin_limit(int(cycles)))
 
 
 def gather_rows(src, anc, stream=None):

@@ -675,20 +675,13 @@ phi4_status smc_observables(const phi4_run* rc, phi4_obs* o) {
   const int N = r->cfg.N;
   {
     StageScope sc(r, STG_OBS);
-    CUDA_TRY(launch_magnetisation(r->phi, r->dtype, N, r->D, r->M, r->stream));
+    CUDA_TRY(launch_observables(r->phi, r->dtype, N, r->D, nullptr, r->M, r->scal + SC_OBS, r->stream));
+    r->kernel_launches += 2;
   }
-  std::vector<double> M(N);
-  CUDA_TRY(cudaMemcpyAsync(M.data(), r->M, (size_t)N * 8, cudaMemcpyDeviceToHost, r->stream));
+  double h[6];
+  CUDA_TRY(cudaMemcpyAsync(h, r->scal + SC_OBS, sizeof(h), cudaMemcpyDeviceToHost, r->stream));
   CUDA_TRY(cudaStreamSynchronize(r->stream));
   if (r->timing) collect_stage_times(r);
-  double s1 = 0, sa = 0, s2 = 0, pos = 0, neg = 0;
-  for (int i = 0; i < N; ++i) {
-    s1 += M[i];
-    sa += fabs(M[i]);
-    s2 += M[i] * M[i];
-    if (M[i] > 0) pos += 1;
-    else if (M[i] < 0) neg += 1;
-  }
   memset(o, 0, sizeof(*o));
   o->beta = r->beta;
   double lz = NAN, le = NAN;
@@ -696,11 +689,11 @@ phi4_status smc_observables(const phi4_run* rc, phi4_obs* o) {
   if (ps != PHI4_OK) return ps;
   o->logz = lz;
   o->logz_err = le;
-  o->mean_M = s1 / N;
-  o->mean_absM = sa / N;
-  o->mean_M2 = s2 / N;
-  o->chi = r->D * (o->mean_M2 - o->mean_M * o->mean_M);
-  o->mode_balance = neg > 0 ? pos / neg : (pos > 0 ? INFINITY : NAN);
+  o->mean_M = h[0];
+  o->mean_absM = h[1];
+  o->mean_M2 = h[2];
+  o->chi = h[3];
+  o->mode_balance = h[4];
   o->ess = r->last_ess;
   o->acc_rate = r->last_acc;
   o->n_steps = r->t;
@@ -759,6 +752,13 @@ phi4_status smc_free(phi4_run* r) {
   return PHI4_OK;
 }
 
+phi4_status phi4_set_spin_limit(int64_t cycles) {
+  const long long c = cycles > 0 ? (long long)cycles : kSpinLimitCyclesDefault;
+  CUDA_TRY(set_spin_limit_temper(c));
+  CUDA_TRY(set_spin_limit_chol(c));
+  return PHI4_OK;
+}
+
 phi4_status phi4_kernel_launches(const phi4_run* r, int64_t* out) {
   ARG_CHECK(r && out, "NULL argument");
   *out = r->kernel_launches;
@@ -787,6 +787,15 @@ phi4_status phi4_stage_times(phi4_run* r, double* ms_out, int64_t* launches_out,
 }
 
 /* -------------------------- kernel-level API -------------------------- */
+
+phi4_status phi4_observables(const void* phi, int32_t dtype, int32_t N, int32_t L, const double* w, double* M,
+                             double* out, void* stream) {
+  ARG_CHECK(phi && M && out, "NULL argument");
+  ARG_CHECK(dtype == PHI4_DT_F64 || dtype == PHI4_DT_F32, "dtype %d: fields are F64 or F32", dtype);
+  ARG_CHECK(N >= 1 && L >= 1 && (int64_t)L * L <= (1 << 20), "bad sizes N = %d, L = %d", N, L);
+  CUDA_TRY(launch_observables(phi, dtype, N, L * L, w, M, out, (cudaStream_t)stream));
+  return PHI4_OK;
+}
 
 phi4_status phi4_philox_normals(uint64_t seed, uint64_t stream_id, int32_t kind, uint32_t step, uint32_t sub,
                                 int32_t row0, int32_t n_rows, int32_t n_cols, int32_t ld, int32_t dtype, void* out,

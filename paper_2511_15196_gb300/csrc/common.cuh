@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
+#include "internal.h"
 
 #define PHI4_DEV __device__ __forceinline__
 
@@ -16,8 +17,19 @@ enum : uint32_t {
   ST_BISECT_FLOOR = 8u,  // no positive dbeta kept ESS >= rho N
 };
 
-// About one second of SM clock: every spin-wait in this library gives up after it.
-constexpr long long kSpinLimitCycles = 2000000000LL;
+// Every spin-wait in this library gives up after about one second of SM clock.
+constexpr long long kSpinLimitCycles = kSpinLimitCyclesDefault;
+
+// Limit of the software waits (grid barriers, flags between CTAs, hand-offs between
+// warps), in SM clock cycles, kSpinLimitCycles unless phi4_set_spin_limit changed it.
+// Each translation unit holds its own copy of this variable; phi4_set_spin_limit sets
+// every copy (see PHI4_SPIN_LIMIT_SETTER). The waits on TMA copies and tensor-core
+// commits keep kSpinLimitCycles: they wait on hardware that completes by itself, and
+// leaving them early would leave copies in flight into the CTA's shared memory.
+static __device__ long long g_spin_limit = kSpinLimitCycles;
+PHI4_DEV long long spin_limit() { return *(volatile long long*)&g_spin_limit; }
+#define PHI4_SPIN_LIMIT_SETTER(fn) \
+  cudaError_t fn(long long cycles) { return cudaMemcpyToSymbol(g_spin_limit, &cycles, sizeof(cycles)); }
 
 // CTA-scope mbarrier helpers (shared-memory barrier objects, phase parity waits).
 PHI4_DEV uint32_t cta_smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -43,15 +55,15 @@ PHI4_DEV bool cta_mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the phase of the given parity; false after kSpinLimitCycles or
-// once another warp has raised *abort_flag.
+// Bounded wait for the phase of the given parity (a hand-off between warps); false
+// after spin_limit() cycles or once another warp has raised *abort_flag.
 PHI4_DEV bool cta_mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
   if (cta_mbar_try_wait(bar, parity)) return true;
-  const long long t0 = clock64();
+  const long long t0 = clock64(), lim = spin_limit();
   for (;;) {
     if (cta_mbar_try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (clock64() - t0 > kSpinLimitCycles) return false;
+    if (clock64() - t0 > lim) return false;
   }
 }
 
@@ -68,11 +80,11 @@ PHI4_DEV int cta_flag_acquire(const int* f) {
 }
 PHI4_DEV bool cta_flag_wait_geq(const int* f, int target, volatile int* abort_flag) {
   if (cta_flag_acquire(f) >= target) return true;
-  const long long t0 = clock64();
+  const long long t0 = clock64(), lim = spin_limit();
   for (;;) {
     if (cta_flag_acquire(f) >= target) return true;
     if (*abort_flag) return false;
-    if (clock64() - t0 > kSpinLimitCycles) return false;
+    if (clock64() - t0 > lim) return false;
   }
 }
 

@@ -8,6 +8,9 @@
 
 namespace phi4 {
 
+// About one second of SM clock: the default limit of every spin-wait in this library.
+constexpr long long kSpinLimitCyclesDefault = 2000000000LL;
+
 struct ActionParams {
   int L, D, N;
   double m2, lam, c_kin, c_mass;
@@ -58,6 +61,10 @@ cudaError_t launch_accept_delta(float* phi, const void* delta_f16, const ActionP
 cudaError_t launch_z2_flip(uint64_t seed, uint64_t stream_id, uint32_t step, void* phi, int dtype, int N, int D,
                            cudaStream_t s);
 cudaError_t launch_magnetisation(const void* phi, int dtype, int N, int D, double* M, cudaStream_t s);
+// kernels_obs.cu: M per particle into M[N], then the weighted moments (w NULL: uniform)
+// out[0..5] = <M>, <|M|>, <M^2>, chi, mode balance, total weight (FP64, one CTA)
+cudaError_t launch_observables(const void* phi, int dtype, int N, int D, const double* w, double* M, double* out,
+                               cudaStream_t s);
 
 // kernels_temper.cu
 size_t bisect_scratch_bytes(int N);
@@ -190,5 +197,9 @@ cudaError_t launch_ns_final(const double* dead, long long n_dead, const double* 
 
 // device properties (capi.cu)
 int sm_count();
+
+// limit of the software waits of each translation unit that has them (common.cuh)
+cudaError_t set_spin_limit_temper(long long cycles);
+cudaError_t set_spin_limit_chol(long long cycles);
 
 }  // namespace phi4

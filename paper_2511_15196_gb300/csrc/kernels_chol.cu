@@ -295,7 +295,7 @@ __device__ __forceinline__ void inv_streamed(const T* __restrict__ a, int D, int
     if (have < m + 1) {
       // every lane acquires the flag itself; the decisions are taken warp-wide so that
       // no lane leaves while another still waits in a shuffle
-      const long long t0 = clock64();
+      const long long t0 = clock64(), lim = spin_limit();
       for (;;) {
         const int f = gpu_flag_acquire(col_flag);
         if (__any_sync(0xffffffffu, f < 0)) return;
@@ -303,7 +303,7 @@ __device__ __forceinline__ void inv_streamed(const T* __restrict__ a, int D, int
           have = __reduce_min_sync(0xffffffffu, (unsigned)f);
           break;
         }
-        const int late = lane == 0 ? (clock64() - t0 > kSpinLimitCycles) : 0;
+        const int late = lane == 0 ? (clock64() - t0 > lim) : 0;
         if (__shfl_sync(0xffffffffu, late, 0)) {
           if (lane == 0) atomicOr(status, ST_TIMEOUT);
           return;
@@ -652,6 +652,8 @@ static cudaError_t cholesky_t(T* a, int D, const double* ridge, void* aux, uint3
   }
   return cudaGetLastError();
 }
+
+PHI4_SPIN_LIMIT_SETTER(set_spin_limit_chol)
 
 size_t cholesky_aux_bytes(int D) {
   const size_t nblk = (size_t)(D + NB - 1) / NB;

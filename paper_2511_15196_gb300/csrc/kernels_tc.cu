@@ -109,32 +109,6 @@ PHI4_DEV void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
 }
-// Cluster helpers (the proposal GEMM runs in clusters of two CTAs that share the B
-// tile: each loads half of it and multicasts it to both).
-PHI4_DEV uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-PHI4_DEV void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-// TMA load written at the same shared-memory offset of every CTA in `mask`, each CTA's
-// barrier at that offset receiving the bytes
-PHI4_DEV void tma_load_2d_mc(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
-      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
-      : "memory");
-}
-// commit arriving on the barrier at this offset in every CTA of `mask`
-PHI4_DEV void umma_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                   smem_u32(bar)),
-               "h"(mask)
-               : "memory");
-}
 PHI4_DEV void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 PHI4_DEV void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -155,23 +129,16 @@ PHI4_DEV void tmem_ld32_nw(uint32_t taddr, uint32_t (&r)[32]) {
                : "r"(taddr));
 }
 
-// CTAs per cluster: the proposal's clusters of two share each B (factor) tile.
-template <int MODE>
-__host__ __device__ constexpr int cluster_size() { return MODE == 0 ? 2 : 1; }
-
-// Work unit u -> this CTA's tile (mb, nb) and number of K blocks. Proposal units are
-// pairs of row tiles (rank 0 and 1 of the cluster) on one column tile, column tiles in
-// decreasing K extent (heaviest first).
-template <int MODE>
-PHI4_DEV void get_tile(const Params& p, int u, int rank, int& mb, int& nb, int& kblocks) {
-  const int pm = (p.tiles_m + 1) / 2;
-  nb = p.tiles_n - 1 - u / pm;
-  mb = (u % pm) * 2 + rank;
+// Work unit u -> tile (mb, nb) and number of K blocks. Column tiles are walked in
+// decreasing K extent (heaviest first); the row tiles of one column tile are
+// consecutive units, so CTAs working at the same time share the factor tile in L2.
+PHI4_DEV void get_tile(const Params& p, int u, int& mb, int& nb, int& kblocks) {
+  nb = p.tiles_n - 1 - u / p.tiles_m;
+  mb = u % p.tiles_m;
   const int kend = min(p.K, (nb + 1) * BN);
   kblocks = (kend + BK - 1) / BK;
 }
 
-template <int MODE>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Params p) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -183,14 +150,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
-  constexpr int CL = cluster_size<MODE>();
-  const int rank = CL > 1 ? (int)cluster_rank() : 0;
-  const int cid = blockIdx.x / CL, ncl = gridDim.x / CL;
+  const int cid = blockIdx.x, ncl = gridDim.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], CL);  // both CTAs' MMAs must be done with a stage before either refills it
+      mbar_init(&empty[s], 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
@@ -209,7 +174,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (CL > 1) cluster_sync_all();  // the peer's barriers exist before any multicast lands
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
@@ -224,17 +188,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       uint32_t phase = 0;
       for (int u = cid; u < p.num_tiles && !*abort_flag; u += ncl) {
         int mb, nb, kblocks;
-        get_tile<MODE>(p, u, rank, mb, nb, kblocks);
+        get_tile(p, u, mb, nb, kblocks);
         for (int kb = 0; kb < kblocks; ++kb) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) { give_up(); break; }
           uint8_t* sa = smem + stage * STAGE_BYTES;
           mbar_expect_tx(&full[stage], STAGE_BYTES);
           tma_load_2d(&tmA, &full[stage], sa, kb * BK, mb * BM);
-          if (CL > 1)  // this CTA's half of the shared B tile, into both CTAs
-            tma_load_2d_mc(&tmB, &full[stage], sa + A_BYTES + rank * (B_BYTES / CL), kb * BK,
-                           nb * BN + rank * (BN / CL), (uint16_t)((1u << CL) - 1u));
-          else
-            tma_load_2d(&tmB, &full[stage], sa + A_BYTES, kb * BK, nb * BN);
+          tma_load_2d(&tmB, &full[stage], sa + A_BYTES, kb * BK, nb * BN);
           if (++stage == STAGES) { stage = 0; phase ^= 1u; }
         }
       }
@@ -245,7 +205,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       uint32_t phase = 0, acc_phase = 0;
       for (int u = cid; u < p.num_tiles && !*abort_flag; u += ncl) {
         int mb, nb, kblocks;
-        get_tile<MODE>(p, u, rank, mb, nb, kblocks);
+        get_tile(p, u, mb, nb, kblocks);
         if (!mbar_wait(&tempty[acc], acc_phase ^ 1u, abort_flag)) { give_up(); break; }
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
@@ -257,10 +217,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk)
             umma_bf16(d_tmem, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), (kb | kk) != 0);
-          if (CL > 1)
-            umma_commit_mc(&empty[stage], (uint16_t)((1u << CL) - 1u));
-          else
-            umma_commit(&empty[stage]);
+          umma_commit(&empty[stage]);
           if (++stage == STAGES) { stage = 0; phase ^= 1u; }
         }
         if (!ok) break;
@@ -276,7 +233,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     uint32_t acc_phase = 0;
     for (int u = cid; u < p.num_tiles; u += ncl) {
       int mb, nb, kblocks;
-      get_tile<MODE>(p, u, rank, mb, nb, kblocks);
+      get_tile(p, u, mb, nb, kblocks);
       if (!mbar_wait(&tfull[acc], acc_phase, abort_flag)) { give_up(); break; }
       tc_fence_after();
       const int gm = mb * BM + r;
@@ -319,8 +276,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
-  // no CTA leaves while its peer may still multicast into it or arrive on its barriers
-  if (CL > 1) cluster_sync_all();
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
@@ -358,27 +313,13 @@ static bool make_map(CUtensorMap* map, const void* ptr, int inner, int rows, int
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int MODE>
 static cudaError_t launch(const CUtensorMap& a, const CUtensorMap& b, const Params& p, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   if (e != cudaSuccess) return e;
-  constexpr int CL = cluster_size<MODE>();
-  int clusters = sm_count() / CL;
-  if (clusters > p.num_tiles) clusters = p.num_tiles;
-  if (clusters < 1) return cudaSuccess;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(clusters * CL));
-  cfg.blockDim = dim3(NUM_THREADS);
-  cfg.dynamicSmemBytes = SMEM_BYTES;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CL;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<MODE>, a, b, p);
+  const int grid = std::min(sm_count(), p.num_tiles);
+  if (grid < 1) return cudaSuccess;
+  tc_gemm_kernel<<<grid, NUM_THREADS, SMEM_BYTES, s>>>(a, b, p);
+  return cudaGetLastError();
 }
 
 }  // namespace tc
@@ -868,8 +809,7 @@ bool tc_available() { return tc::encode_fn() != nullptr; }
 cudaError_t launch_propose_tc(void* delta_f16, const void* Zb, int ldz, const void* Lb, int ldl, int N, int D,
                               float scale, uint32_t* status, cudaStream_t s) {
   CUtensorMap ma, mb;
-  // clusters of two: each CTA loads half (BN / 2 rows) of the shared factor tile
-  if (!tc::make_map(&ma, Zb, D, N, ldz, tc::BM) || !tc::make_map(&mb, Lb, D, D, ldl, tc::BN / 2))
+  if (!tc::make_map(&ma, Zb, D, N, ldz, tc::BM) || !tc::make_map(&mb, Lb, D, D, ldl, tc::BN))
     return cudaErrorInvalidValue;
   tc::Params p{};
   p.M = N;
@@ -877,11 +817,11 @@ cudaError_t launch_propose_tc(void* delta_f16, const void* Zb, int ldz, const vo
   p.K = D;
   p.tiles_m = (N + tc::BM - 1) / tc::BM;
   p.tiles_n = (D + tc::BN - 1) / tc::BN;
-  p.num_tiles = ((p.tiles_m + 1) / 2) * p.tiles_n;  // work units: pairs of row tiles
+  p.num_tiles = p.tiles_m * p.tiles_n;
   p.delta = (__half*)delta_f16;
   p.scale = scale;
   p.status = status;
-  return tc::launch<0>(ma, mb, p, s);
+  return tc::launch(ma, mb, p, s);
 }
 
 cudaError_t launch_gram_tc(const void* H, const void* Lo, int ldx, int D, int N, const int* shift, int a,

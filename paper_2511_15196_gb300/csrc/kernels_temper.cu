@@ -23,14 +23,14 @@ struct GridSync {
 };
 
 PHI4_DEV bool spin_until(const unsigned* bar, unsigned target, const unsigned* abort) {
-  const long long t0 = clock64();
+  const long long t0 = clock64(), lim = spin_limit();
   for (;;) {
     unsigned v, a;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
     if (v >= target) return true;
     asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(a) : "l"(abort) : "memory");
     if (a) return false;
-    if (clock64() - t0 > kSpinLimitCycles) return false;
+    if (clock64() - t0 > lim) return false;
     __nanosleep(32);
   }
 }
@@ -225,6 +225,8 @@ cudaError_t launch_bisect(const double* ell, int N, const double* beta_in, doubl
   if (ept <= 8) return launch_bisect_t<8>(G, ell, N, beta_in, rho, iters, w, out, gs, s);
   return cudaErrorInvalidValue;
 }
+
+PHI4_SPIN_LIMIT_SETTER(set_spin_limit_temper)
 
 cudaError_t launch_logz_accumulate(const double* out, double* logz_kahan, double* beta, cudaStream_t s) {
   logz_accumulate_kernel<<<1, 1, 0, s>>>(out, logz_kahan, beta);

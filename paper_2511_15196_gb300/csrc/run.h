@@ -15,7 +15,7 @@ enum { STG_BISECT, STG_RESAMPLE, STG_GATHER, STG_COV, STG_CHOL, STG_NORMALS, STG
 
 // Device scalars of a run (one 256-byte block).
 enum { SC_OUT = 0 /* 8 doubles: bisection results */, SC_KAHAN = 8 /* 2 */, SC_BETA = 10, SC_RIDGE = 11,
-       SC_NS = 12 /* NS bookkeeping, 8 doubles */, SC_COUNT = 32 };
+       SC_NS = 12 /* NS bookkeeping, 8 doubles */, SC_OBS = 20 /* observables, 6 doubles */, SC_COUNT = 32 };
 
 struct phi4_run {
   phi4_config cfg;

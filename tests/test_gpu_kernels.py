@@ -489,3 +489,45 @@ def test_kappa_config_action_on_the_gpu():
     kin = sum(((np.roll(f, -1, axis=a) - f) ** 2).sum(axis=(1, 2)) for a in (1, 2))
     s_kappa = 0.5 * kappa * kin + (f ** 2 + lam * (f ** 2 - 1.0) ** 2).sum(axis=(1, 2))
     np.testing.assert_allclose(S.cpu().numpy() - p.kappa_logz_shift(lam, L * L), s_kappa, rtol=1e-12)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("weighted", [False, True], ids=["uniform", "weighted"])
+@pytest.mark.parametrize("L,N", [(8, 700), (5, 1), (16, 3001), (64, 8192)])
+def test_observables_reduction_matches_oracle(dtype, weighted, L, N):
+    # a12 on the device: M per field, then the weighted FP64 moments, chi and the mode
+    # balance in one CTA, against the oracle's summary of the same fields and weights
+    from oracle import observables as oobs
+    D = L * L
+    phi = inputs.broken_phase_fields(N, D, seed=N + L).astype(np.float32 if dtype == torch.float32 else np.float64)
+    w = inputs.positive_weights(N, seed=N, zeros=min(3, N - 1)) if weighted else None
+    M, out = p.observables(torch.from_numpy(phi).cuda(), L, None if w is None else torch.from_numpy(w).cuda())
+    torch.cuda.synchronize()
+    ref = oobs.summary(phi.astype(np.float64), w)
+    Mref = phi.astype(np.float64).mean(axis=1)
+    assert np.abs(M.cpu().numpy() - Mref).max() <= 1e-13 * max(1.0, np.abs(Mref).max())
+    o = out.cpu().numpy()
+    for i, k in enumerate(("mean_M", "mean_absM", "mean_M2", "chi")):
+        assert o[i] == pytest.approx(ref[k], rel=1e-11, abs=1e-14), k
+    if math.isinf(ref["mode_balance"]):
+        assert math.isinf(o[4]) and o[4] > 0
+    else:
+        assert o[4] == pytest.approx(ref["mode_balance"], rel=1e-12)
+    assert o[5] == pytest.approx(N if w is None else w.sum(), rel=1e-13)
+
+
+def test_observables_mode_balance_edge_cases():
+    # App. F's edge cases: zeros ignored, +inf with nothing negative, NaN with neither side
+    from oracle import observables as oobs
+    L, D = 4, 16
+    rows = np.array([1.0, 0.0, 2.0, 0.0])
+    phi = np.repeat(rows[:, None], D, axis=1)
+    _, out = p.observables(torch.from_numpy(phi).cuda(), L)
+    o = out.cpu().numpy()
+    assert math.isinf(o[4]) and o[4] > 0 and math.isinf(oobs.mode_balance(rows))
+    _, out = p.observables(torch.zeros((5, D), dtype=torch.float64, device="cuda"), L)
+    assert math.isnan(out.cpu().numpy()[4]) and math.isnan(oobs.mode_balance(np.zeros(5)))
+    phi = np.repeat(np.array([-1.0, 0.0, 3.0, -2.0])[:, None], D, axis=1)
+    w = np.array([0.5, 1.0, 0.25, 0.25])
+    _, out = p.observables(torch.from_numpy(phi).cuda(), L, torch.from_numpy(w).cuda())
+    assert out.cpu().numpy()[4] == pytest.approx(0.25 / 0.75, rel=1e-15)
