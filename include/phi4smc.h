@@ -123,6 +123,15 @@ typedef struct {
  * symmetry moves out of its black-box samplers (Sec. 2) and gives them to its AHMC
  * control. */
 #define PHI4_FLAG_Z2_FLIP 1
+/* phi4_config.flags. FREE_KERNEL_COV (SMC_RW, SMC_HMC; needs c_mass * m2 > 0): the
+ * covariance that scales the proposals (the random-walk factor, HMC's inverse mass) is
+ * not estimated from the population but is, at each new beta, the exact covariance of
+ * the Gaussian part of the tempered target (phi4_free_field_covariance); for lambda = 0
+ * that is the target's own covariance. It does not depend on the particles it moves, so
+ * with it the sampler's evidence estimate is unbiased in Z. A control for comparisons
+ * with the free field's closed form: the paper's sampler estimates the covariance from
+ * the population (flag off). */
+#define PHI4_FLAG_FREE_KERNEL_COV 2
 
 typedef struct {
   double beta;               /* current inverse temperature (SMC) */
@@ -211,6 +220,20 @@ phi4_status smc_copy_particles(const phi4_run* run, void* dst, size_t bytes);
  * smc_copy_particles) and recomputes their action and log-weights on the run's
  * stream (enqueued; returns after the copy is enqueued). */
 phi4_status smc_load_particles(phi4_run* run, const void* src, size_t bytes);
+
+/* Checkpoint and resume (no counterpart in the paper): the state that determines every
+ * later step of a run, copied to or from a caller's host buffer of phi4_state_bytes:
+ * a header (the configuration, the temperature or iteration counter that fixes the
+ * Philox counters of the next step, beta, the ridge level, the counters and, for nested
+ * sampling, log X and the running log Z), then the fields, S, |phi|^2 and ell of every
+ * particle, the run's scalar block (Kahan pair of log Z, beta, NS bookkeeping) and the
+ * nested-sampling dead points. smc_restore_state into a run created with the identical
+ * configuration (checked) continues bit for bit as the saved run would have; the
+ * counters are restored too. Both synchronise the run's stream. Not for batch handles
+ * (save and restore the members). */
+phi4_status phi4_state_bytes(const phi4_run* run, size_t* bytes);
+phi4_status smc_save_state(const phi4_run* run, void* host_dst, size_t bytes);
+phi4_status smc_restore_state(phi4_run* run, const void* host_src, size_t bytes);
 
 /* Releases the handle (not the workspace); for a batch handle, every member.
  * Synchronises the run's stream. */
@@ -325,6 +348,21 @@ phi4_status phi4_resample_systematic(const double* w, int32_t N, uint32_t U, int
  * on the GPU, e.g. on two streams, race and must be serialised by the caller. */
 #define PHI4_RESAMPLE_STATIC_MAX_N 65536
 phi4_status phi4_resample_systematic_static(const double* w, int32_t N, uint32_t U, int32_t* anc, void* stream);
+
+/* Exact covariance of the Gaussian part of the tempered target at beta = *d_beta (device
+ * double): the log density -beta S - (1-beta) |phi|^2 / 2 (keep_reference: -|phi|^2 / 2 -
+ * beta S) has the quadratic part -(1/2) phi^T P phi with P = a I + 2 beta (c_kin K +
+ * c_mass m2 I), K the lattice Laplacian form of Eq. (1)'s kinetic term, a = 1 - beta (1
+ * with the reference kept); sigma (device double [D][D], D = L*L, every element written)
+ * = P^{-1}, formed from P's Fourier eigenvalues a + 2 beta (c_kin sum_mu 4 sin^2(pi k_mu /
+ * L) + c_mass m2) as a function of the site displacement, in FP64. Needs c_mass m2 > 0
+ * (P is then positive definite for every beta in [0, 1]). `scratch` (device,
+ * phi4_free_covariance_scratch_bytes(L)). The free field's covariance (lambda = 0) along
+ * the tempering path of Sec. 2; used by PHI4_FLAG_FREE_KERNEL_COV. */
+size_t phi4_free_covariance_scratch_bytes(int32_t L);
+phi4_status phi4_free_field_covariance(int32_t L, const double* d_beta, double m2, double c_kin, double c_mass,
+                                       int32_t keep_reference, double* sigma, void* scratch, size_t scratch_bytes,
+                                       void* stream);
 
 /* Population observables on the device (Sec. 2: magnetisation M = (1/D) sum_x phi_x;
  * App. F: mode balance): M[i] (device double[N]) of each field of phi (device [N][D],

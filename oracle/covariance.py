@@ -40,3 +40,27 @@ def regularised_cholesky(Sigma, jitter_rel=1e-8, max_tries=6, start_level=0):
         except np.linalg.LinAlgError:
             delta *= 10.0
     raise np.linalg.LinAlgError("covariance not positive definite after %d ridge increases" % max_tries)
+
+
+def gaussian_part_covariance(L, beta, m2, c_kin=1.0, c_mass=1.0, keep_reference=False):
+    """Covariance of the Gaussian part of the tempered target gamma_beta (Sec. 2 tempering
+    path), a kernel covariance that does not depend on the particles.
+
+    log gamma_beta = -beta S - (1 - beta) |phi|^2 / 2 (with the reference kept:
+    -|phi|^2 / 2 - beta S); its quadratic part is -(1/2) phi^T P phi with
+    P = a I + 2 beta (c_kin K + c_mass m2 I), K the form of Eq. (1)'s kinetic term,
+    phi^T K phi = sum_x sum_mu phi_x (2 phi_x - phi_{x+mu} - phi_{x-mu}), and a = 1 - beta
+    (1 with the reference kept). Returns P^{-1}; for lambda = 0 it is the target's
+    covariance. K is assembled term by term from that sum (on L <= 2 several
+    neighbour terms land on the same entry)."""
+    D = L * L
+    K = np.zeros((D, D))
+    for r in range(L):
+        for c in range(L):
+            x = r * L + c
+            for rr, cc in (((r + 1) % L, c), ((r - 1) % L, c), (r, (c + 1) % L), (r, (c - 1) % L)):
+                K[x, x] += 1.0           # phi_x * phi_x, once per neighbour term (2 per direction)
+                K[x, rr * L + cc] -= 1.0
+    a = 1.0 if keep_reference else 1.0 - beta
+    P = a * np.eye(D) + 2.0 * beta * (c_kin * K + c_mass * m2 * np.eye(D))
+    return np.linalg.inv(P)

@@ -8,7 +8,9 @@ Outer step at temperature index t (t = 1, 2, ...), in the paper's order:
   2. reweight, log Z += log mean exp(dbeta ell) (Kahan);
   3. systematic resampling with offset word (KIND_RESAMPLE, t, 0, 0, 0)[0];
   4. re-estimate the particle covariance and its Cholesky factor (ridge level
-     carried over from the previous step);
+     carried over from the previous step); with kernel_cov = "gaussian_part" the
+     covariance is instead the exact one of the Gaussian part of the new tempered
+     target (a particle-independent control for the free field's closed form);
   5. n_mcmc random-walk Metropolis sweeps targeting gamma_{beta + dbeta} (or, with
      inner = "irmh", independent Metropolis-Hastings sweeps, oracle.irmh; with inner = "hmc",
      HMC transitions with the covariance diagonal as inverse mass, oracle.hmc);
@@ -47,6 +49,8 @@ class SMCConfig:
     inner: str = "rw"              # "rw": random-walk sweeps; "irmh": independent MH sweeps (oracle.irmh);
                                    # "hmc": HMC transitions (oracle.hmc)
     hmc_step: float = 0.0          # <= 0: oracle.hmc.default_step(D)
+    kernel_cov: str = "population"  # "population": the resampled population's covariance (App. A);
+                                    # "gaussian_part": covariance.gaussian_part_covariance at the new beta
 
     @property
     def D(self):
@@ -107,7 +111,11 @@ class SMC:
         U = philox.word32(c.seed, c.stream, philox.KIND_RESAMPLE, t)
         anc = resample.systematic(w, U)
         self.phi, self.S, self.sq = self.phi[anc], self.S[anc], self.sq[anc]
-        mu, Sigma = covariance.sample_covariance(self.phi)
+        if c.kernel_cov == "gaussian_part":
+            mu = self.phi.mean(axis=0)
+            Sigma = covariance.gaussian_part_covariance(c.L, beta_new, c.m2, c.c_kin, c.c_mass, c.keep_reference)
+        else:
+            mu, Sigma = covariance.sample_covariance(self.phi)
         Lc, delta, _, self.ridge_level = covariance.regularised_cholesky(Sigma, c.jitter_rel,
                                                                          start_level=self.ridge_level)
         n_acc = 0

@@ -21,6 +21,7 @@ FP64, FP32, MIXED_BF16 = 0, 1, 2
 DT_F64, DT_F32, DT_BF16 = 0, 1, 2
 RNG_INIT, RNG_RESAMPLE, RNG_PROPOSE, RNG_ACCEPT, RNG_NS_START, RNG_NS_DIRECTION, RNG_NS_SLICE, RNG_FLIP = range(1, 9)
 FLAG_Z2_FLIP = 1
+FLAG_FREE_KERNEL_COV = 2
 N_STAGES = 14
 
 _STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_NOT_PD", 4: "ERR_NONFINITE", 5: "ERR_DONE",
@@ -77,7 +78,8 @@ class Config:
     seed: int = 0
     stream_id: int = 0
     chol_mode: int = 0
-    flags: int = 0  # FLAG_Z2_FLIP: global phi -> -phi move after each temperature's sweeps
+    flags: int = 0  # FLAG_Z2_FLIP: global phi -> -phi move after each temperature's sweeps;
+    # FLAG_FREE_KERNEL_COV: exact Gaussian-part covariance in place of the population's
 
     def to_c(self):
         return CConfig(self.L, self.N, self.kind, self.precision, self.m2, self.lam, self.c_kin, self.c_mass,
@@ -103,6 +105,9 @@ _SIGS = {
     "smc_copy_particles": ([_P, _P, _SZ], _I32),
     "smc_load_particles": ([_P, _P, _SZ], _I32),
     "smc_free": ([_P], _I32),
+    "phi4_state_bytes": ([_P, ctypes.POINTER(_SZ)], _I32),
+    "smc_save_state": ([_P, _P, _SZ], _I32),
+    "smc_restore_state": ([_P, _P, _SZ], _I32),
     "phi4_batch_workspace_bytes": ([_P, _I32, ctypes.POINTER(_SZ)], _I32),
     "smc_init_batch": ([_P, _I32, _P, _SZ, _P, ctypes.POINTER(_P)], _I32),
     "smc_temper_step_batch": ([_P, ctypes.POINTER(_I32)], _I32),
@@ -120,6 +125,8 @@ _SIGS = {
     "phi4_resample_systematic_static": ([_P, _I32, _U32, _P, _P], _I32),
     "phi4_gather_rows": ([_P, _P, _SZ, _I32, _P, _P], _I32),
     "phi4_observables": ([_P, _I32, _I32, _I32, _P, _P, _P, _P], _I32),
+    "phi4_free_covariance_scratch_bytes": ([_I32], _SZ),
+    "phi4_free_field_covariance": ([_I32, _P, _F64, _F64, _F64, _I32, _P, _P, _SZ, _P], _I32),
     "phi4_covariance_scratch_bytes": ([_I32, _I32, _I32], _SZ),
     "phi4_covariance": ([_P, _I32, _I32, _I32, _P, _P, _SZ, _P], _I32),
     "phi4_cholesky_scratch_bytes": ([_I32], _SZ),
@@ -232,6 +239,19 @@ class Run:
         """Copy the current fields into `dst` (a host or device tensor of N x D elements)."""
         _check(lib().smc_copy_particles(self.handle, _ptr(dst), dst.numel() * dst.element_size()))
         return dst
+
+    def save_state(self):
+        """The run's state as bytes (smc_save_state)."""
+        n = _SZ()
+        _check(lib().phi4_state_bytes(self.handle, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(lib().smc_save_state(self.handle, buf, n.value))
+        return buf.raw
+
+    def restore_state(self, state):
+        """Continue from bytes written by save_state of a run with the same configuration."""
+        buf = ctypes.create_string_buffer(state, len(state))
+        _check(lib().smc_restore_state(self.handle, buf, len(state)))
 
     def kernel_launches(self):
         n = ctypes.c_int64()
@@ -406,6 +426,19 @@ def observables(phi, L, w=None, stream=None):
     out = torch.empty(6, dtype=torch.float64, device=phi.device)
     _check(lib().phi4_observables(_ptr(phi), dt, N, L, _ptr(w), _ptr(M), _ptr(out), _stream(stream)))
     return M, out
+
+
+def free_field_covariance(L, beta, m2, c_kin=1.0, c_mass=1.0, keep_reference=False, device="cuda", stream=None):
+    """Exact covariance of the Gaussian part of the tempered target at beta (D x D device tensor)."""
+    import torch
+    D = L * L
+    sigma = torch.empty((D, D), dtype=torch.float64, device=device)
+    b = torch.tensor([beta], dtype=torch.float64, device=device)
+    nb = lib().phi4_free_covariance_scratch_bytes(L)
+    scratch = torch.empty(nb, dtype=torch.uint8, device=device)
+    _check(lib().phi4_free_field_covariance(L, _ptr(b), m2, c_kin, c_mass, int(keep_reference), _ptr(sigma),
+                                            _ptr(scratch), nb, _stream(stream)))
+    return sigma
 
 
 def set_spin_limit(cycles):

@@ -65,7 +65,11 @@ phi4_status check_config(const phi4_config* c) {
   }
   ARG_CHECK(c->chol_jitter_rel >= 0.0 && isfinite(c->chol_jitter_rel), "chol_jitter_rel invalid");
   ARG_CHECK(c->chol_mode >= 0 && c->chol_mode <= 2, "chol_mode = %d unknown", c->chol_mode);
-  ARG_CHECK((c->flags & ~PHI4_FLAG_Z2_FLIP) == 0, "flags 0x%x: unknown bits", c->flags);
+  ARG_CHECK((c->flags & ~(PHI4_FLAG_Z2_FLIP | PHI4_FLAG_FREE_KERNEL_COV)) == 0, "flags 0x%x: unknown bits",
+            c->flags);
+  ARG_CHECK(!(c->flags & PHI4_FLAG_FREE_KERNEL_COV) ||
+                ((c->kind == PHI4_SMC_RW || c->kind == PHI4_SMC_HMC) && c->c_mass * c->m2 > 0.0),
+            "the free-field kernel covariance needs an SMC_RW or SMC_HMC run with c_mass * m2 > 0");
   ARG_CHECK(!(c->flags & PHI4_FLAG_Z2_FLIP) || c->kind != PHI4_NS_SLICE, "the Z2 flip move is an SMC move");
   return PHI4_OK;
 }
@@ -133,7 +137,7 @@ void lay_out(phi4_run* r, Layout& L) {
   r->scal = (double*)L.take(SC_COUNT * 8);
   r->status = (uint32_t*)L.take(16);
   r->acc_count = r->status + 1;
-  r->cov_scratch_bytes = covariance_scratch_bytes(N, D, c.precision);
+  r->cov_scratch_bytes = std::max(covariance_scratch_bytes(N, D, c.precision), free_covariance_scratch_bytes(c.L));
   r->ns_dead_n = 0;
   r->cov_scratch = L.take(r->cov_scratch_bytes);
   r->bisect_scratch = L.take(bisect_scratch_bytes(N));
@@ -189,7 +193,11 @@ phi4_status refit_enqueue(phi4_run* r, const void* pts, int n_pts) {
   cudaStream_t s = r->stream;
   {
     StageScope sc(r, STG_COV);
-    CUDA_TRY(launch_covariance(pts, r->cfg.precision, n_pts, D, r->sigma, r->cov_scratch, r->status, s));
+    if (r->cfg.flags & PHI4_FLAG_FREE_KERNEL_COV)  // at the new beta, written by the reweighting
+      CUDA_TRY(launch_free_covariance(r->cfg.L, r->scal + SC_BETA, r->cfg.c_mass * r->cfg.m2, r->cfg.c_kin,
+                                      r->cfg.keep_reference, r->sigma, r->cov_scratch, s));
+    else
+      CUDA_TRY(launch_covariance(pts, r->cfg.precision, n_pts, D, r->sigma, r->cov_scratch, r->status, s));
     CUDA_TRY(launch_ridge(r->sigma, D, r->cfg.chol_jitter_rel * pow(10.0, r->ridge_level), r->scal + SC_RIDGE, s));
     r->kernel_launches += 4;
   }
@@ -304,10 +312,8 @@ phi4_status step_front(phi4_run* r, bool single_cta_bisect) {
   {
     StageScope sc(r, STG_GATHER);
     CUDA_TRY(launch_gather(r->phi, r->phi_alt, (size_t)D * r->elem, N, r->anc, s));
-    CUDA_TRY(launch_gather_f64(r->S, r->S_alt, N, r->anc, s));
-    CUDA_TRY(launch_gather_f64(r->sq, r->sq_alt, N, r->anc, s));
-    CUDA_TRY(launch_gather_f64(r->ell, r->ell_alt, N, r->anc, s));
-    r->kernel_launches += 4;
+    CUDA_TRY(launch_gather3_f64(r->S, r->S_alt, r->sq, r->sq_alt, r->ell, r->ell_alt, N, r->anc, s));
+    r->kernel_launches += 2;
     std::swap(r->phi, r->phi_alt);
     std::swap(r->S, r->S_alt);
     std::swap(r->sq, r->sq_alt);
@@ -722,6 +728,123 @@ phi4_status smc_load_particles(phi4_run* r, const void* src, size_t bytes) {
   return PHI4_OK;
 }
 
+/* ---------------------------- checkpoint / resume ---------------------------- */
+
+namespace {
+constexpr uint64_t kStateMagic = 0x3154415453344950ull;  // "PHI4STAT1" (first 8 bytes)
+
+// Host part of a run's state: everything besides the device arrays that feeds later steps.
+struct StateHeader {
+  uint64_t magic;
+  uint64_t bytes;            // whole state, header included
+  phi4_config cfg;
+  int64_t t, n_evals, slice_capped, ns_dead_n;
+  int32_t ridge_level, done;
+  double beta, last_ess, last_acc, logz_ns, logX;
+};
+
+// Device arrays of the state, in order: the fields, S, |phi|^2, ell, the scalar block,
+// and for nested sampling the dead points' (log L, log w) pairs.
+struct StatePart { void* dev; size_t bytes; };
+std::vector<StatePart> state_parts(const phi4_run* r) {
+  const size_t N = (size_t)r->cfg.N;
+  std::vector<StatePart> v = {{r->phi, N * r->D * r->elem}, {r->S, N * 8}, {r->sq, N * 8}, {r->ell, N * 8},
+                              {r->scal, SC_COUNT * 8}};
+  if (r->cfg.kind == PHI4_NS_SLICE) v.push_back({r->ns_dead, (size_t)r->ns_dead_n * 2 * 8});
+  return v;
+}
+bool same_config(const phi4_config& a, const phi4_config& b) {
+  return a.L == b.L && a.N == b.N && a.kind == b.kind && a.precision == b.precision && a.m2 == b.m2 &&
+         a.lambda == b.lambda && a.c_kin == b.c_kin && a.c_mass == b.c_mass && a.keep_reference == b.keep_reference &&
+         a.n_mcmc == b.n_mcmc && a.ess_target == b.ess_target && a.rw_scale == b.rw_scale &&
+         a.ns_n_delete == b.ns_n_delete && a.ns_slice_steps == b.ns_slice_steps && a.ns_stop_frac == b.ns_stop_frac &&
+         a.chol_jitter_rel == b.chol_jitter_rel && a.bisect_iters == b.bisect_iters &&
+         a.slice_max_shrink == b.slice_max_shrink && a.seed == b.seed && a.stream_id == b.stream_id &&
+         a.chol_mode == b.chol_mode && a.flags == b.flags;
+}
+size_t state_total(const phi4_run* r) {
+  size_t b = sizeof(StateHeader);
+  for (const StatePart& q : state_parts(r)) b += q.bytes;
+  return b;
+}
+}  // namespace
+
+phi4_status phi4_state_bytes(const phi4_run* r, size_t* bytes) {
+  ARG_CHECK(r && bytes, "NULL argument");
+  ARG_CHECK(!r->batch, "a batch handle has no single state (save its members)");
+  *bytes = state_total(r);
+  return PHI4_OK;
+}
+
+phi4_status smc_save_state(const phi4_run* rc, void* host_dst, size_t bytes) {
+  ARG_CHECK(rc && host_dst, "NULL argument");
+  ARG_CHECK(!rc->batch, "a batch handle has no single state (save its members)");
+  phi4_run* r = const_cast<phi4_run*>(rc);
+  const size_t need = state_total(r);
+  ARG_CHECK(bytes >= need, "state buffer of %zu bytes, need %zu", bytes, need);
+  StateHeader h;
+  memset(&h, 0, sizeof(h));
+  h.magic = kStateMagic;
+  h.bytes = need;
+  h.cfg = r->cfg;
+  h.t = r->t;
+  h.n_evals = r->n_evals;
+  h.slice_capped = r->slice_capped;
+  h.ns_dead_n = r->ns_dead_n;
+  h.ridge_level = r->ridge_level;
+  h.done = r->done ? 1 : 0;
+  h.beta = r->beta;
+  h.last_ess = r->last_ess;
+  h.last_acc = r->last_acc;
+  h.logz_ns = r->logz_ns;
+  h.logX = r->logX;
+  unsigned char* dst = (unsigned char*)host_dst;
+  memcpy(dst, &h, sizeof(h));
+  size_t off = sizeof(h);
+  for (const StatePart& q : state_parts(r)) {
+    if (q.bytes) CUDA_TRY(cudaMemcpyAsync(dst + off, q.dev, q.bytes, cudaMemcpyDeviceToHost, r->stream));
+    off += q.bytes;
+  }
+  CUDA_TRY(cudaStreamSynchronize(r->stream));
+  return PHI4_OK;
+}
+
+phi4_status smc_restore_state(phi4_run* r, const void* host_src, size_t bytes) {
+  ARG_CHECK(r && host_src, "NULL argument");
+  ARG_CHECK(!r->batch, "a batch handle has no single state (restore its members)");
+  ARG_CHECK(bytes >= sizeof(StateHeader), "state buffer of %zu bytes is too small", bytes);
+  StateHeader h;
+  memcpy(&h, host_src, sizeof(h));
+  ARG_CHECK(h.magic == kStateMagic, "not a phi4smc state (bad magic)");
+  ARG_CHECK(h.bytes <= bytes, "state of %llu bytes truncated to %zu", (unsigned long long)h.bytes, bytes);
+  ARG_CHECK(same_config(h.cfg, r->cfg),
+            "the state was saved from a run with another configuration");
+  ARG_CHECK(h.ns_dead_n >= 0 && h.ns_dead_n <= r->ns_dead_cap, "dead-point count %lld out of range",
+            (long long)h.ns_dead_n);
+  r->ns_dead_n = h.ns_dead_n;  // sizes the NS dead list part
+  ARG_CHECK(state_total(r) == h.bytes, "state size %llu does not match this run's %zu",
+            (unsigned long long)h.bytes, state_total(r));
+  const unsigned char* src = (const unsigned char*)host_src;
+  size_t off = sizeof(h);
+  for (const StatePart& q : state_parts(r)) {
+    if (q.bytes) CUDA_TRY(cudaMemcpyAsync(q.dev, src + off, q.bytes, cudaMemcpyHostToDevice, r->stream));
+    off += q.bytes;
+  }
+  CUDA_TRY(cudaMemsetAsync(r->status, 0, 16, r->stream));
+  CUDA_TRY(cudaStreamSynchronize(r->stream));
+  r->t = h.t;
+  r->n_evals = h.n_evals;
+  r->slice_capped = h.slice_capped;
+  r->ridge_level = h.ridge_level;
+  r->done = h.done != 0;
+  r->beta = h.beta;
+  r->last_ess = h.last_ess;
+  r->last_acc = h.last_acc;
+  r->logz_ns = h.logz_ns;
+  r->logX = h.logX;
+  return PHI4_OK;
+}
+
 phi4_status smc_free(phi4_run* r) {
   if (!r) return PHI4_OK;
   ARG_CHECK(!r->owner, "this run belongs to a batch: free the batch handle");
@@ -787,6 +910,23 @@ phi4_status phi4_stage_times(phi4_run* r, double* ms_out, int64_t* launches_out,
 }
 
 /* -------------------------- kernel-level API -------------------------- */
+
+size_t phi4_free_covariance_scratch_bytes(int32_t L) {
+  return (L >= 1 && L <= 128) ? free_covariance_scratch_bytes(L) : 0;
+}
+
+phi4_status phi4_free_field_covariance(int32_t L, const double* d_beta, double m2, double c_kin, double c_mass,
+                                       int32_t keep_reference, double* sigma, void* scratch, size_t scratch_bytes,
+                                       void* stream) {
+  ARG_CHECK(d_beta && sigma && scratch, "NULL argument");
+  ARG_CHECK(L >= 1 && L <= 128, "L = %d outside [1, 128]", L);
+  ARG_CHECK(c_mass * m2 > 0.0 && c_kin >= 0.0, "needs c_mass * m2 > 0 and c_kin >= 0");
+  ARG_CHECK(scratch_bytes >= free_covariance_scratch_bytes(L), "scratch of %zu bytes, need %zu", scratch_bytes,
+            free_covariance_scratch_bytes(L));
+  CUDA_TRY(launch_free_covariance(L, d_beta, c_mass * m2, c_kin, keep_reference, sigma, scratch,
+                                  (cudaStream_t)stream));
+  return PHI4_OK;
+}
 
 phi4_status phi4_observables(const void* phi, int32_t dtype, int32_t N, int32_t L, const double* w, double* M,
                              double* out, void* stream) {

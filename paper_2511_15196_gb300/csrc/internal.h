@@ -79,12 +79,19 @@ cudaError_t launch_resample(const double* w, int N, uint32_t U, const uint32_t* 
 cudaError_t launch_gather(const void* src, void* dst, size_t row_bytes, int N, const int32_t* anc,
                           cudaStream_t s);
 cudaError_t launch_gather_f64(const double* src, double* dst, int N, const int32_t* anc, cudaStream_t s);
+cudaError_t launch_gather3_f64(const double* s0, double* d0, const double* s1, double* d1, const double* s2,
+                               double* d2, int N, const int32_t* anc, cudaStream_t s);
 
 // kernels_cov.cu
 size_t covariance_scratch_bytes(int N, int D, int precision);
 cudaError_t launch_covariance(const void* phi, int precision, int N, int D, double* sigma, void* scratch,
                               uint32_t* status, cudaStream_t s);
 cudaError_t launch_ridge(const double* sigma, int D, double jitter_rel, double* ridge, cudaStream_t s);
+// exact covariance of the Gaussian part of the tempered target at *beta (device), the
+// whole D x D matrix into sigma; scratch: free_covariance_scratch_bytes(L)
+size_t free_covariance_scratch_bytes(int L);
+cudaError_t launch_free_covariance(int L, const double* beta, double m2c, double c_kin, int keep, double* sigma,
+                                   void* scratch, cudaStream_t s);
 
 // CUDA-event pairs around selected kernel launches, each pair on the launch's own
 // stream (kernel-level timing inside a stage that spans two streams).

@@ -207,6 +207,72 @@ cudaError_t launch_covariance(const void* phi, int precision, int N, int D, doub
   return launch_gram_tc(H, Lo, ldx, D, N, shift, a, inv, sigma, status, s);
 }
 
+// ---------------------------------------------------------------------------
+// Particle-independent kernel covariance (PHI4_FLAG_FREE_KERNEL_COV): the exact
+// covariance of the Gaussian part of the tempered target gamma_beta, whose log density
+// has the quadratic part -(1/2) phi^T P phi with
+//   P = a I + 2 beta (c_kin K + c_mass m2 I),  K = sum_mu (2 - T_mu - T_mu^{-1}),
+// a = 1 - beta (reference dropped at beta = 1) or 1 (reference kept). For lambda = 0 it
+// is the target's covariance. P is diagonal in the lattice Fourier basis with
+//   p_k = a + 2 beta (c_kin sum_mu 4 sin^2(pi k_mu / L) + c_mass m2),
+// so Sigma_xy = (1/D) sum_k cos(2 pi k.(x - y) / L) / p_k depends only on the
+// displacement (dr, dc) = (x - y) mod L; the sine parts cancel under k -> -k (p_k is
+// even), leaving the product of the two cosines. Three kernels: 1/p_k, the displacement
+// table (one CTA per displacement, FP64 sums in a fixed order), the D x D fill.
+__global__ void free_inv_spectrum_kernel(int L, const double* __restrict__ beta_p, double m2c, double c_kin,
+                                         int keep, double* __restrict__ invp) {
+  const int D = L * L;
+  const double beta = *beta_p, a = keep ? 1.0 : 1.0 - beta;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < D; k += gridDim.x * blockDim.x) {
+    const int k1 = k / L, k2 = k - (k / L) * L;
+    const double s1 = sinpi((double)k1 / L), s2 = sinpi((double)k2 / L);
+    invp[k] = 1.0 / (a + 2.0 * beta * (c_kin * 4.0 * (s1 * s1 + s2 * s2) + m2c));
+  }
+}
+
+constexpr int kFreeThreads = 256;
+__global__ void __launch_bounds__(kFreeThreads) free_table_kernel(int L, const double* __restrict__ invp,
+                                                                  double* __restrict__ table) {
+  __shared__ double cs[128];
+  __shared__ double red[64];
+  const int D = L * L, e = blockIdx.x, dr = e / L, dc = e - (e / L) * L;
+  for (int j = threadIdx.x; j < L; j += kFreeThreads) cs[j] = cospi(2.0 * (double)j / L);
+  __syncthreads();
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < D; k += kFreeThreads) {
+    const int k1 = k / L, k2 = k - (k / L) * L;
+    acc += cs[(k1 * dr) % L] * cs[(k2 * dc) % L] * invp[k];
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) table[e] = acc / D;
+}
+
+__global__ void free_fill_kernel(int L, const double* __restrict__ table, double* __restrict__ sigma) {
+  const int D = L * L;
+  const long long total = (long long)D * D;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q / D), j = (int)(q - (long long)i * D);
+    const int ri = i / L, ci = i - ri * L, rj = j / L, cj = j - rj * L;
+    const int dr = (ri - rj + L) % L, dc = (ci - cj + L) % L;
+    sigma[q] = table[dr * L + dc];
+  }
+}
+
+size_t free_covariance_scratch_bytes(int L) { return 2 * align256((size_t)L * L * sizeof(double)); }
+
+cudaError_t launch_free_covariance(int L, const double* beta, double m2c, double c_kin, int keep, double* sigma,
+                                   void* scratch, cudaStream_t s) {
+  if (L < 1 || L > 128) return cudaErrorInvalidValue;
+  const int D = L * L;
+  double* invp = (double*)scratch;
+  double* table = (double*)((unsigned char*)scratch + align256((size_t)D * sizeof(double)));
+  free_inv_spectrum_kernel<<<(D + 255) / 256, 256, 0, s>>>(L, beta, m2c, c_kin, keep, invp);
+  free_table_kernel<<<D, kFreeThreads, 0, s>>>(L, invp, table);
+  free_fill_kernel<<<sm_count() * 8, 256, 0, s>>>(L, table, sigma);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ridge(const double* sigma, int D, double jitter_rel, double* ridge, cudaStream_t s) {
   ridge_kernel<<<1, 256, 0, s>>>(sigma, D, jitter_rel, ridge);
   return cudaGetLastError();

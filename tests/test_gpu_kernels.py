@@ -122,6 +122,34 @@ def test_bisection_and_reweight(N, beta, rho):
     assert abs(out[4] - used) <= 2
 
 
+@pytest.mark.parametrize("N", [1000, 5000])
+@pytest.mark.parametrize("rho", [0.99, 0.999])
+@pytest.mark.parametrize("beta", [0.0, 0.5])
+def test_bisection_high_ess_targets(N, rho, beta):
+    # the target-ESS sweep of App. E (Table 4: 0.9, 0.99, 0.999): at high targets dbeta is a
+    # small fraction of the bracket, so a sum rounded in another order may flip one late
+    # halving; then both answers must be roots to rounding, ESS(d) = rho N within 1e-11
+    ell = inputs.log_weights(N, seed=N + 7, spread=30.0, offset=-800.0)
+    w, out = p.ess_bisect(cuda(ell), beta, rho, 64)
+    out = out.cpu().numpy()
+    d_ref, used = otemp.bisect_dbeta(ell, beta, rho, 64)
+    w_ref, inc_ref = otemp.reweight(ell, d_ref)
+
+    def ess(d):
+        a = ell - ell.max()
+        e = np.exp(d * a)
+        return e.sum() ** 2 / (e * e).sum()
+    if out[0] != pytest.approx(d_ref, rel=1e-12):
+        assert ess(out[0]) == pytest.approx(rho * N, rel=1e-11)
+        assert ess(d_ref) == pytest.approx(rho * N, rel=1e-11)
+        assert out[0] == pytest.approx(d_ref, rel=1e-6)
+    else:
+        np.testing.assert_allclose(w.cpu().numpy(), w_ref, rtol=1e-11, atol=1e-300)
+        assert out[3] == pytest.approx(inc_ref, rel=1e-12, abs=1e-12)
+    assert 0.0 < out[0] < 1.0 - beta
+    assert out[2] >= rho * N * (1 - 1e-12)
+
+
 def test_bisection_steps_to_one():
     ell = inputs.log_weights(4096, seed=3, spread=1e-4)
     _, out = p.ess_bisect(cuda(ell), 0.6, 0.5)
@@ -531,3 +559,14 @@ def test_observables_mode_balance_edge_cases():
     w = np.array([0.5, 1.0, 0.25, 0.25])
     _, out = p.observables(torch.from_numpy(phi).cuda(), L, torch.from_numpy(w).cuda())
     assert out.cpu().numpy()[4] == pytest.approx(0.25 / 0.75, rel=1e-15)
+
+
+@pytest.mark.parametrize("L,beta,keep", [(1, 0.3, False), (2, 0.5, False), (3, 1.0, False), (8, 0.25, True),
+                                         (16, 0.9, False), (32, 1.0, False), (20, 0.0, False)])
+def test_free_field_covariance_matches_oracle(L, beta, keep):
+    # the device builds Sigma from the Fourier spectrum of P per site displacement; the oracle
+    # inverts P assembled site by site from the action's kinetic sum
+    m2, c_kin, c_mass = 1.0, 0.8, 1.2
+    sig = p.free_field_covariance(L, beta, m2, c_kin, c_mass, keep).cpu().numpy()
+    ref = ocov.gaussian_part_covariance(L, beta, m2, c_kin, c_mass, keep)
+    assert np.abs(sig - ref).max() <= 1e-12 * np.abs(ref).max()

@@ -269,25 +269,89 @@ def test_broken_phase_fp64_32_seeds():
     assert np.abs(g[:, 0] - o[:, 0]).max() < 1e-6
 
 
+_ORACLE_RUNS = {}
+
+
+def _oracle_runs_cached(n_seeds, **kw):
+    key = (n_seeds, tuple(sorted(kw.items())))
+    if key not in _ORACLE_RUNS:
+        _ORACLE_RUNS[key] = _oracle_runs(n_seeds, **kw)
+    return _ORACLE_RUNS[key]
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("precision", [p.FP32, p.MIXED_BF16], ids=["fp32", "bf16"])
-def test_broken_phase_single_forms_16_seeds(precision):
-    g = _gpu_runs(16, precision=precision)
-    o = _oracle_runs(16, normal_bits=24)
+def test_broken_phase_single_forms_32_seeds(precision):
+    # the float and mixed forms against the oracle with float-precision normals (the same
+    # 32 oracle runs serve both forms)
+    g = _gpu_runs(32, precision=precision)
+    o = _oracle_runs_cached(32, normal_bits=24)
     _within_3se(g, o)
 
 
+def _logz_plus_half_var(lz):
+    # log Zhat is biased low by about Var/2: mean + var/2 estimates log Z; its error combines
+    # the mean's standard error and the spread of the variance estimate
+    lz = np.asarray(lz, dtype=np.float64)
+    n, var = len(lz), lz.var(ddof=1)
+    return lz.mean() + 0.5 * var, math.sqrt(var / n + (0.5 * var * math.sqrt(2.0 / (n - 1))) ** 2)
+
+
+@pytest.mark.parametrize("L,N,keep", [(8, 512, False), (16, 1024, False), (6, 300, True)])
+def test_free_kernel_covariance_fp64_steps_match_oracle(L, N, keep):
+    # PHI4_FLAG_FREE_KERNEL_COV: the proposal's factor comes from the exact covariance of the
+    # tempered Gaussian part (built on the device from the Fourier spectrum; the oracle
+    # inverts the precision matrix assembled site by site) and the run follows the oracle
+    run = p.Run(gpu_cfg(L=L, N=N, n_mcmc=3, seed=6, m2=1.0, lam=0.0, keep_reference=keep,
+                        flags=p.FLAG_FREE_KERNEL_COV))
+    ref = SMC(oracle_cfg(L=L, N=N, n_mcmc=3, seed=6, m2=1.0, lam=0.0, keep_reference=keep,
+                         kernel_cov="gaussian_part"))
+    for _ in range(3):
+        beta = run.temper_step()
+        rec = ref.temper_step()
+        assert beta == pytest.approx(rec["beta"], rel=1e-10, abs=1e-13)
+        assert np.abs(run.particles().cpu().numpy() - ref.phi).max() < 1e-8
+        assert run.log_evidence()[0] == pytest.approx(rec["logz"], rel=1e-10, abs=1e-9)
+    run.close()
+
+
 @pytest.mark.slow
-def test_free_field_precision_forms_bf16():
-    # free field lambda = 0, m2 = 1, L = 32 (D = 1024), N = 4096: the three arithmetic forms
-    # run on the same random streams and agree within their seed-to-seed spread
+@pytest.mark.parametrize("precision", [p.FP64, p.FP32, p.MIXED_BF16], ids=["fp64", "fp32", "bf16"])
+def test_free_field_closed_form_each_form_with_the_free_kernel_covariance(precision):
+    # the precision check against the closed form, in a setting where the sampler mixes:
+    # the 8 x 8 free field (m2 = 1), N = 1024, ESS 0.9 N, 20 sweeps, the exact Gaussian-part
+    # kernel covariance, 32 seeds; each arithmetic form's mean log Zhat + Var/2 lands on the
+    # closed form -11.6228852573 within four of its errors
+    lz = _gpu_runs(32, L=8, N=1024, m2=1.0, lam=0.0, ess_target=0.9, n_mcmc=20, precision=precision,
+                   flags=p.FLAG_FREE_KERNEL_COV)[:, 0]
+    est, err = _logz_plus_half_var(lz)
+    exact = cf.free_field_logz(8, 1.0)
+    print("free field L=8, %s: log Zhat mean %.4f sd %.4f; mean + var/2 - exact = %+.4f (err %.4f)"
+          % (precision, lz.mean(), lz.std(ddof=1), est - exact, err))
+    assert abs(est - exact) < 4.0 * err + 0.01
+
+
+@pytest.mark.slow
+def test_free_field_precision_forms_32_seeds():
+    # the precision-check workload as configured: free field (lambda = 0, m2 = 1), L = 32
+    # (D = 1024), N = 4096, ESS 0.5 N, 10 sweeps, the population's covariance. The three
+    # arithmetic forms run on the same random streams; the float and bf16 forms' log Z, <|M|>
+    # and chi agree with the FP64 form (step-matched to the oracle elsewhere) within three
+    # standard errors over 32 seeds. Each form's log Zhat - log Z (closed form
+    # -185.9853908122) is printed: with this sampler and 10 sweeps it is hundreds of nats
+    # above the closed form for every form alike, the bias of the population-estimated
+    # kernel covariance, not an arithmetic error (the free-kernel-covariance test above is
+    # the closed-form comparison where the sampler mixes).
     res = {}
+    exact = cf.free_field_logz(32, 1.0)
     for prec in (p.FP64, p.FP32, p.MIXED_BF16):
-        res[prec] = _gpu_runs(4, L=32, N=4096, m2=1.0, lam=0.0, precision=prec)
+        res[prec] = _gpu_runs(32, L=32, N=4096, m2=1.0, lam=0.0, precision=prec)
+        m, se = _stats(res[prec][:, 0])
+        print("L=32 free field, precision %d: log Zhat - log Z = %+.3f (SE %.3f); minus the FP64 form's: %+.3f"
+              % (prec, m - exact, se, m - res[p.FP64][:, 0].mean()))
+        assert np.isfinite(res[prec]).all()
     for prec in (p.FP32, p.MIXED_BF16):
         _within_3se(res[prec], res[p.FP64])
-    exact = cf.free_field_logz(32, 1.0)
-    assert np.isfinite(res[p.MIXED_BF16][:, 0]).all() and exact == pytest.approx(-185.9853908122, abs=1e-9)
 
 
 @pytest.mark.parametrize("L,N", [(16, 2048), (20, 300), (10, 2048)],
@@ -311,6 +375,24 @@ def test_mixed_runs_are_deterministic(L, N):
         r.close()
 
 
+@pytest.mark.parametrize("rho", [0.9, 0.99])
+def test_paper_mode_fp64_steps_match_oracle(rho):
+    # the paper's own setting step by step: Eq. (1) with factors 1/2 (c_kin = c_mass = 1/2),
+    # m^2 = -4, lambda = 1, the reference kept at beta = 1 (target exp(-U_0 - S)), L = 10,
+    # target ESS 0.9 and 0.99 (App. E), FP64 on the same streams as the oracle
+    kw = dict(L=10, N=1000, m2=-4.0, lam=1.0, c_kin=0.5, c_mass=0.5, keep_reference=True, n_mcmc=5, seed=12)
+    run = p.Run(gpu_cfg(ess_target=rho, **kw))
+    ref = SMC(oracle_cfg(rho=rho, **kw))
+    for _ in range(4):
+        beta = run.temper_step()
+        rec = ref.temper_step()
+        assert beta == pytest.approx(rec["beta"], rel=1e-10, abs=1e-13)
+        assert run.log_evidence()[0] == pytest.approx(rec["logz"], rel=1e-10, abs=1e-9)
+        assert np.abs(run.particles().cpu().numpy() - ref.phi).max() < 1e-8
+        assert run.observables()["ess"] == pytest.approx(rec["ess"], rel=1e-10)
+    run.close()
+
+
 def test_paper_mode_logz_L10():
     # the paper's setting (Sec. 3, App. A): L = 10, Eq. (1) with factors 1/2, m^2 = -4,
     # lambda = 1, target exp(-U_0 - S), N = 5000, n_MCMC = 3 V, ESS target 0.9. The
@@ -324,3 +406,31 @@ def test_paper_mode_logz_L10():
     assert -37.2 < row["logz_mean"] < -36.1, row
     assert row["logz_sd"] < 0.5, row
     assert 0.5 < row["mode_balance"] < 2.0, row
+
+
+@pytest.mark.parametrize("precision,kind", [(p.FP64, p.SMC_RW), (p.MIXED_BF16, p.SMC_RW), (p.FP32, p.SMC_HMC)],
+                         ids=["fp64_rw", "bf16_rw", "fp32_hmc"])
+def test_checkpoint_resume_is_bit_identical(precision, kind):
+    # save after two temperatures, continue the original for two more; a fresh run of the
+    # same configuration restored from the saved state follows it bit for bit
+    cfg = gpu_cfg(L=16, N=512, n_mcmc=3, seed=21, precision=precision, kind=kind)
+    a = p.Run(cfg)
+    for _ in range(2):
+        a.temper_step()
+    state = a.save_state()
+    ba = [a.temper_step() for _ in range(2)]
+    b = p.Run(cfg)
+    b.restore_state(state)
+    bb = [b.temper_step() for _ in range(2)]
+    assert ba == bb
+    assert torch.equal(a.particles(), b.particles())
+    assert a.log_evidence()[0] == b.log_evidence()[0]
+    oa, ob = a.observables(), b.observables()
+    assert oa["n_steps"] == ob["n_steps"] == 4 and oa["acc_rate"] == ob["acc_rate"]
+    # another configuration is refused
+    c = p.Run(gpu_cfg(L=16, N=512, n_mcmc=3, seed=22, precision=precision, kind=kind))
+    with pytest.raises(p.Phi4Error) as e:
+        c.restore_state(state)
+    assert e.value.status == p.PHI4_ERR_ARG
+    for r in (a, b, c):
+        r.close()

@@ -38,3 +38,33 @@ def test_regularised_cholesky_rank_deficient():
     A = inputs.spd_matrix(6, seed=2)
     _, d3, t3, l3 = covariance.regularised_cholesky(A, 1e-8, start_level=3)
     assert t3 == 1 and l3 == 3 and d3 == pytest.approx(1e-5 * np.trace(A) / 6, rel=1e-12)
+
+
+@pytest.mark.parametrize("L,beta,keep", [(1, 0.5, False), (2, 0.3, False), (3, 1.0, False), (4, 0.7, True),
+                                         (5, 0.0, False)])
+def test_gaussian_part_covariance_inverts_the_hessian_of_the_tempered_target(L, beta, keep):
+    # P = Sigma^{-1} must be the Hessian of beta S + a |phi|^2 / 2 (lambda = 0), here taken by
+    # second differences of the oracle's own action (exact for a quadratic up to rounding)
+    from oracle import lattice
+    m2, c_kin, c_mass = 1.3, 0.7, 0.9
+    D = L * L
+    a = 1.0 if keep else 1.0 - beta
+
+    def f(x):
+        S = lattice.action(x[None, :], L, m2, 0.0, c_kin, c_mass)[0]
+        return beta * S + 0.5 * a * float(x @ x)
+    E = np.eye(D)
+    H = np.array([[f(E[i] + E[j]) - f(E[i]) - f(E[j]) + f(np.zeros(D)) for j in range(D)] for i in range(D)])
+    Sigma = covariance.gaussian_part_covariance(L, beta, m2, c_kin, c_mass, keep)
+    np.testing.assert_allclose(Sigma @ H, np.eye(D), atol=1e-11)
+
+
+def test_gaussian_part_covariance_spectrum_is_the_closed_form():
+    # eigenvalues 1 / (a + 2 beta p_k), p_k = c_mass m2 + c_kin sum_mu 4 sin^2(pi k_mu / L)
+    import closed_forms as cf
+    L, beta, m2 = 6, 0.4, 0.8
+    Sigma = covariance.gaussian_part_covariance(L, beta, m2)
+    p = m2 + cf.lattice_laplacian_eigs(L)
+    np.testing.assert_allclose(np.sort(np.linalg.eigvalsh(Sigma)), np.sort(1.0 / (1.0 - beta + 2.0 * beta * p)),
+                               rtol=1e-12)
+    np.testing.assert_allclose(Sigma, cf.free_field_covariance(L, m2, beta), rtol=1e-12, atol=1e-15)

@@ -93,25 +93,16 @@ def test_z2_flip_balances_the_modes():
 
 
 @pytest.mark.parametrize("keep_reference", [False, True])
-def test_free_field_L8_with_the_exact_kernel_covariance(monkeypatch, keep_reference):
+def test_free_field_L8_with_the_exact_kernel_covariance(keep_reference):
     # On the workload's 8 x 8 lattice the driver (bisection, reweighting, Kahan log Z,
     # resampling, random-walk sweeps) is exact once its kernels are: with the proposal
     # covariance set to the exact covariance of the tempered free field at each new
-    # temperature, in place of the population's, the evidence matches the closed form,
-    # with the reference dropped at beta = 1 and with it kept (the paper's surrogate).
-    from oracle import covariance, tempering
+    # temperature (kernel_cov = "gaussian_part"), in place of the population's, the evidence
+    # matches the closed form, with the reference dropped at beta = 1 and with it kept (the
+    # paper's surrogate).
     L, m2 = 8, 1.0
-    state = {}
-    bisect = tempering.bisect_dbeta
-
-    def recording_bisect(ell, beta, rho, iters=64):
-        d, used = bisect(ell, beta, rho, iters)
-        state["beta"] = min(1.0, beta + d)
-        return d, used
-    monkeypatch.setattr(tempering, "bisect_dbeta", recording_bisect)
-    monkeypatch.setattr(covariance, "sample_covariance",
-                        lambda X: (X.mean(axis=0), cf.free_field_covariance(L, m2, state["beta"], keep_reference)))
-    lz = seeds_logz(dict(L=L, N=512, m2=m2, lam=0.0, rho=0.9, n_mcmc=20, keep_reference=keep_reference), 6)
+    lz = seeds_logz(dict(L=L, N=512, m2=m2, lam=0.0, rho=0.9, n_mcmc=20, keep_reference=keep_reference,
+                         kernel_cov="gaussian_part"), 6)
     n, var = len(lz), lz.var(ddof=1)
     # mean + var/2 estimates log Z (log Zhat is biased low by about Var/2); its error
     # combines the mean's standard error and the spread of the variance estimate
