@@ -1,64 +1,17 @@
-// Systematic resampling in exact fixed point and the particle gather.
-//   q_i = floor(ldexp(w_i / max w, 46)),  C = inclusive prefix sum of q (uint64),
-//   p_i = floor((i 2^32 + U) Q / (N 2^32)),  anc_i = min{ j : C_j > p_i }.
-// One 1024-thread CTA: per-thread serial scans of contiguous chunks, a warp-
-// shuffle scan of the chunk totals, then a binary search per position. Integer
-// arithmetic only after the (correctly rounded) division, so any implementation
-// of this definition returns the same ancestors.
+// Systematic resampling in exact fixed point (resample.cuh) and the particle gather.
 #include <math.h>
 #include <algorithm>
 #include "internal.h"
-#include "common.cuh"
+#include "resample.cuh"
 
 namespace phi4 {
-
-namespace {
-constexpr int kResampleThreads = 1024;
-}
 
 __global__ void __launch_bounds__(kResampleThreads) resample_kernel(const double* __restrict__ w, int N,
                                                                     uint32_t U_host,
                                                                     const uint32_t* __restrict__ U_dev,
                                                                     int32_t* __restrict__ anc,
                                                                     unsigned long long* __restrict__ C) {
-  __shared__ double red[64];
-  __shared__ unsigned long long tot[32];
-  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-  double m = 0.0;
-  for (int i = t; i < N; i += kResampleThreads) m = fmax(m, w[i]);
-  m = block_max(m, red);
-  const int chunk = (N + kResampleThreads - 1) / kResampleThreads;
-  const int i0 = min(N, t * chunk), i1 = min(N, i0 + chunk);
-  unsigned long long run = 0;
-  for (int i = i0; i < i1; ++i) {
-    const unsigned long long q = (unsigned long long)floor(ldexp(w[i] / m, 46));
-    run += q;
-    C[i] = run;
-  }
-  const unsigned long long incl = warp_incl_scan(run, lane);
-  if (lane == 31) tot[wid] = incl;
-  __syncthreads();
-  if (wid == 0) {
-    const unsigned long long v = tot[lane];
-    tot[lane] = warp_incl_scan(v, lane);
-  }
-  __syncthreads();
-  const unsigned long long offset = (incl - run) + (wid > 0 ? tot[wid - 1] : 0ull);
-  for (int i = i0; i < i1; ++i) C[i] += offset;
-  const unsigned long long Q = tot[31];
-  __syncthreads();
-  const unsigned long long U = U_dev ? (unsigned long long)*U_dev : (unsigned long long)U_host;
-  for (int i = t; i < N; i += kResampleThreads) {
-    const unsigned long long T = ((unsigned long long)i << 32) | U;
-    const unsigned __int128 prod = (unsigned __int128)T * Q;
-    const unsigned long long p = (unsigned long long)((prod >> 32) / (unsigned)N);
-    int lo = 0, hi = N - 1;  // first j with C[j] > p (exists: p < Q = C[N-1])
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (C[mid] > p) hi = mid; else lo = mid + 1;
-    }
-    anc[i] = lo;
-  }
+  resample_body(w, N, U_dev ? *U_dev : U_host, anc, C);
 }
 
 // Row gather dst[r] = src[anc[r]]: CTA y-index walks rows, so each CTA reads its row's
