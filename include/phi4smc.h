@@ -273,11 +273,28 @@ phi4_status phi4_batch_workspace_bytes(const phi4_config* cfgs, int32_t n_runs, 
 phi4_status smc_init_batch(const phi4_config* cfgs, int32_t n_runs, void* d_workspace, size_t workspace_bytes,
                            void* stream, phi4_run** out);
 
-/* One temperature for every member still below beta = 1 (the same steps as
- * smc_temper_step, stage-interleaved across members; the ESS bisection runs in one
- * CTA per member). *n_active_out = members still below beta = 1 afterwards.
- * Synchronises. PHI4_ERR_DONE when no member is active. */
+/* One temperature for every member still below beta = 1: the same steps as
+ * smc_temper_step, each stage one launch over all members. The ESS bisection with the
+ * reweighting and log Z (one CTA per member), the resampling and the particle gather
+ * run on the batch's own stream; the covariance and Cholesky of each member on the
+ * member's stream; the sweeps of the mixed-form members with L % 4 == 0 as one CUDA
+ * graph per buffer parity (per sweep: the normals of all members, one grouped tcgen05
+ * proposal GEMM over all members' tiles, one fused accept over all members' particles),
+ * captured at the first temperature and replayed; other members' sweeps on their own
+ * streams. Each member's arithmetic is that of the run advanced alone, except that its
+ * bisection sums in one CTA. Launch shapes come from the autotuner (phi4_batch_tuning;
+ * environment PHI4_TUNE=0 keeps the defaults, PHI4_TUNE_CACHE names the JSON cache file,
+ * default $HOME/.cache/phi4smc_tune.json). *n_active_out = members still below beta = 1
+ * afterwards. Synchronises. PHI4_ERR_DONE when no member is active. Members must have
+ * flags == 0. */
 phi4_status smc_temper_step_batch(phi4_run* batch, int32_t* n_active_out);
+
+/* The launch shapes the batch's autotuner chose at its first temperature, as a JSON
+ * object (each with its source: "measured", "cache" or "default"; the cache file; whether
+ * the sweeps run as a captured CUDA graph), into `out` (host, `cap` bytes). "{}" before
+ * the first smc_temper_step_batch. The tuned shapes (CTAs of the grouped proposal GEMM,
+ * threads of the batched normals and gather) change no result. */
+phi4_status phi4_batch_tuning(const phi4_run* batch, char* out, size_t cap);
 
 /* Borrowed handle of member r for smc_log_evidence / smc_observables /
  * smc_copy_particles (owned by the batch; smc_free on it is rejected). */

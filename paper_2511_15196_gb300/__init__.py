@@ -112,6 +112,7 @@ _SIGS = {
     "smc_init_batch": ([_P, _I32, _P, _SZ, _P, ctypes.POINTER(_P)], _I32),
     "smc_temper_step_batch": ([_P, ctypes.POINTER(_I32)], _I32),
     "phi4_batch_member": ([_P, _I32, ctypes.POINTER(_P)], _I32),
+    "phi4_batch_tuning": ([_P, ctypes.c_char_p, _SZ], _I32),
     "phi4_kernel_launches": ([_P, ctypes.POINTER(ctypes.c_int64)], _I32),
     "phi4_set_stage_timing": ([_P, _I32], _I32),
     "phi4_stage_times": ([_P, ctypes.POINTER(_F64), ctypes.POINTER(ctypes.c_int64), _I32], _I32),
@@ -344,6 +345,13 @@ class Batch:
             if self.temper_step() == 0:
                 break
         return [m.observables() for m in self.members]
+
+    def tuning(self):
+        """The autotuner's launch shapes (phi4_batch_tuning) as a dict."""
+        import json
+        buf = ctypes.create_string_buffer(4096)
+        _check(lib().phi4_batch_tuning(self.handle, buf, 4096))
+        return json.loads(buf.value.decode())
 
     def close(self):
         if getattr(self, "handle", None):

@@ -24,7 +24,7 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", 
          "--expt-relaxed-constexpr", "-diag-suppress", "177"]
 SOURCES = ["capi.cu", "ns.cu", "kernels_rng.cu", "kernels_lattice.cu", "kernels_temper.cu", "kernels_resample.cu",
            "kernels_cov.cu", "kernels_chol.cu", "kernels_gemm_simt.cu", "kernels_tc.cu", "kernels_ns.cu",
-           "resample_static.cu", "kernels_irmh.cu", "kernels_obs.cu"]
+           "resample_static.cu", "kernels_irmh.cu", "kernels_obs.cu", "batch.cu"]
 
 
 def nvcc():

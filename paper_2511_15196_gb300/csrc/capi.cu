@@ -489,43 +489,6 @@ phi4_status step_finish(phi4_run* r, const double* h, const uint32_t* sw, double
 
 }  // namespace phi4
 
-namespace phi4 {
-
-// Per-member results of a batch into one array: [0..7] bisection results, [8] log Z,
-// [9] beta, [10] status word, [11] accepted moves of the last sweeps.
-__global__ void batch_gather_kernel(void* const* __restrict__ ptrs, int R, double* __restrict__ out) {
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
-    const double* scal = (const double*)ptrs[2 * r];
-    const uint32_t* st = (const uint32_t*)ptrs[2 * r + 1];
-    double* o = out + (size_t)r * 12;
-    for (int k = 0; k < 8; ++k) o[k] = scal[SC_OUT + k];
-    o[8] = scal[SC_KAHAN];
-    o[9] = scal[SC_BETA];
-    o[10] = (double)st[0];
-    o[11] = (double)st[1];
-  }
-}
-
-namespace {
-// Caller stream waits for every member stream, then one launch gathers the members'
-// scalars and one copy brings them to the host.
-phi4_status batch_collect(phi4_run* b, const std::vector<phi4_run*>& act, std::vector<double>& host) {
-  const int R = (int)b->members.size();
-  for (phi4_run* m : act) {
-    CUDA_TRY(cudaEventRecord(m->join, m->stream));
-    CUDA_TRY(cudaStreamWaitEvent(b->stream, m->join, 0));
-  }
-  batch_gather_kernel<<<(R + 127) / 128, 128, 0, b->stream>>>(b->batch_ptrs, R, b->batch_scalars);
-  CUDA_TRY(cudaGetLastError());
-  host.resize((size_t)R * 12);
-  CUDA_TRY(cudaMemcpyAsync(host.data(), b->batch_scalars, host.size() * 8, cudaMemcpyDeviceToHost, b->stream));
-  CUDA_TRY(cudaStreamSynchronize(b->stream));
-  return PHI4_OK;
-}
-}  // namespace
-
-}  // namespace phi4
-
 extern "C" {
 
 const char* phi4_last_error(void) { return g_err; }
@@ -849,6 +812,7 @@ phi4_status smc_free(phi4_run* r) {
   if (!r) return PHI4_OK;
   ARG_CHECK(!r->owner, "this run belongs to a batch: free the batch handle");
   if (r->batch) {
+    batch_release(r);
     for (phi4_run* m : r->members) {
       m->owner = nullptr;
       cudaStream_t ms = m->stream;
@@ -1110,121 +1074,5 @@ phi4_status phi4_rw_accept_delta(float* phi, const void* delta_f16, int32_t N, i
   return PHI4_OK;
 }
 
-/* ------------------------------ batched form ------------------------------ */
-
-static size_t batch_header_bytes(int32_t n) { return align256((size_t)n * 12 * 8) + align256((size_t)n * 2 * 8); }
-
-phi4_status phi4_batch_workspace_bytes(const phi4_config* cfgs, int32_t n_runs, size_t* bytes) {
-  ARG_CHECK(cfgs && bytes, "NULL argument");
-  ARG_CHECK(n_runs >= 1 && n_runs <= 4096, "n_runs = %d outside [1, 4096]", n_runs);
-  size_t tot = batch_header_bytes(n_runs);
-  for (int r = 0; r < n_runs; ++r) {
-    size_t b = 0;
-    phi4_status st = phi4_workspace_bytes(&cfgs[r], &b);
-    if (st != PHI4_OK) return st;
-    ARG_CHECK(cfgs[r].kind == PHI4_SMC_RW, "batch member %d: only SMC runs are batched", r);
-    ARG_CHECK(cfgs[r].N <= 4096, "batch member %d: N = %d above the 4096 of a one-CTA bisection", r, cfgs[r].N);
-    tot += align256(b);
-  }
-  *bytes = tot;
-  return PHI4_OK;
-}
-
-phi4_status smc_init_batch(const phi4_config* cfgs, int32_t n_runs, void* d_ws, size_t ws_bytes, void* stream,
-                           phi4_run** out) {
-  ARG_CHECK(out, "out is NULL");
-  size_t need = 0;
-  phi4_status ps = phi4_batch_workspace_bytes(cfgs, n_runs, &need);
-  if (ps != PHI4_OK) return ps;
-  ARG_CHECK(d_ws && ((uintptr_t)d_ws & 255) == 0, "workspace must be non-NULL and 256-byte aligned");
-  if (ws_bytes < need) {
-    set_error("workspace of %zu bytes, need %zu", ws_bytes, need);
-    return PHI4_ERR_WORKSPACE;
-  }
-  phi4_run* b = new phi4_run();
-  b->batch = true;
-  b->cfg = cfgs[0];
-  b->stream = (cudaStream_t)stream;
-  unsigned char* base = (unsigned char*)d_ws;
-  b->batch_scalars = (double*)base;
-  b->batch_ptrs = (void**)(base + align256((size_t)n_runs * 12 * 8));
-  size_t off = batch_header_bytes(n_runs);
-  std::vector<void*> ptrs((size_t)n_runs * 2);
-  for (int r = 0; r < n_runs; ++r) {
-    size_t bytes = 0;
-    phi4_workspace_bytes(&cfgs[r], &bytes);
-    cudaStream_t ms = nullptr;
-    cudaError_t e = cudaStreamCreateWithFlags(&ms, cudaStreamNonBlocking);
-    phi4_run* m = nullptr;
-    if (e == cudaSuccess) ps = smc_init(&cfgs[r], base + off, bytes, ms, &m);
-    if (e != cudaSuccess || ps != PHI4_OK) {
-      if (e != cudaSuccess) set_error("member stream: %s", cudaGetErrorString(e));
-      if (ms) cudaStreamDestroy(ms);
-      smc_free(b);
-      return e != cudaSuccess ? PHI4_ERR_CUDA : ps;
-    }
-    m->owner = b;
-    m->owns_stream = true;
-    cudaEventCreateWithFlags(&m->join, cudaEventDisableTiming);
-    b->members.push_back(m);
-    ptrs[2 * r] = m->scal;
-    ptrs[2 * r + 1] = m->status;
-    off += align256(bytes);
-  }
-  CUDA_TRY(cudaMemcpyAsync(b->batch_ptrs, ptrs.data(), ptrs.size() * sizeof(void*), cudaMemcpyHostToDevice,
-                           b->stream));
-  cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
-  for (phi4_run* m : b->members) {
-    CUDA_TRY(cudaEventRecord(m->join, m->stream));
-    CUDA_TRY(cudaStreamWaitEvent(b->stream, m->join, 0));
-  }
-  *out = b;
-  return PHI4_OK;
-}
-
-phi4_status smc_temper_step_batch(phi4_run* b, int32_t* n_active_out) {
-  ARG_CHECK(b && b->batch, "not a batch handle");
-  std::vector<phi4_run*> act;
-  for (phi4_run* m : b->members)
-    if (!m->done) act.push_back(m);
-  if (act.empty()) {
-    if (n_active_out) *n_active_out = 0;
-    set_error("every run of the batch is at beta = 1");
-    return PHI4_ERR_DONE;
-  }
-  // members start after the caller's earlier work
-  CUDA_TRY(cudaEventRecord(b->join, b->stream));
-  for (phi4_run* m : act) CUDA_TRY(cudaStreamWaitEvent(m->stream, b->join, 0));
-  phi4_status ps;
-  for (phi4_run* m : act)
-    if ((ps = step_front(m, true)) != PHI4_OK) return ps;
-  std::vector<double> h;
-  if ((ps = batch_collect(b, act, h)) != PHI4_OK) return ps;
-  for (phi4_run* m : act) {
-    const size_t i = (size_t)(std::find(b->members.begin(), b->members.end(), m) - b->members.begin());
-    if ((ps = refit_check(m, (uint32_t)h[i * 12 + 10])) != PHI4_OK) return ps;
-  }
-  for (phi4_run* m : act)
-    if ((ps = step_back(m)) != PHI4_OK) return ps;
-  if ((ps = batch_collect(b, act, h)) != PHI4_OK) return ps;
-  int n_active = 0;
-  for (size_t i = 0; i < b->members.size(); ++i) {
-    phi4_run* m = b->members[i];
-    if (std::find(act.begin(), act.end(), m) != act.end()) {
-      const uint32_t sw[2] = {(uint32_t)h[i * 12 + 10], (uint32_t)h[i * 12 + 11]};
-      if ((ps = step_finish(m, &h[i * 12], sw, nullptr)) != PHI4_OK) return ps;
-    }
-    if (!m->done) ++n_active;
-  }
-  if (n_active_out) *n_active_out = n_active;
-  return PHI4_OK;
-}
-
-phi4_status phi4_batch_member(phi4_run* b, int32_t r, phi4_run** member_out) {
-  ARG_CHECK(b && b->batch && member_out, "not a batch handle");
-  ARG_CHECK(r >= 0 && r < (int32_t)b->members.size(), "member %d outside [0, %d)", r, (int)b->members.size());
-  *member_out = b->members[r];
-  return PHI4_OK;
-}
 
 }  // extern "C"

@@ -11,6 +11,13 @@ namespace phi4 {
 // About one second of SM clock: the default limit of every spin-wait in this library.
 constexpr long long kSpinLimitCyclesDefault = 2000000000LL;
 
+// Device scalars of a run (one 256-byte block): bisection results, the Kahan pair of
+// log Z, beta, the ridge, nested-sampling bookkeeping, observables, and for the batched
+// form the temperature counter and the run's participation in the current step.
+enum { SC_OUT = 0 /* 8 doubles: bisection results */, SC_KAHAN = 8 /* 2 */, SC_BETA = 10, SC_RIDGE = 11,
+       SC_NS = 12 /* NS bookkeeping, 8 doubles */, SC_OBS = 20 /* observables, 6 doubles */, SC_T = 26,
+       SC_ACTIVE = 27, SC_COUNT = 32 };
+
 struct ActionParams {
   int L, D, N;
   double m2, lam, c_kin, c_mass;

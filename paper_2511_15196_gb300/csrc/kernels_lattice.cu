@@ -7,6 +7,7 @@
 #include "internal.h"
 #include <cuda_fp16.h>
 #include "philox.cuh"
+#include "batch.h"
 
 namespace phi4 {
 
@@ -405,27 +406,28 @@ PHI4_DEV int accept_decision_bits(uint32_t w0, uint32_t w1, double log_alpha) {
 // lattice row (kept in registers), reads the up/down neighbour groups and the two
 // horizontal end neighbours from the staged row, and keeps plain float partial sums
 // over at most a few groups; each warp sums its lanes in float (a tree over at most
-// 512 sites) and the warps' sums are combined in double. The proposal is either a float row `prop` or phi + delta with
-// delta an fp16 increment (the tensor-core proposal's epilogue output).
-template <int PPB, int TPP, bool kDelta, int kMaxG>
-__global__ void __launch_bounds__(PPB* TPP) accept_vec_kernel(float* __restrict__ phi, const float* __restrict__ prop,
-                                                              const __half* __restrict__ delta, ActionParams p,
-                                                              int keep_ref, double* __restrict__ S,
-                                                              double* __restrict__ sq, double* __restrict__ ell,
-                                                              const double* __restrict__ beta_ptr, PhiloxKey key,
-                                                              uint32_t w0, uint32_t sweep,
-                                                              uint32_t* __restrict__ acc_count,
-                                                              uint32_t* __restrict__ status) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ float red[PPB][TPP / 32][2];
-  __shared__ int accept_flag[PPB];
-  __shared__ uint2 uwords[PPB];
+// 512 sites) and the warps' sums are combined in double. The proposal is either a float
+// row `prop` or phi + delta with delta an fp16 increment (the tensor-core proposal's
+// epilogue output). The block holds PPB particles of TPP threads each (PPB <= 8,
+// TPP <= 256, TPP a multiple of 32, PPB * TPP = blockDim.x); particle g of the block is
+// i = i0 + g, and `rot` rotates the decision warp over the block's warps.
+constexpr int kVecMaxPPB = 8, kVecMaxWarps = 8;
+template <bool kDelta, int kMaxG>
+PHI4_DEV void accept_vec_body(int PPB, int TPP, int i0, int N, int rot, float* __restrict__ phi,
+                              const float* __restrict__ prop, const __half* __restrict__ delta,
+                              const ActionParams& p, int keep_ref, double* __restrict__ S, double* __restrict__ sq,
+                              double* __restrict__ ell, const double* __restrict__ beta_ptr, PhiloxKey key,
+                              uint32_t w0, uint32_t sweep, uint32_t* __restrict__ acc_count,
+                              uint32_t* __restrict__ status, float* __restrict__ rows) {
+  __shared__ float red[kVecMaxPPB][kVecMaxWarps][2];
+  __shared__ int accept_flag[kVecMaxPPB];
+  __shared__ uint2 uwords[kVecMaxPPB];
   const int g = threadIdx.x / TPP, t = threadIdx.x % TPP;
-  const int i = blockIdx.x * PPB + g;
+  const int i = i0 + g;
   const int L = p.L, D = p.D, ng = D >> 2;
-  float* row = reinterpret_cast<float*>(smem_raw) + (size_t)g * D;
+  float* row = rows + (size_t)g * D;
   float4 v[kMaxG];
-  if (i < p.N) {
+  if (i < N) {
 #pragma unroll
     for (int k = 0; k < kMaxG; ++k) {
       const int q = t + k * TPP;
@@ -448,16 +450,16 @@ __global__ void __launch_bounds__(PPB* TPP) accept_vec_kernel(float* __restrict_
   // the particle's decision is taken by warp wd (rotating with the block so the serial
   // double work lands on every sub-partition in turn); another warp draws its uniform's
   // words while the others start the stencil
-  constexpr int kWarps = TPP / 32;
-  const int wd = (blockIdx.x + g) % kWarps;
-  if (i < p.N && t == ((wd + kWarps / 2) % kWarps) * 32) {
+  const int kWarps = TPP / 32;
+  const int wd = (rot + g) % kWarps;
+  if (i < N && t == ((wd + kWarps / 2) % kWarps) * 32) {
     const uint4 w = philox4x32_10(make_uint4(w0, sweep, (uint32_t)i, 0u), key);
     uwords[g] = make_uint2(w.x, w.y);
   }
   __syncthreads();
   const float ck = (float)p.c_kin, cm = (float)(p.c_mass * p.m2), lm = (float)p.lam;
   float s = 0.f, qq = 0.f;
-  if (i < p.N) {
+  if (i < N) {
 #pragma unroll
     for (int k = 0; k < kMaxG; ++k) {
       const int q = t + k * TPP;
@@ -492,10 +494,9 @@ __global__ void __launch_bounds__(PPB* TPP) accept_vec_kernel(float* __restrict_
     red[g][wg][1] = qq;
   }
   __syncthreads();
-  if (i < p.N && wg == wd) {
+  if (i < N && wg == wd) {
     double Sp = lane < kWarps ? (double)red[g][lane][0] : 0.0;
     double Qp = lane < kWarps ? (double)red[g][lane][1] : 0.0;
-#pragma unroll
     for (int o = kWarps / 2; o > 0; o >>= 1) {
       Sp += __shfl_xor_sync(0xffffffffu, Sp, o);
       Qp += __shfl_xor_sync(0xffffffffu, Qp, o);
@@ -522,13 +523,66 @@ __global__ void __launch_bounds__(PPB* TPP) accept_vec_kernel(float* __restrict_
     }
   }
   __syncthreads();
-  if (i < p.N && accept_flag[g]) {
+  if (i < N && accept_flag[g]) {
 #pragma unroll
     for (int k = 0; k < kMaxG; ++k) {
       const int q = t + k * TPP;
       if (q < ng) reinterpret_cast<float4*>(phi + (size_t)i * D)[q] = v[k];
     }
   }
+}
+
+template <int PPB, int TPP, bool kDelta, int kMaxG>
+__global__ void __launch_bounds__(PPB* TPP) accept_vec_kernel(float* __restrict__ phi, const float* __restrict__ prop,
+                                                              const __half* __restrict__ delta, ActionParams p,
+                                                              int keep_ref, double* __restrict__ S,
+                                                              double* __restrict__ sq, double* __restrict__ ell,
+                                                              const double* __restrict__ beta_ptr, PhiloxKey key,
+                                                              uint32_t w0, uint32_t sweep,
+                                                              uint32_t* __restrict__ acc_count,
+                                                              uint32_t* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  accept_vec_body<kDelta, kMaxG>(PPB, TPP, (int)blockIdx.x * PPB, p.N, (int)blockIdx.x, phi, prop, delta, p,
+                                 keep_ref, S, sq, ell, beta_ptr, key, w0, sweep, acc_count, status,
+                                 reinterpret_cast<float*>(smem_raw));
+}
+
+// Batched form: one launch over the blocks of every member run (mixed form, L % 4 == 0).
+// Block b belongs to the run r with blk0[r] <= b < blk0[r + 1] (binary search over the
+// runs' block offsets); its particles and block shape (PPB, TPP) are that run's, the same
+// as a single run's launch picks, so the results equal the single-run kernel's. Runs that
+// are done (scal[SC_ACTIVE] == 0) or whose sweeps are fewer than `sweep` + 1 are skipped;
+// the temperature index comes from the run's device counter. Every shape the single-run
+// launcher picks fills the 256 threads (PPB * TPP = 256).
+__global__ void __launch_bounds__(256) batch_accept_kernel(const BatchRun* __restrict__ runs, int R,
+                                                           const int* __restrict__ blk0, uint32_t sweep) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int lo = 0, hi = R - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (blk0[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const BatchRun& b = runs[lo];
+  if (b.scal[SC_ACTIVE] == 0.0 || (int)sweep >= b.n_mcmc) return;
+  const int local = (int)blockIdx.x - blk0[lo];
+  const uint32_t t = (uint32_t)b.scal[SC_T];
+  accept_vec_body<true, 8>(b.ppb, b.tpp, local * b.ppb, b.ap.N, local, (float*)b.phi_dst, nullptr, b.delta, b.ap,
+                           b.keep_ref, b.S_dst, b.sq_dst, b.ell_dst, b.scal + SC_BETA, b.key,
+                           counter_word0(RNG_ACCEPT, t), sweep, b.acc, b.status, reinterpret_cast<float*>(smem_raw));
+}
+
+cudaError_t batch_accept_prepare(size_t smem) { return set_smem_bytes((const void*)batch_accept_kernel, smem); }
+
+cudaError_t launch_batch_accept(const BatchRun* runs, int R, const int* blk0, int n_blocks, size_t smem,
+                                uint32_t sweep, cudaStream_t s) {
+  if (n_blocks <= 0) return cudaSuccess;
+  batch_accept_kernel<<<n_blocks, 256, smem, s>>>(runs, R, blk0, sweep);
+  return cudaGetLastError();
+}
+
+// The block shape the single-run launcher picks for a mixed run of D sites (see accept_vec).
+void accept_vec_shape(int D, int* ppb, int* tpp) {
+  if (D >= 1024) { *ppb = 1; *tpp = 256; } else { *ppb = 8; *tpp = 32; }
 }
 
 template <typename T>
@@ -540,6 +594,11 @@ __global__ void magnetisation_kernel(const T* __restrict__ phi, int N, int D, do
   for (int x = lane; x < D; x += 32) s += (double)phi[(size_t)i * D + x];
   s = warp_sum(s);
   if (lane == 0) M[i] = s / D;
+}
+
+cudaError_t set_smem_bytes(const void* kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 namespace {

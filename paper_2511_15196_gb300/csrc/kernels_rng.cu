@@ -2,6 +2,7 @@
 #include <algorithm>
 #include "internal.h"
 #include "philox.cuh"
+#include "batch.h"
 
 namespace phi4 {
 
@@ -72,6 +73,75 @@ cudaError_t launch_z2_flip(uint64_t seed, uint64_t stream_id, uint32_t step, voi
   if (dtype == 0) z2_flip_kernel<double><<<grid, 256, 0, s>>>(key, w0, N, D, (double*)phi);
   else if (dtype == 1) z2_flip_kernel<float><<<grid, 256, 0, s>>>(key, w0, N, D, (float*)phi);
   else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+// Batched form: the proposal normals of every member run in one launch. Global row gr
+// (grid y) belongs to run r with row0[r] <= gr < row0[r + 1]; each thread makes the same
+// eight values of its row as normals_kernel (counter (PROPOSE << 24 | t, sweep, row,
+// block), t the run's temperature counter) in the run's element type. Runs that are done
+// or have fewer sweeps are skipped.
+__global__ void batch_normals_kernel(const BatchRun* __restrict__ runs, int R, const int* __restrict__ row0,
+                                     int total_rows, uint32_t sweep) {
+  for (int gr = blockIdx.y; gr < total_rows; gr += gridDim.y) {
+    int lo = 0, hi = R - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (row0[mid] <= gr) lo = mid; else hi = mid - 1;
+    }
+    const BatchRun& b = runs[lo];
+    if (b.scal[SC_ACTIVE] == 0.0 || (int)sweep >= b.n_mcmc) continue;
+    const int r = gr - row0[lo], n_cols = b.ap.D;
+    const int nblk = (n_cols + 3) >> 2;
+    const uint32_t w0 = counter_word0(RNG_PROPOSE, (uint32_t)b.scal[SC_T]);
+    for (int b0 = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x); b0 < nblk; b0 += 2 * (int)(gridDim.x * blockDim.x)) {
+      float z[8];
+      double zd[8];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint4 w = philox4x32_10(make_uint4(w0, sweep, (uint32_t)r, (uint32_t)(b0 + h)), b.key);
+        if (b.dtype == 0) {  // double
+          const double2 z01 = box_muller_f64(w.x, w.y), z23 = box_muller_f64(w.z, w.w);
+          zd[4 * h] = z01.x; zd[4 * h + 1] = z01.y; zd[4 * h + 2] = z23.x; zd[4 * h + 3] = z23.y;
+        } else {
+          const float2 z01 = box_muller_f32(w.x, w.y), z23 = box_muller_f32(w.z, w.w);
+          z[4 * h] = z01.x; z[4 * h + 1] = z01.y; z[4 * h + 2] = z23.x; z[4 * h + 3] = z23.y;
+        }
+      }
+      const int left = n_cols - 4 * b0;
+      if (b.dtype == 0) {  // double
+        double* o = (double*)b.Z + (size_t)r * b.ldz + 4 * b0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (j < left) o[j] = zd[j];
+      } else if (b.dtype == 1) {  // float
+        float* o = (float*)b.Z + (size_t)r * b.ldz + 4 * b0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (j < left) o[j] = z[j];
+      } else {
+        __nv_bfloat16* o = (__nv_bfloat16*)b.Z + (size_t)r * b.ldz + 4 * b0;
+        if (left >= 8 && (((uintptr_t)o) & 15) == 0) {
+          __nv_bfloat16 zb[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) zb[j] = __float2bfloat16_rn(z[j]);
+          *reinterpret_cast<uint4*>(o) = *reinterpret_cast<const uint4*>(zb);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (j < left) o[j] = __float2bfloat16_rn(z[j]);
+        }
+      }
+    }
+  }
+}
+
+cudaError_t launch_batch_normals(const BatchRun* runs, int R, const int* row0, int total_rows, int max_d,
+                                 uint32_t sweep, int threads, cudaStream_t s) {
+  if (total_rows <= 0) return cudaSuccess;
+  const int nblk = (max_d + 3) / 4;
+  const dim3 grid((unsigned)((nblk + 2 * threads - 1) / (2 * threads)), (unsigned)std::min(total_rows, 65535));
+  batch_normals_kernel<<<grid, threads, 0, s>>>(runs, R, row0, total_rows, sweep);
   return cudaGetLastError();
 }
 

@@ -16,8 +16,10 @@
 #include <cuda_fp16.h>
 #include <algorithm>
 #include <cstdlib>
+#include <cstring>
 #include "internal.h"
 #include "common.cuh"
+#include "batch.h"
 
 namespace phi4 {
 namespace tc {
@@ -129,18 +131,74 @@ PHI4_DEV void tmem_ld32_nw(uint32_t taddr, uint32_t (&r)[32]) {
                : "r"(taddr));
 }
 
-// Work unit u -> tile (mb, nb) and number of K blocks. Column tiles are walked in
-// decreasing K extent (heaviest first); the row tiles of one column tile are
-// consecutive units, so CTAs working at the same time share the factor tile in L2.
-PHI4_DEV void get_tile(const Params& p, int u, int& mb, int& nb, int& kblocks) {
-  nb = p.tiles_n - 1 - u / p.tiles_m;
-  mb = u % p.tiles_m;
-  const int kend = min(p.K, (nb + 1) * BN);
-  kblocks = (kend + BK - 1) / BK;
-}
+// One tile of the proposal GEMM as the three roles see it: the two tensor maps, the row
+// and column tile, the K blocks it needs, and where and how its epilogue writes.
+struct Tile {
+  const CUtensorMap* ma;
+  const CUtensorMap* mb_map;
+  int mb, nb, kblocks, M, Nn;
+  __half* delta;
+  float scale;
+  bool skip;  // a unit of a run that sits out this launch (all roles skip it alike)
+};
 
-__global__ void __launch_bounds__(NUM_THREADS, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Params p) {
+// Tiles of one run. Column tiles are walked in decreasing K extent (heaviest first); the
+// row tiles of one column tile are consecutive units, so CTAs working at the same time
+// share the factor tile in L2. A column tile [n0, n0 + BN) needs only k < n0 + BN.
+struct SingleTiles {
+  const CUtensorMap* ma;
+  const CUtensorMap* mb_map;
+  const Params* p;
+  PHI4_DEV Tile get(int u) const {
+    Tile t;
+    t.ma = ma;
+    t.mb_map = mb_map;
+    t.nb = p->tiles_n - 1 - u / p->tiles_m;
+    t.mb = u % p->tiles_m;
+    t.kblocks = (min(p->K, (t.nb + 1) * BN) + BK - 1) / BK;
+    t.M = p->M;
+    t.Nn = p->Nn;
+    t.delta = p->delta;
+    t.scale = p->scale;
+    t.skip = false;
+    return t;
+  }
+};
+
+// Tiles of every run of a batch: unit u belongs to the run r with tile0[r] <= u <
+// tile0[r + 1] (binary search), then the run's own order as above. A run that is done
+// (SC_ACTIVE == 0) or has fewer sweeps than this launch's sweep index sits out.
+struct GroupedTiles {
+  const GemmRun* runs;
+  int R;
+  uint32_t sweep;
+  PHI4_DEV Tile get(int u) const {
+    int lo = 0, hi = R - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (runs[mid].tile0 <= u) lo = mid; else hi = mid - 1;
+    }
+    const GemmRun& g = runs[lo];
+    const int v = u - g.tile0;
+    Tile t;
+    t.ma = reinterpret_cast<const CUtensorMap*>(g.mapA);
+    t.mb_map = reinterpret_cast<const CUtensorMap*>(g.mapB);
+    t.nb = g.tiles_n - 1 - v / g.tiles_m;
+    t.mb = v % g.tiles_m;
+    t.kblocks = (min(g.K, (t.nb + 1) * BN) + BK - 1) / BK;
+    t.M = g.M;
+    t.Nn = g.Nn;
+    t.delta = g.delta;
+    t.scale = g.scale;
+    t.skip = g.scal[SC_ACTIVE] == 0.0 || (int)sweep >= g.n_mcmc;
+    return t;
+  }
+};
+
+// Persistent CTAs (one per SM) walk units cid, cid + grid, ...; warp 0 = TMA producer,
+// warp 1 = MMA issuer and TMEM owner, warps 2..5 = epilogue (s * acc -> fp16 Delta).
+template <class Tiles>
+PHI4_DEV void gemm_body(const Tiles& tiles, int num_units, uint32_t* status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
@@ -163,8 +221,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -179,22 +235,28 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
   auto give_up = [&]() {
     *abort_flag = 1;
-    atomicOr(p.status, ST_TIMEOUT);
+    atomicOr(status, ST_TIMEOUT);
   };
 
   if (warp == 0) {
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
-      for (int u = cid; u < p.num_tiles && !*abort_flag; u += ncl) {
-        int mb, nb, kblocks;
-        get_tile(p, u, mb, nb, kblocks);
-        for (int kb = 0; kb < kblocks; ++kb) {
+      const CUtensorMap* last = nullptr;
+      for (int u = cid; u < num_units && !*abort_flag; u += ncl) {
+        const Tile t = tiles.get(u);
+        if (t.skip) continue;
+        if (t.ma != last) {
+          asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)t.ma) : "memory");
+          asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)t.mb_map) : "memory");
+          last = t.ma;
+        }
+        for (int kb = 0; kb < t.kblocks; ++kb) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) { give_up(); break; }
           uint8_t* sa = smem + stage * STAGE_BYTES;
           mbar_expect_tx(&full[stage], STAGE_BYTES);
-          tma_load_2d(&tmA, &full[stage], sa, kb * BK, mb * BM);
-          tma_load_2d(&tmB, &full[stage], sa + A_BYTES, kb * BK, nb * BN);
+          tma_load_2d(t.ma, &full[stage], sa, kb * BK, t.mb * BM);
+          tma_load_2d(t.mb_map, &full[stage], sa + A_BYTES, kb * BK, t.nb * BN);
           if (++stage == STAGES) { stage = 0; phase ^= 1u; }
         }
       }
@@ -203,14 +265,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     if (lane == 0) {
       int stage = 0, acc = 0;
       uint32_t phase = 0, acc_phase = 0;
-      for (int u = cid; u < p.num_tiles && !*abort_flag; u += ncl) {
-        int mb, nb, kblocks;
-        get_tile(p, u, mb, nb, kblocks);
+      for (int u = cid; u < num_units && !*abort_flag; u += ncl) {
+        const Tile t = tiles.get(u);
+        if (t.skip) continue;
         if (!mbar_wait(&tempty[acc], acc_phase ^ 1u, abort_flag)) { give_up(); break; }
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
         bool ok = true;
-        for (int kb = 0; kb < kblocks; ++kb) {
+        for (int kb = 0; kb < t.kblocks; ++kb) {
           if (!mbar_wait(&full[stage], phase, abort_flag)) { give_up(); ok = false; break; }
           tc_fence_after();
           const uint32_t a0 = smem_u32(smem + stage * STAGE_BYTES), b0 = a0 + A_BYTES;
@@ -231,29 +293,29 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const int r = q * 32 + lane;
     int acc = 0;
     uint32_t acc_phase = 0;
-    for (int u = cid; u < p.num_tiles; u += ncl) {
-      int mb, nb, kblocks;
-      get_tile(p, u, mb, nb, kblocks);
+    for (int u = cid; u < num_units; u += ncl) {
+      const Tile t = tiles.get(u);
+      if (t.skip) continue;
       if (!mbar_wait(&tfull[acc], acc_phase, abort_flag)) { give_up(); break; }
       tc_fence_after();
-      const int gm = mb * BM + r;
+      const int gm = t.mb * BM + r;
       const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
 #pragma unroll 1
       for (int c = 0; c < BN / 32; ++c) {
         float v[32];
         tmem_ld32(trow + (uint32_t)(c * 32), v);
-        const int gn0 = nb * BN + c * 32;
-        if (gm < p.M && gn0 < p.Nn) {
-          const size_t o = (size_t)gm * p.Nn + gn0;
-          if (gn0 + 32 <= p.Nn && (p.Nn & 7) == 0) {
-            uint4* dst = reinterpret_cast<uint4*>(p.delta + o);
+        const int gn0 = t.nb * BN + c * 32;
+        if (gm < t.M && gn0 < t.Nn) {
+          const size_t o = (size_t)gm * t.Nn + gn0;
+          if (gn0 + 32 <= t.Nn && (t.Nn & 7) == 0) {
+            uint4* dst = reinterpret_cast<uint4*>(t.delta + o);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
               uint4 pk;
-              __half2 h0 = __floats2half2_rn(p.scale * v[8 * j], p.scale * v[8 * j + 1]);
-              __half2 h1 = __floats2half2_rn(p.scale * v[8 * j + 2], p.scale * v[8 * j + 3]);
-              __half2 h2 = __floats2half2_rn(p.scale * v[8 * j + 4], p.scale * v[8 * j + 5]);
-              __half2 h3 = __floats2half2_rn(p.scale * v[8 * j + 6], p.scale * v[8 * j + 7]);
+              __half2 h0 = __floats2half2_rn(t.scale * v[8 * j], t.scale * v[8 * j + 1]);
+              __half2 h1 = __floats2half2_rn(t.scale * v[8 * j + 2], t.scale * v[8 * j + 3]);
+              __half2 h2 = __floats2half2_rn(t.scale * v[8 * j + 4], t.scale * v[8 * j + 5]);
+              __half2 h3 = __floats2half2_rn(t.scale * v[8 * j + 6], t.scale * v[8 * j + 7]);
               pk.x = *reinterpret_cast<uint32_t*>(&h0);
               pk.y = *reinterpret_cast<uint32_t*>(&h1);
               pk.z = *reinterpret_cast<uint32_t*>(&h2);
@@ -263,7 +325,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           } else {
 #pragma unroll
             for (int j = 0; j < 32; ++j)
-              if (gn0 + j < p.Nn) p.delta[o + j] = __float2half_rn(p.scale * v[j]);
+              if (gn0 + j < t.Nn) t.delta[o + j] = __float2half_rn(t.scale * v[j]);
           }
         }
       }
@@ -280,6 +342,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
   }
+}
+
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Params p) {
+  SingleTiles tiles{&tmA, &tmB, &p};
+  gemm_body(tiles, p.num_tiles, p.status);
+}
+
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    tc_gemm_grouped_kernel(const GemmRun* __restrict__ runs, int R, int num_units, uint32_t sweep,
+                           uint32_t* status) {
+  GroupedTiles tiles{runs, R, sweep};
+  gemm_body(tiles, num_units, status);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -822,6 +897,38 @@ cudaError_t launch_propose_tc(void* delta_f16, const void* Zb, int ldz, const vo
   p.scale = scale;
   p.status = status;
   return tc::launch(ma, mb, p, s);
+}
+
+bool make_gemm_run(GemmRun* g, const void* Zb, int ldz, const void* Lb, int ldl, int N, int D, float scale,
+                   __half* delta, const double* scal, int n_mcmc) {
+  static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+  CUtensorMap ma, mb;
+  if (!tc::make_map(&ma, Zb, D, N, ldz, tc::BM) || !tc::make_map(&mb, Lb, D, D, ldl, tc::BN)) return false;
+  memcpy(g->mapA, &ma, sizeof(ma));
+  memcpy(g->mapB, &mb, sizeof(mb));
+  g->delta = delta;
+  g->scal = scal;
+  g->scale = scale;
+  g->M = N;
+  g->Nn = D;
+  g->K = D;
+  g->tiles_m = (N + tc::BM - 1) / tc::BM;
+  g->tiles_n = (D + tc::BN - 1) / tc::BN;
+  g->tile0 = 0;
+  g->n_mcmc = n_mcmc;
+  return true;
+}
+
+cudaError_t grouped_propose_prepare() {
+  return cudaFuncSetAttribute(tc::tc_gemm_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+}
+
+cudaError_t launch_grouped_propose(const GemmRun* runs, int R, int total_tiles, int grid, uint32_t sweep,
+                                   uint32_t* status, cudaStream_t s) {
+  if (total_tiles <= 0 || R <= 0) return cudaSuccess;
+  grid = std::max(1, std::min(grid, total_tiles));
+  tc::tc_gemm_grouped_kernel<<<grid, tc::NUM_THREADS, tc::SMEM_BYTES, s>>>(runs, R, total_tiles, sweep, status);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gram_tc(const void* H, const void* Lo, int ldx, int D, int N, const int* shift, int a,

@@ -13,9 +13,9 @@ enum { STG_BISECT, STG_RESAMPLE, STG_GATHER, STG_COV, STG_CHOL, STG_NORMALS, STG
        STG_NS_SELECT, STG_NS_SLICE, STG_OTHER, STG_CHOL_UPDATE /* kernel-level, inside STG_CHOL */,
        STG_MUTATION /* wall time of the n_mcmc sweeps (their stages overlap on three streams) */ };
 
-// Device scalars of a run (one 256-byte block).
-enum { SC_OUT = 0 /* 8 doubles: bisection results */, SC_KAHAN = 8 /* 2 */, SC_BETA = 10, SC_RIDGE = 11,
-       SC_NS = 12 /* NS bookkeeping, 8 doubles */, SC_OBS = 20 /* observables, 6 doubles */, SC_COUNT = 32 };
+namespace phi4 {
+struct BatchHost;  // host state of a batch handle (batch.cu)
+}
 
 struct phi4_run {
   phi4_config cfg;
@@ -70,6 +70,7 @@ struct phi4_run {
   phi4_run* owner = nullptr;
   std::vector<phi4_run*> members;
   bool owns_stream = false;
+  phi4::BatchHost* bh = nullptr;      // batch handle: streams, descriptors, graphs, tuning
   double* batch_scalars = nullptr;    // device [R][12] gathered per-run results
   void** batch_ptrs = nullptr;        // device [R][2]: each member's scal and status
   cudaEvent_t join = nullptr;
@@ -142,6 +143,7 @@ phi4_status step_back(phi4_run* r);
 phi4_status step_finish(phi4_run* r, const double* h, const uint32_t* sw, double* beta_out);
 phi4_status ns_replace(phi4_run* r, int32_t* done_out);
 phi4_status ns_evidence(phi4_run* r, double* logz, double* logz_err);
+void batch_release(phi4_run* b);
 
 }  // namespace phi4
 

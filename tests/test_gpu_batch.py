@@ -57,3 +57,66 @@ def test_batch_rejects_large_members():
     with pytest.raises(p.Phi4Error) as e:
         p.Batch([p.Config(L=4, N=8192)])
     assert e.value.status == p.PHI4_ERR_ARG
+
+
+def test_batch_fp64_members_match_oracle():
+    # FP64 members of a batch follow the oracle step by step: the batched bisection,
+    # reweighting, resampling and gather (one launch each over all members) and the
+    # members' own refits and sweeps
+    from oracle.smc import SMC, SMCConfig
+    shapes = [(4, 256, 4.0), (6, 300, 8.0), (8, 512, 16.0), (3, 130, 8.0)]
+    cfgs = [p.Config(L=L, N=N, m2=-4.0, lam=lam, precision=p.FP64, n_mcmc=3, seed=40 + r)
+            for r, (L, N, lam) in enumerate(shapes)]
+    refs = [SMC(SMCConfig(L=L, N=N, m2=-4.0, lam=lam, n_mcmc=3, rho=0.5, seed=40 + r))
+            for r, (L, N, lam) in enumerate(shapes)]
+    batch = p.Batch(cfgs)
+    for _ in range(3):
+        batch.temper_step()
+        for m, ref in zip(batch.members, refs):
+            if ref.done:
+                continue
+            rec = ref.temper_step()
+            assert m.observables()["beta"] == pytest.approx(rec["beta"], rel=1e-10, abs=1e-13)
+            assert m.log_evidence()[0] == pytest.approx(rec["logz"], rel=1e-10, abs=1e-9)
+            assert np.abs(m.particles().cpu().numpy() - ref.phi).max() < 1e-8
+    batch.close()
+
+
+def test_batch_graph_sweeps_and_tuning_cache(tmp_path, monkeypatch):
+    # an all-mixed batch takes the captured-graph sweeps (normals, grouped tcgen05 GEMM and
+    # fused accept over all members per sweep); its launch shapes are measured at the first
+    # temperature and written to the JSON cache, which a second batch of the same members
+    # reads back; both batches follow the same trajectories (no shape changes a result)
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("PHI4_TUNE_CACHE", str(cache))
+    monkeypatch.delenv("PHI4_TUNE", raising=False)
+    shapes = [(8, 1024), (12, 2048), (16, 4096), (24, 1024), (32, 2048), (8, 300)]
+    cfgs = [p.Config(L=L, N=N, m2=-4.0, lam=8.0, precision=p.MIXED_BF16, n_mcmc=5, seed=70 + r)
+            for r, (L, N) in enumerate(shapes)]
+    a = p.Batch(cfgs)
+    assert a.tuning() == {}
+    for _ in range(3):
+        a.temper_step()
+    ta = a.tuning()
+    assert ta["graph"] is True and ta["gemm_ctas_source"] == "measured" and cache.exists()
+    b = p.Batch(cfgs)
+    for _ in range(3):
+        b.temper_step()
+    tb = b.tuning()
+    assert tb["gemm_ctas_source"] == "cache" and tb["gemm_ctas"] == ta["gemm_ctas"]
+    for ma, mb in zip(a.members, b.members):
+        assert torch.equal(ma.particles(), mb.particles())
+        assert ma.log_evidence()[0] == mb.log_evidence()[0]
+        o = ma.observables()
+        assert o["n_steps"] == 3 and 0.0 < o["acc_rate"] < 1.0
+    # the members agree with the same runs advanced alone (the bisection sums in another
+    # order, so to rounding)
+    singles = [p.Run(c) for c in cfgs]
+    for s, m in zip(singles, a.members):
+        for _ in range(3):
+            s.temper_step()
+        assert m.log_evidence()[0] == pytest.approx(s.log_evidence()[0], rel=1e-9, abs=1e-9)
+        assert np.abs(m.particles().cpu().numpy() - s.particles().cpu().numpy()).max() < 1e-4
+        s.close()
+    a.close()
+    b.close()
