@@ -120,7 +120,7 @@ def run_batch(a):
                                    "N in {1024,2048,4096} by seed, lambda in {4,8,16}, m2=-4, %d RWM sweeps, "
                                    "ESS 0.5N, bf16 tensor-core GEMMs" % (a.batch_runs, n_mcmc),
                        "runs": a.batch_runs, "l2": "per-step working set of all runs (~1.5 GB) larger than L2"},
-            "gpu_launches": launches, "clocks": clk.summary()}
+            "gpu_launches": launches, "clocks": clk.summary(), "tuning": b.tuning()}
     if rank == 0:
         print(json.dumps(line))
     b.close()

@@ -444,6 +444,7 @@ phi4_status smc_init_batch(const phi4_config* cfgs, int32_t n_runs, void* d_ws, 
     d.iters = c.bisect_iters;
     d.keep_ref = c.keep_reference;
     d.dtype = m->dtype;
+    d.zdtype = m->zdtype;
     d.ldz = m->ldz;
     d.w = m->w;
     d.scal = m->scal;
@@ -570,18 +571,21 @@ phi4_status smc_temper_step_batch(phi4_run* b, int32_t* n_active_out) {
   // back: the vec members' sweeps on the batch stream, the others' on their own streams
   for (size_t i = 0; i < b->members.size(); ++i) {
     phi4_run* m = b->members[i];
-    if (m->done) continue;
-    if (h->vec[i]) {
-      CUDA_TRY(cudaEventRecord(m->join, m->stream));
-      CUDA_TRY(cudaStreamWaitEvent(s, m->join, 0));
-      m->n_evals += (int64_t)m->cfg.N * m->cfg.n_mcmc;
-      m->kernel_launches += 3 * m->cfg.n_mcmc;
-    } else if ((ps = step_back(m)) != PHI4_OK) {
-      return ps;
-    }
+    if (m->done || !h->vec[i]) continue;
+    CUDA_TRY(cudaEventRecord(m->join, m->stream));
+    CUDA_TRY(cudaStreamWaitEvent(s, m->join, 0));
+    m->n_evals += (int64_t)m->cfg.N * m->cfg.n_mcmc;
+    m->kernel_launches += 3 * m->cfg.n_mcmc;
+  }
+  // the autotuner reruns this step's gather (into buffers nothing else touches until the
+  // sweeps below) and the vec members' normals and GEMM (both recomputed by the sweeps)
+  if (!h->tuned && (ps = tune(b, q)) != PHI4_OK) return ps;
+  for (size_t i = 0; i < b->members.size(); ++i) {
+    phi4_run* m = b->members[i];
+    if (m->done || h->vec[i]) continue;
+    if ((ps = step_back(m)) != PHI4_OK) return ps;
   }
   if (h->n_vec > 0) {
-    if (!h->tuned && (ps = tune(b, q)) != PHI4_OK) return ps;
     if (!h->graph[q]) {
       cudaGraph_t g = nullptr;
       CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));

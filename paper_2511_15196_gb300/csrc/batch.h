@@ -17,7 +17,10 @@ struct BatchRun {
   ActionParams ap;
   PhiloxKey key;
   double rho;
-  int iters, keep_ref, n_mcmc, dtype, ldz;
+  int iters, keep_ref, n_mcmc;
+  int dtype;   // element type of the fields (0 double, 1 float)
+  int zdtype;  // element type of the proposal normals Z (0 double, 1 float, 2 bf16)
+  int ldz;
   int ppb, tpp;  // block shape of the fused accept (the single-run launcher's)
   const void* phi_src;
   void* phi_dst;

@@ -100,7 +100,7 @@ __global__ void batch_normals_kernel(const BatchRun* __restrict__ runs, int R, c
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const uint4 w = philox4x32_10(make_uint4(w0, sweep, (uint32_t)r, (uint32_t)(b0 + h)), b.key);
-        if (b.dtype == 0) {  // double
+        if (b.zdtype == 0) {  // double
           const double2 z01 = box_muller_f64(w.x, w.y), z23 = box_muller_f64(w.z, w.w);
           zd[4 * h] = z01.x; zd[4 * h + 1] = z01.y; zd[4 * h + 2] = z23.x; zd[4 * h + 3] = z23.y;
         } else {
@@ -109,12 +109,12 @@ __global__ void batch_normals_kernel(const BatchRun* __restrict__ runs, int R, c
         }
       }
       const int left = n_cols - 4 * b0;
-      if (b.dtype == 0) {  // double
+      if (b.zdtype == 0) {  // double
         double* o = (double*)b.Z + (size_t)r * b.ldz + 4 * b0;
 #pragma unroll
         for (int j = 0; j < 8; ++j)
           if (j < left) o[j] = zd[j];
-      } else if (b.dtype == 1) {  // float
+      } else if (b.zdtype == 1) {  // float
         float* o = (float*)b.Z + (size_t)r * b.ldz + 4 * b0;
 #pragma unroll
         for (int j = 0; j < 8; ++j)
