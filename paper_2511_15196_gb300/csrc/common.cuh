@@ -167,6 +167,67 @@ struct KahanF {
   PHI4_DEV double value() const { return (double)s - (double)c; }
 };
 
+// Error-free transformations in float (Knuth's two-sum; the two-product through one
+// fused multiply-add): a + b = s + e and a * b = p + e exactly, with s, p the rounded
+// results. They let the float forms sum float site terms to about 2^-48 relative.
+PHI4_DEV void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+PHI4_DEV void two_prod(float a, float b, float& p, float& e) {
+  p = a * b;
+  e = fmaf(a, b, -p);
+}
+
+// A float pair hi + lo accumulating (hi, lo) terms: the running sum's rounding errors are
+// collected exactly by two_sum and added, with the terms' low parts, into lo.
+struct AccF2 {
+  float hi = 0.f, lo = 0.f;
+  PHI4_DEV void add(float th, float tl) {
+    float s, e;
+    two_sum(hi, th, s, e);
+    hi = s;
+    lo += e + tl;
+  }
+  PHI4_DEV void add(const AccF2& o) {
+    add(o.hi, o.lo);
+  }
+  PHI4_DEV double value() const { return (double)hi + (double)lo; }
+};
+
+// Sum of an AccF2 over the 32 lanes (the same tree on every lane).
+PHI4_DEV AccF2 warp_sum_f2(AccF2 a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    AccF2 b;
+    b.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
+    b.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
+    a.add(b);
+  }
+  return a;
+}
+
+// The float site terms of Eq. (1) in the bond form sum_x sum_mu (phi_{x+mu} - phi_x)^2 of
+// the kinetic term (equal to the site form for periodic lattices), split so that every
+// product is exact: the kinetic bonds to the right and down neighbours into K, phi^2 into
+// P2 and phi^4 into P4. S = c_kin K + c_mass m2 P2 + lambda P4 and |phi|^2 = P2 are formed
+// in double from the three sums. Dropped parts: squares of the low halves (2^-48 relative).
+PHI4_DEV void site_terms_f2(float f, float fr, float fd, AccF2& K, AccF2& P2, AccF2& P4) {
+  float bh, bl, ph, pl;
+  two_sum(fr, -f, bh, bl);
+  two_prod(bh, bh, ph, pl);
+  K.add(ph, fmaf(2.f * bh, bl, pl));
+  two_sum(fd, -f, bh, bl);
+  two_prod(bh, bh, ph, pl);
+  K.add(ph, fmaf(2.f * bh, bl, pl));
+  float qh, ql;
+  two_prod(f, f, qh, ql);
+  P2.add(qh, ql);
+  two_prod(qh, qh, ph, pl);
+  P4.add(ph, fmaf(2.f * qh, ql, pl));
+}
+
 template <typename T> PHI4_DEV T to_t(float x);
 template <> PHI4_DEV float to_t<float>(float x) { return x; }
 template <> PHI4_DEV __nv_bfloat16 to_t<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }

@@ -13,7 +13,7 @@ namespace phi4 {
 
 template <typename T>
 struct SiteCoef {
-  T ck, cm, lm;
+  double ck, cm, lm;
 };
 
 // Per-thread partial sums of the site terms and of phi^2 over sites x = t, t+TPP, ...
@@ -37,19 +37,18 @@ PHI4_DEV void site_sums(const T* __restrict__ row, int L, int D, int t, SiteCoef
     }
     s_out = s; q_out = q;
   } else {
-    KahanF s, q;
+    // float fields: exact products and compensated sums (site_terms_f2), the three partial
+    // sums combined in double
+    AccF2 K, P2, P4;
     for (int x = t; x < D; x += TPP) {
-      const int cl = c == 0 ? L - 1 : c - 1, cr = c == L - 1 ? 0 : c + 1;
-      const int ru = r == 0 ? L - 1 : r - 1, rd = r == L - 1 ? 0 : r + 1;
-      const float f = row[x];
-      const float nb = row[r * L + cl] + row[r * L + cr] + row[ru * L + c] + row[rd * L + c];
-      const float f2 = f * f;
-      s.add(k.ck * (f * (4.0f * f - nb)) + k.cm * f2 + k.lm * (f2 * f2));
-      q.add(f2);
+      const int cr = c == L - 1 ? 0 : c + 1, rd = r == L - 1 ? 0 : r + 1;
+      site_terms_f2(row[x], row[r * L + cr], row[rd * L + c], K, P2, P4);
       c += dc; r += dr;
       if (c >= L) { c -= L; ++r; }
     }
-    s_out = s.value(); q_out = q.value();
+    const double p2 = P2.value();
+    s_out = (double)k.ck * K.value() + (double)k.cm * p2 + (double)k.lm * P4.value();
+    q_out = p2;
   }
 }
 
@@ -67,7 +66,7 @@ PHI4_DEV void group_sum2(double& a, double& b, double* red) {
 
 template <typename T>
 PHI4_DEV SiteCoef<T> coefs(const ActionParams& p) {
-  return SiteCoef<T>{(T)p.c_kin, (T)(p.c_mass * p.m2), (T)p.lam};
+  return SiteCoef<T>{p.c_kin, p.c_mass * p.m2, p.lam};
 }
 
 template <typename T, int PPB, int TPP>
@@ -403,12 +402,12 @@ PHI4_DEV int accept_decision_bits(uint32_t w0, uint32_t w1, double log_alpha) {
 }
 
 // Float fields with L % 4 == 0: each thread owns float4 groups of four sites of one
-// lattice row (kept in registers), reads the up/down neighbour groups and the two
-// horizontal end neighbours from the staged row, and keeps plain float partial sums
-// over at most a few groups; each warp sums its lanes in float (a tree over at most
-// 512 sites) and the warps' sums are combined in double. The proposal is either a float
-// row `prop` or phi + delta with delta an fp16 increment (the tensor-core proposal's
-// epilogue output). The block holds PPB particles of TPP threads each (PPB <= 8,
+// lattice row (kept in registers), reads the down neighbour group and the right end
+// neighbour from the staged row, and sums the bond-form site terms with exact products
+// and compensated float sums (site_terms_f2); the sums travel as float pairs through the
+// warp and CTA trees and are combined into S and |phi|^2 in double, so S of the float
+// fields is exact to about 2^-48 relative. The proposal is either a float row `prop` or
+// phi + delta with delta an fp16 increment (the tensor-core proposal's epilogue output). The block holds PPB particles of TPP threads each (PPB <= 8,
 // TPP <= 256, TPP a multiple of 32, PPB * TPP = blockDim.x); particle g of the block is
 // i = i0 + g, and `rot` rotates the decision warp over the block's warps.
 constexpr int kVecMaxPPB = 8, kVecMaxWarps = 8;
@@ -419,7 +418,7 @@ PHI4_DEV void accept_vec_body(int PPB, int TPP, int i0, int N, int rot, float* _
                               double* __restrict__ ell, const double* __restrict__ beta_ptr, PhiloxKey key,
                               uint32_t w0, uint32_t sweep, uint32_t* __restrict__ acc_count,
                               uint32_t* __restrict__ status, float* __restrict__ rows) {
-  __shared__ float red[kVecMaxPPB][kVecMaxWarps][2];
+  __shared__ float red[kVecMaxPPB][kVecMaxWarps][6];
   __shared__ int accept_flag[kVecMaxPPB];
   __shared__ uint2 uwords[kVecMaxPPB];
   const int g = threadIdx.x / TPP, t = threadIdx.x % TPP;
@@ -457,8 +456,10 @@ PHI4_DEV void accept_vec_body(int PPB, int TPP, int i0, int N, int rot, float* _
     uwords[g] = make_uint2(w.x, w.y);
   }
   __syncthreads();
-  const float ck = (float)p.c_kin, cm = (float)(p.c_mass * p.m2), lm = (float)p.lam;
-  float s = 0.f, qq = 0.f;
+  // exact products and compensated float sums of the bond-form site terms (site_terms_f2):
+  // per thread, then per warp in float pairs; the decision warp adds the warps' pairs and
+  // forms S and |phi|^2 in double
+  AccF2 K, P2, P4;
   if (i < N) {
 #pragma unroll
     for (int k = 0; k < kMaxG; ++k) {
@@ -466,42 +467,38 @@ PHI4_DEV void accept_vec_body(int PPB, int TPP, int i0, int N, int rot, float* _
       if (q < ng) {
         const int x0 = q << 2;
         const int r = x0 / L, c0 = x0 - r * L;
-        const int ru = r == 0 ? L - 1 : r - 1, rd = r == L - 1 ? 0 : r + 1;
-        const float4 up = reinterpret_cast<const float4*>(row + ru * L)[c0 >> 2];
+        const int rd = r == L - 1 ? 0 : r + 1;
         const float4 dn = reinterpret_cast<const float4*>(row + rd * L)[c0 >> 2];
-        const float lf = row[r * L + (c0 == 0 ? L - 1 : c0 - 1)];
         const float rt = row[r * L + (c0 + 4 == L ? 0 : c0 + 4)];
         const float4 f = v[k];
-        const float n0 = lf + f.y + up.x + dn.x, n1 = f.x + f.z + up.y + dn.y;
-        const float n2 = f.y + f.w + up.z + dn.z, n3 = f.z + rt + up.w + dn.w;
-        const float a0 = f.x * f.x, a1 = f.y * f.y, a2 = f.z * f.z, a3 = f.w * f.w;
-        s += ck * (f.x * (4.f * f.x - n0)) + cm * a0 + lm * (a0 * a0);
-        s += ck * (f.y * (4.f * f.y - n1)) + cm * a1 + lm * (a1 * a1);
-        s += ck * (f.z * (4.f * f.z - n2)) + cm * a2 + lm * (a2 * a2);
-        s += ck * (f.w * (4.f * f.w - n3)) + cm * a3 + lm * (a3 * a3);
-        qq += (a0 + a1) + (a2 + a3);
+        site_terms_f2(f.x, f.y, dn.x, K, P2, P4);
+        site_terms_f2(f.y, f.z, dn.y, K, P2, P4);
+        site_terms_f2(f.z, f.w, dn.z, K, P2, P4);
+        site_terms_f2(f.w, rt, dn.w, K, P2, P4);
       }
     }
   }
-  // float warp trees (<= 32 partials of <= 4 groups each); the warps' results are
-  // combined in double by the decision warp, one lane per warp result (a 3-level
-  // double tree instead of a serial chain on one sub-partition)
-  s = warp_sum(s);
-  qq = warp_sum(qq);
+  K = warp_sum_f2(K);
+  P2 = warp_sum_f2(P2);
+  P4 = warp_sum_f2(P4);
   const int lane = t & 31, wg = t >> 5;
   if (lane == 0) {
-    red[g][wg][0] = s;
-    red[g][wg][1] = qq;
+    float* rr = red[g][wg];
+    rr[0] = K.hi; rr[1] = K.lo; rr[2] = P2.hi; rr[3] = P2.lo; rr[4] = P4.hi; rr[5] = P4.lo;
   }
   __syncthreads();
   if (i < N && wg == wd) {
-    double Sp = lane < kWarps ? (double)red[g][lane][0] : 0.0;
-    double Qp = lane < kWarps ? (double)red[g][lane][1] : 0.0;
-    for (int o = kWarps / 2; o > 0; o >>= 1) {
-      Sp += __shfl_xor_sync(0xffffffffu, Sp, o);
-      Qp += __shfl_xor_sync(0xffffffffu, Qp, o);
+    AccF2 k2, q2, f2;
+    if (lane < kWarps) {
+      const float* rr = red[g][lane];
+      k2.hi = rr[0]; k2.lo = rr[1]; q2.hi = rr[2]; q2.lo = rr[3]; f2.hi = rr[4]; f2.lo = rr[5];
     }
+    k2 = warp_sum_f2(k2);
+    q2 = warp_sum_f2(q2);
+    f2 = warp_sum_f2(f2);
     if (lane == 0) {
+      const double Qp = q2.value();
+      const double Sp = p.c_kin * k2.value() + (p.c_mass * p.m2) * Qp + p.lam * f2.value();
       const double beta = *beta_ptr;
       const double dS = Sp - S[i], dq2 = Qp - sq[i];
       const double log_alpha = keep_ref ? (-beta * dS - 0.5 * dq2) : (-beta * dS - (1.0 - beta) * 0.5 * dq2);

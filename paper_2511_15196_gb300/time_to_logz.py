@@ -4,15 +4,19 @@ of a grid whose seeds' mean log Z lies within tol of a reference value and whose
 seed-to-seed standard deviation is at most tol. The reference is the pooled mean of the
 reference form's runs at the grid's most expensive cell.
 
-Workload: broken-phase phi^4 (m2 = -4, lambda = 8), n_mcmc random-walk sweeps per
-temperature, runs from beta = 0 to 1. The number of sweeps is a grid axis because the
-estimate's bias depends on it: the proposal covariance is estimated from the population
-it moves, and with few sweeps per temperature that biases log Z upwards by far more than
-the tolerance at large D.
+Workloads: broken-phase phi^4 (m2 = -4, lambda = 8; default), or with --free the free
+field (m2 = 1, lambda = 0), whose log Z has a closed form that then serves as the
+reference (no reference runs). n_mcmc random-walk sweeps per temperature, runs from
+beta = 0 to 1. The number of sweeps is a grid axis because the estimate's bias depends on
+it: the proposal covariance is estimated from the population it moves, and with few
+sweeps per temperature that biases log Z upwards by far more than the tolerance at large
+D. --kernel-cov gaussian replaces that covariance by the exact one of the tempered
+Gaussian part (PHI4_FLAG_FREE_KERNEL_COV; the target's own for the free field), which
+does not depend on the particles.
 
     python -m paper_2511_15196_gb300.time_to_logz [--L 64] [--N 8192 16384 32768 65536]
         [--rho 0.5 0.9] [--n-mcmc 20] [--seeds 32] [--forms mixed fp32] [--ref-form fp64]
-        [--tol 0.05]
+        [--tol 0.05] [--free] [--kernel-cov population|gaussian] [--confirm-seeds 8]
 """
 import argparse
 import json
@@ -21,6 +25,13 @@ import statistics
 import time
 
 FORMS = {"fp64": 0, "fp32": 1, "mixed": 2}
+
+
+def free_field_logz(L, m2):
+    """log Z = (D/2) log pi - (1/2) sum_k log(m2 + sum_mu 4 sin^2(pi k_mu / L)) of the free
+    field with the unhalved action (the closed form of the workload statement)."""
+    s = [4.0 * math.sin(math.pi * k / L) ** 2 for k in range(L)]
+    return 0.5 * L * L * math.log(math.pi) - 0.5 * sum(math.log(m2 + a + b) for a in s for b in s)
 
 
 def cells(Ns, rhos, sweeps=(20,)):
@@ -45,11 +56,15 @@ def first_within(rows, ref, tol):
     return None
 
 
+MODEL = {"m2": -4.0, "lam": 8.0, "flags": 0}
+
+
 def gpu_runner(L, N, rho, form, seed, n_mcmc):
     """One run to beta = 1 on the GPU: (log Z, wall milliseconds)."""
     import torch
     from . import Config, Run
-    cfg = Config(L=L, N=N, m2=-4.0, lam=8.0, precision=FORMS[form], n_mcmc=n_mcmc, ess_target=rho, seed=seed)
+    cfg = Config(L=L, N=N, m2=MODEL["m2"], lam=MODEL["lam"], flags=MODEL["flags"], precision=FORMS[form],
+                 n_mcmc=n_mcmc, ess_target=rho, seed=seed)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     run = Run(cfg)
@@ -67,16 +82,44 @@ def run_cell(L, N, rho, form, seeds, n_mcmc, runner=gpu_runner, seed0=0):
     return row
 
 
-def measure(L, Ns, rhos, forms, ref_form, seeds, tol, n_mcmc, runner=gpu_runner, emit=print):
-    """n_mcmc: sweeps per temperature, one value or a list of them (a grid axis)."""
+def measure(L, Ns, rhos, forms, ref_form, seeds, tol, n_mcmc, runner=gpu_runner, emit=print, exact=None,
+            confirm_seeds=0):
+    """n_mcmc: sweeps per temperature, one value or a list of them (a grid axis).
+    exact: a known log Z (closed form) used as the reference instead of reference runs.
+    confirm_seeds > 0: only the first form scans the grid; every other form is run at the
+    first form's cell (and at the cell before it in cost order, when there is one) with
+    that many seeds, its time there reported (the forms run the same sampler, so they reach
+    the tolerance at the same cell; the rows show whether they do)."""
     sweeps = [n_mcmc] if isinstance(n_mcmc, int) else list(n_mcmc)
     grid = cells(Ns, rhos, sweeps)
-    N_ref, rho_ref, m_ref = grid[-1]
-    ref_row = run_cell(L, N_ref, rho_ref, ref_form, seeds, m_ref, runner, seed0=10000)
-    ref = ref_row["logz_mean"]
-    emit(json.dumps({"reference": ref_row}))
+    if exact is None:
+        N_ref, rho_ref, m_ref = grid[-1]
+        ref_row = run_cell(L, N_ref, rho_ref, ref_form, seeds, m_ref, runner, seed0=10000)
+        ref = ref_row["logz_mean"]
+        emit(json.dumps({"reference": ref_row}))
+    else:
+        ref = exact
+        emit(json.dumps({"reference": {"closed_form": exact}}))
     out = {}
-    for form in forms:
+    for fi, form in enumerate(forms):
+        if confirm_seeds > 0 and fi > 0:
+            first = out[forms[0]]["cell"]
+            if first is None:
+                out[form] = {"time_to_logz_s": None, "cell": None, "logz_ref": ref, "tol": tol}
+                emit(json.dumps({"form": form, **out[form]}))
+                continue
+            idx = grid.index((first["N"], first["rho"], first["n_mcmc"]))
+            rows = []
+            for N, rho, m in grid[max(0, idx - 1):idx + 1]:
+                row = run_cell(L, N, rho, form, confirm_seeds, m, runner)
+                rows.append(row)
+                emit(json.dumps(row))
+            hit = rows[-1]
+            ok = abs(hit["logz_mean"] - ref) <= tol and hit["logz_sd"] <= tol
+            out[form] = {"time_to_logz_s": hit["ms_per_run"] * 1e-3, "cell": first, "logz_ref": ref, "tol": tol,
+                         "within_tol_at_cell": ok, "seeds": confirm_seeds}
+            emit(json.dumps({"form": form, **out[form]}))
+            continue
         rows = []
         hit = None
         for N, rho, m in grid:
@@ -103,8 +146,19 @@ def main():
     ap.add_argument("--ref-form", default="fp64", choices=list(FORMS))
     ap.add_argument("--tol", type=float, default=0.05)
     ap.add_argument("--n-mcmc", type=int, nargs="+", default=[20])
+    ap.add_argument("--free", action="store_true", help="free field m2 = 1, lambda = 0 against its closed form")
+    ap.add_argument("--kernel-cov", default="population", choices=["population", "gaussian"])
+    ap.add_argument("--confirm-seeds", type=int, default=0)
     a = ap.parse_args()
-    measure(a.L, a.N, a.rho, a.forms, a.ref_form, a.seeds, a.tol, a.n_mcmc)
+    exact = None
+    if a.free:
+        MODEL.update(m2=1.0, lam=0.0)
+        exact = free_field_logz(a.L, 1.0)
+    if a.kernel_cov == "gaussian":
+        from . import FLAG_FREE_KERNEL_COV
+        MODEL["flags"] = FLAG_FREE_KERNEL_COV
+    measure(a.L, a.N, a.rho, a.forms, a.ref_form, a.seeds, a.tol, a.n_mcmc, exact=exact,
+            confirm_seeds=a.confirm_seeds)
 
 
 if __name__ == "__main__":

@@ -47,3 +47,30 @@ def test_measure_with_sweeps_as_an_axis():
     r = out["mixed"]
     assert r["cell"] == {"N": 1024, "rho": 0.5, "n_mcmc": 200}
     assert abs(r["logz_ref"] - (-100.0 + 3.0 / 200)) < 0.01
+
+
+def test_free_field_closed_form_matches_the_pinned_values():
+    # the module's closed form (the reference of --free) against tests/golden/exact_logz.txt
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "exact_logz.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    for kind, L, m2, lam, lz in rows:
+        if kind == "free":
+            assert abs(ttl.free_field_logz(int(L), float(m2)) - float(lz)) < 1e-9
+
+
+def test_measure_against_an_exact_value_and_confirm_the_second_form():
+    # with a closed form as the reference no reference runs are made; the second form is
+    # run only at the first form's cell and the one before it
+    calls = []
+
+    def runner(L, N, rho, form, seed, n_mcmc):
+        calls.append((form, N))
+        return -100.0 + 100.0 / N + (4.0 / N) * math.sin(seed + 1.0), N * (10.0 if form == "fp32" else 1.0)
+
+    out = ttl.measure(8, [256, 1024, 4096], [0.5], ["mixed", "fp32"], "fp64", 4, 0.05, 10, runner=runner,
+                      emit=lambda s: None, exact=-100.0, confirm_seeds=2)
+    assert out["mixed"]["cell"] == {"N": 4096, "rho": 0.5, "n_mcmc": 10}
+    assert out["fp32"]["cell"] == out["mixed"]["cell"] and out["fp32"]["within_tol_at_cell"]
+    assert out["fp32"]["time_to_logz_s"] == 4096 * 10.0 * 1e-3
+    assert sorted(set(n for f, n in calls if f == "fp32")) == [1024, 4096]
