@@ -51,7 +51,7 @@ def summarise(logz, ms):
 def first_within(rows, ref, tol):
     """The first row (rows in increasing cost) with |mean - ref| <= tol and sd <= tol."""
     for r in rows:
-        if abs(r["logz_mean"] - ref) <= tol and r["logz_sd"] <= tol:
+        if "given_up_after" not in r and abs(r["logz_mean"] - ref) <= tol and r["logz_sd"] <= tol:
             return r
     return None
 
@@ -75,15 +75,24 @@ def gpu_runner(L, N, rho, form, seed, n_mcmc):
     return obs["logz"], ms
 
 
-def run_cell(L, N, rho, form, seeds, n_mcmc, runner=gpu_runner, seed0=0):
-    res = [runner(L, N, rho, form, seed0 + s, n_mcmc) for s in range(seeds)]
+def run_cell(L, N, rho, form, seeds, n_mcmc, runner=gpu_runner, seed0=0, ref=None, tol=None, early=0):
+    """Runs `seeds` seeds of a cell. With early > 1 and a reference, the cell is given up
+    after its first `early` seeds when their mean lies more than tol + 5 standard errors
+    from the reference (it cannot end within tol); the row then says so."""
+    res = [runner(L, N, rho, form, seed0 + s, n_mcmc) for s in range(min(seeds, early) if early > 1 else seeds)]
+    if early > 1 and ref is not None and len(res) < seeds:
+        head = summarise([r[0] for r in res], [r[1] for r in res])
+        if abs(head["logz_mean"] - ref) > tol + 5.0 * head["logz_sd"] / math.sqrt(len(res)):
+            head.update({"L": L, "N": N, "rho": rho, "form": form, "n_mcmc": n_mcmc, "given_up_after": len(res)})
+            return head
+        res += [runner(L, N, rho, form, seed0 + s, n_mcmc) for s in range(len(res), seeds)]
     row = summarise([r[0] for r in res], [r[1] for r in res])
     row.update({"L": L, "N": N, "rho": rho, "form": form, "n_mcmc": n_mcmc})
     return row
 
 
 def measure(L, Ns, rhos, forms, ref_form, seeds, tol, n_mcmc, runner=gpu_runner, emit=print, exact=None,
-            confirm_seeds=0):
+            confirm_seeds=0, early=0):
     """n_mcmc: sweeps per temperature, one value or a list of them (a grid axis).
     exact: a known log Z (closed form) used as the reference instead of reference runs.
     confirm_seeds > 0: only the first form scans the grid; every other form is run at the
@@ -123,7 +132,7 @@ def measure(L, Ns, rhos, forms, ref_form, seeds, tol, n_mcmc, runner=gpu_runner,
         rows = []
         hit = None
         for N, rho, m in grid:
-            row = run_cell(L, N, rho, form, seeds, m, runner)
+            row = run_cell(L, N, rho, form, seeds, m, runner, ref=ref, tol=tol, early=early)
             rows.append(row)
             emit(json.dumps(row))
             hit = first_within(rows, ref, tol)
@@ -149,6 +158,8 @@ def main():
     ap.add_argument("--free", action="store_true", help="free field m2 = 1, lambda = 0 against its closed form")
     ap.add_argument("--kernel-cov", default="population", choices=["population", "gaussian"])
     ap.add_argument("--confirm-seeds", type=int, default=0)
+    ap.add_argument("--early-seeds", type=int, default=0,
+                    help="give a cell up after this many seeds when it cannot end within the tolerance")
     a = ap.parse_args()
     exact = None
     if a.free:
@@ -158,7 +169,7 @@ def main():
         from . import FLAG_FREE_KERNEL_COV
         MODEL["flags"] = FLAG_FREE_KERNEL_COV
     measure(a.L, a.N, a.rho, a.forms, a.ref_form, a.seeds, a.tol, a.n_mcmc, exact=exact,
-            confirm_seeds=a.confirm_seeds)
+            confirm_seeds=a.confirm_seeds, early=a.early_seeds)
 
 
 if __name__ == "__main__":

@@ -74,3 +74,17 @@ def test_measure_against_an_exact_value_and_confirm_the_second_form():
     assert out["fp32"]["cell"] == out["mixed"]["cell"] and out["fp32"]["within_tol_at_cell"]
     assert out["fp32"]["time_to_logz_s"] == 4096 * 10.0 * 1e-3
     assert sorted(set(n for f, n in calls if f == "fp32")) == [1024, 4096]
+
+
+def test_cells_far_from_the_reference_are_given_up_early():
+    # a cell whose first seeds sit far outside the tolerance is not run to all its seeds
+    calls = []
+
+    def runner(L, N, rho, form, seed, n_mcmc):
+        calls.append(N)
+        return -100.0 + 200.0 / N + (1.0 / N) * math.sin(seed + 1.0), float(N)
+
+    out = ttl.measure(8, [256, 8192], [0.5], ["mixed"], "fp64", 16, 0.05, 10, runner=runner,
+                      emit=lambda s: None, exact=-100.0, early=4)
+    assert out["mixed"]["cell"] == {"N": 8192, "rho": 0.5, "n_mcmc": 10}
+    assert calls.count(256) == 4 and calls.count(8192) == 16
