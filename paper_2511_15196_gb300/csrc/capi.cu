@@ -33,6 +33,9 @@ int sm_count() {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Sweeps whose proposal normals are drawn ahead, during the temperature's refit.
+constexpr int kZRing = 32;
+
 }  // namespace phi4
 
 using namespace phi4;
@@ -88,6 +91,11 @@ void release_streams(phi4_run* r) {
       cudaEventDestroy(*ev);
       *ev = nullptr;
     }
+  for (auto* v : {&r->ev_nz, &r->ev_gz}) {
+    for (cudaEvent_t e : *v)
+      if (e) cudaEventDestroy(e);
+    v->clear();
+  }
 }
 
 // Workspace layout; with base == nullptr only the total size is computed.
@@ -101,6 +109,11 @@ struct Layout {
   }
 };
 
+// The address `bytes` past `p` inside the workspace (nullptr while only sizing it).
+void* base_or_null(const Layout& L, void* p, size_t bytes) {
+  return L.base ? (void*)((unsigned char*)p + bytes) : (void*)1;
+}
+
 void lay_out(phi4_run* r, Layout& L) {
   const phi4_config& c = r->cfg;
   const int N = c.N, D = c.L * c.L;
@@ -112,8 +125,10 @@ void lay_out(phi4_run* r, Layout& L) {
     r->ldz = (D + 7) & ~7;
     r->ldl = (D + 7) & ~7;
     r->zdtype = PHI4_DT_BF16;
-    r->Z = L.take((size_t)N * r->ldz * 2);
-    r->Z2 = L.take((size_t)N * r->ldz * 2);
+    // pipelined sweeps draw up to kZRing sweeps' normals ahead into a ring of slots
+    r->n_zslots = std::max(2, std::min(c.n_mcmc, kZRing));
+    r->Z = L.take((size_t)N * r->ldz * 2 * r->n_zslots);
+    r->Z2 = base_or_null(L, r->Z, (size_t)N * r->ldz * 2);
     r->Lg = L.take((size_t)D * r->ldl * 2);
   } else {
     r->ldz = D;
@@ -295,6 +310,24 @@ phi4_status step_front(phi4_run* r, bool single_cta_bisect) {
   cudaStream_t s = r->stream;
   const uint32_t t = (uint32_t)(++r->t);
   double* out = r->scal + SC_OUT;
+  if (c.kind == PHI4_SMC_RW && c.precision == PHI4_MIXED_BF16 && c.L % 4 == 0 && r->Z2 && r->s_norm) {
+    // the proposal normals of the temperature's first sweeps do not depend on the fields:
+    // draw them now, on the lowest-priority stream, while the bisection, resampling and
+    // refit run (the previous temperature's GEMMs, which read the slots, finished before
+    // this stream's current point)
+    CUDA_TRY(cudaEventRecord(r->ev_start, s));
+    CUDA_TRY(cudaStreamWaitEvent(r->s_norm, r->ev_start, 0));
+    const size_t zslot = (size_t)N * r->ldz * 2;
+    LaunchTimer* tn = r->timing ? &r->norm_timer : nullptr;
+    for (int sweep = 0; sweep < std::min(c.n_mcmc, r->n_zslots); ++sweep) {
+      cudaEvent_t a0 = tn ? tn->begin(r->s_norm) : nullptr;
+      CUDA_TRY(launch_normals(c.seed, c.stream_id, RNG_PROPOSE, t, (uint32_t)sweep, 0, N, D, r->ldz, r->zdtype,
+                              (unsigned char*)r->Z + (size_t)sweep * zslot, r->s_norm));
+      if (tn) tn->end(r->s_norm, a0);
+      CUDA_TRY(cudaEventRecord(r->ev_nz[sweep], r->s_norm));
+      r->kernel_launches += 1;
+    }
+  }
   {
     StageScope sc(r, STG_BISECT);
     CUDA_TRY(launch_bisect(r->ell, N, r->scal + SC_BETA, c.ess_target, c.bisect_iters, r->w, out, r->bisect_scratch,
@@ -339,34 +372,40 @@ static phi4_status step_sweeps(phi4_run* r) {
   const ActionParams ap = action_params(r);
   StageScope wall(r, STG_MUTATION);
   if (c.precision == PHI4_MIXED_BF16 && c.L % 4 == 0 && r->Z2) {
-    void* Zb[2] = {r->Z, r->Z2};
+    const int R = r->n_zslots;
+    const size_t zslot = (size_t)N * r->ldz * 2;
+    auto Zs = [&](int sweep) { return (void*)((unsigned char*)r->Z + (size_t)(sweep % R) * zslot); };
     void* Db[2] = {r->prop, (unsigned char*)r->prop + (size_t)N * D * 2};
     CUDA_TRY(cudaEventRecord(r->ev_start, s));  // the factor and the fields are ready
-    CUDA_TRY(cudaStreamWaitEvent(r->s_norm, r->ev_start, 0));
     CUDA_TRY(cudaStreamWaitEvent(r->s_gemm, r->ev_start, 0));
     CUDA_TRY(cudaStreamWaitEvent(r->s_acc, r->ev_start, 0));
     cudaStream_t sa = r->s_acc;
     LaunchTimer* tn = r->timing ? &r->norm_timer : nullptr;
     LaunchTimer* tg = r->timing ? &r->gemm_timer : nullptr;
     LaunchTimer* ta = r->timing ? &r->acc_timer : nullptr;
-    // (normals on the GEMM's stream, i.e. only the accept overlapped, measured slower)
     cudaStream_t sn = r->s_norm;
     for (int sweep = 0; sweep < c.n_mcmc; ++sweep) {
-      const int q = sweep & 1;
-      // normals into Z[q] once the GEMM of sweep-2 has read it
-      if (sweep >= 2) CUDA_TRY(cudaStreamWaitEvent(sn, r->ev_g[q], 0));
-      cudaEvent_t a0 = tn ? tn->begin(sn) : nullptr;
-      CUDA_TRY(launch_normals(c.seed, c.stream_id, RNG_PROPOSE, t, (uint32_t)sweep, 0, N, D, r->ldz, r->zdtype,
-                              Zb[q], sn));
-      if (tn) tn->end(sn, a0);
-      CUDA_TRY(cudaEventRecord(r->ev_n[q], sn));
-      // Delta[q] = s Z[q] L^T once the normals are there and the accept of sweep-2 read it
-      CUDA_TRY(cudaStreamWaitEvent(r->s_gemm, r->ev_n[q], 0));
+      const int q = sweep & 1, slot = sweep % R;
+      if (sweep >= R) {
+        // normals of this sweep into its slot once the GEMM of sweep - R has read it (the
+        // first R sweeps' normals were drawn during the refit, step_front)
+        CUDA_TRY(cudaStreamWaitEvent(sn, r->ev_gz[slot], 0));
+        cudaEvent_t a0 = tn ? tn->begin(sn) : nullptr;
+        CUDA_TRY(launch_normals(c.seed, c.stream_id, RNG_PROPOSE, t, (uint32_t)sweep, 0, N, D, r->ldz, r->zdtype,
+                                Zs(sweep), sn));
+        if (tn) tn->end(sn, a0);
+        CUDA_TRY(cudaEventRecord(r->ev_nz[slot], sn));
+        r->kernel_launches += 1;
+      }
+      // Delta[q] = s Z[slot] L^T once the normals are there and the accept of sweep-2 read Delta[q]
+      CUDA_TRY(cudaStreamWaitEvent(r->s_gemm, r->ev_nz[slot], 0));
       if (sweep >= 2) CUDA_TRY(cudaStreamWaitEvent(r->s_gemm, r->ev_a[q], 0));
       cudaEvent_t a1 = tg ? tg->begin(r->s_gemm) : nullptr;
-      CUDA_TRY(launch_propose_tc(Db[q], Zb[q], r->ldz, r->Lg, r->ldl, N, D, (float)r->scale, r->status, r->s_gemm));
+      CUDA_TRY(launch_propose_tc(Db[q], Zs(sweep), r->ldz, r->Lg, r->ldl, N, D, (float)r->scale, r->status,
+                                 r->s_gemm));
       if (tg) tg->end(r->s_gemm, a1);
       CUDA_TRY(cudaEventRecord(r->ev_g[q], r->s_gemm));
+      CUDA_TRY(cudaEventRecord(r->ev_gz[slot], r->s_gemm));
       // the accept chain
       CUDA_TRY(cudaStreamWaitEvent(sa, r->ev_g[q], 0));
       cudaEvent_t a2 = ta ? ta->begin(sa) : nullptr;
@@ -375,7 +414,7 @@ static phi4_status step_sweeps(phi4_run* r) {
                                    r->status, sa));
       if (ta) ta->end(sa, a2);
       CUDA_TRY(cudaEventRecord(r->ev_a[q], sa));
-      r->kernel_launches += 3;
+      r->kernel_launches += 2;
     }
     CUDA_TRY(cudaEventRecord(r->ev_done, sa));  // the last accept follows every GEMM and normals draw
     CUDA_TRY(cudaStreamWaitEvent(s, r->ev_done, 0));
@@ -571,6 +610,12 @@ phi4_status smc_init(const phi4_config* cfg, void* d_workspace, size_t workspace
       if ((e = cudaEventCreateWithFlags(&r->ev_a[q], cudaEventDisableTiming)) != cudaSuccess) return fail(e, "event");
     }
     if ((e = cudaEventCreateWithFlags(&r->ev_start, cudaEventDisableTiming)) != cudaSuccess) return fail(e, "event");
+    r->ev_nz.assign(r->n_zslots, nullptr);
+    r->ev_gz.assign(r->n_zslots, nullptr);
+    for (int q = 0; q < r->n_zslots; ++q) {
+      if ((e = cudaEventCreateWithFlags(&r->ev_nz[q], cudaEventDisableTiming)) != cudaSuccess) return fail(e, "event");
+      if ((e = cudaEventCreateWithFlags(&r->ev_gz[q], cudaEventDisableTiming)) != cudaSuccess) return fail(e, "event");
+    }
   }
   if ((e = cudaMemsetAsync(r->scal, 0, SC_COUNT * 8, s)) != cudaSuccess) return fail(e, "memset");
   if ((e = cudaMemsetAsync(r->status, 0, 16, s)) != cudaSuccess) return fail(e, "memset");

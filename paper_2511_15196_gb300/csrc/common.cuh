@@ -208,24 +208,29 @@ PHI4_DEV AccF2 warp_sum_f2(AccF2 a) {
   return a;
 }
 
-// The float site terms of Eq. (1) in the bond form sum_x sum_mu (phi_{x+mu} - phi_x)^2 of
-// the kinetic term (equal to the site form for periodic lattices), split so that every
-// product is exact: the kinetic bonds to the right and down neighbours into K, phi^2 into
-// P2 and phi^4 into P4. S = c_kin K + c_mass m2 P2 + lambda P4 and |phi|^2 = P2 are formed
-// in double from the three sums. Dropped parts: squares of the low halves (2^-48 relative).
-PHI4_DEV void site_terms_f2(float f, float fr, float fd, AccF2& K, AccF2& P2, AccF2& P4) {
-  float bh, bl, ph, pl;
-  two_sum(fr, -f, bh, bl);
-  two_prod(bh, bh, ph, pl);
-  K.add(ph, fmaf(2.f * bh, bl, pl));
-  two_sum(fd, -f, bh, bl);
-  two_prod(bh, bh, ph, pl);
-  K.add(ph, fmaf(2.f * bh, bl, pl));
-  float qh, ql;
+// The float site terms of Eq. (1), split so that every product is exact: the kinetic
+// sum sum_x sum_mu (phi_{x+mu} - phi_x)^2 (the site form summed over the periodic lattice)
+// equals 4 sum_x phi_x^2 - 2 sum_x phi_x (phi_right + phi_down), so each site contributes
+// phi^2 to P2, phi^4 to P4 and phi phi_right + phi phi_down to C, each an exact product
+// (two_prod) added to a compensated float pair. Then, in double,
+//   S = (4 c_kin + c_mass m2) P2 - 2 c_kin C + lambda P4  and  |phi|^2 = P2;
+// the pairs are exact to about 2^-48 of the summed terms, so S is exact to that order of
+// the site terms' magnitude (the difference 4 P2 - 2 C may cancel; its absolute error does
+// not grow). Dropped parts: squares of the low halves.
+PHI4_DEV void site_terms_f2(float f, float fr, float fd, AccF2& C, AccF2& P2, AccF2& P4) {
+  float ph, pl, qh, ql;
+  two_prod(f, fr, ph, pl);
+  C.add(ph, pl);
+  two_prod(f, fd, ph, pl);
+  C.add(ph, pl);
   two_prod(f, f, qh, ql);
   P2.add(qh, ql);
   two_prod(qh, qh, ph, pl);
   P4.add(ph, fmaf(2.f * qh, ql, pl));
+}
+// S and |phi|^2 from the three sums (double).
+PHI4_DEV double action_from_sums(double C, double P2, double P4, double c_kin, double cm2, double lam) {
+  return (4.0 * c_kin + cm2) * P2 - 2.0 * c_kin * C + lam * P4;
 }
 
 template <typename T> PHI4_DEV T to_t(float x);

@@ -38,7 +38,7 @@ PHI4_DEV void site_sums(const T* __restrict__ row, int L, int D, int t, SiteCoef
     s_out = s; q_out = q;
   } else {
     // float fields: exact products and compensated sums (site_terms_f2), the three partial
-    // sums combined in double
+    // sums combined in double (K here is the neighbour-product sum C)
     AccF2 K, P2, P4;
     for (int x = t; x < D; x += TPP) {
       const int cr = c == L - 1 ? 0 : c + 1, rd = r == L - 1 ? 0 : r + 1;
@@ -47,7 +47,7 @@ PHI4_DEV void site_sums(const T* __restrict__ row, int L, int D, int t, SiteCoef
       if (c >= L) { c -= L; ++r; }
     }
     const double p2 = P2.value();
-    s_out = (double)k.ck * K.value() + (double)k.cm * p2 + (double)k.lm * P4.value();
+    s_out = action_from_sums(K.value(), p2, P4.value(), k.ck, k.cm, k.lm);
     q_out = p2;
   }
 }
@@ -403,8 +403,8 @@ PHI4_DEV int accept_decision_bits(uint32_t w0, uint32_t w1, double log_alpha) {
 
 // Float fields with L % 4 == 0: each thread owns float4 groups of four sites of one
 // lattice row (kept in registers), reads the down neighbour group and the right end
-// neighbour from the staged row, and sums the bond-form site terms with exact products
-// and compensated float sums (site_terms_f2); the sums travel as float pairs through the
+// neighbour from the staged row, and sums the site terms with exact products and
+// compensated float sums (site_terms_f2); the sums travel as float pairs through the
 // warp and CTA trees and are combined into S and |phi|^2 in double, so S of the float
 // fields is exact to about 2^-48 relative. The proposal is either a float row `prop` or
 // phi + delta with delta an fp16 increment (the tensor-core proposal's epilogue output). The block holds PPB particles of TPP threads each (PPB <= 8,
@@ -456,7 +456,8 @@ PHI4_DEV void accept_vec_body(int PPB, int TPP, int i0, int N, int rot, float* _
     uwords[g] = make_uint2(w.x, w.y);
   }
   __syncthreads();
-  // exact products and compensated float sums of the bond-form site terms (site_terms_f2):
+  // exact products and compensated float sums of the site terms (site_terms_f2; K holds the
+  // neighbour-product sum C):
   // per thread, then per warp in float pairs; the decision warp adds the warps' pairs and
   // forms S and |phi|^2 in double
   AccF2 K, P2, P4;
@@ -498,7 +499,7 @@ PHI4_DEV void accept_vec_body(int PPB, int TPP, int i0, int N, int rot, float* _
     f2 = warp_sum_f2(f2);
     if (lane == 0) {
       const double Qp = q2.value();
-      const double Sp = p.c_kin * k2.value() + (p.c_mass * p.m2) * Qp + p.lam * f2.value();
+      const double Sp = action_from_sums(k2.value(), Qp, f2.value(), p.c_kin, p.c_mass * p.m2, p.lam);
       const double beta = *beta_ptr;
       const double dS = Sp - S[i], dq2 = Qp - sq[i];
       const double log_alpha = keep_ref ? (-beta * dS - 0.5 * dq2) : (-beta * dS - (1.0 - beta) * 0.5 * dq2);

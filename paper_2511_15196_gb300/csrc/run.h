@@ -51,7 +51,12 @@ struct phi4_run {
   phi4::LaunchTimer upd_timer;  // the tensor-core trailing-update launches (STG_CHOL_UPDATE)
   // pipelined sweeps of the mixed form: normals and proposal GEMM of sweep t+1 run on
   // their own streams while sweep t's accept runs on `stream`
-  void* Z2 = nullptr;                 // second normals buffer
+  void* Z2 = nullptr;                 // second normals buffer (ring slot 1)
+  // ring of normals buffers of the pipelined sweeps: slot s % n_zslots holds sweep s's
+  // normals (slot 0 is Z, slot 1 is Z2); up to kZRing sweeps are drawn ahead, during the
+  // temperature's refit; ev_nz[slot] marks a slot's normals drawn, ev_gz[slot] its GEMM done
+  int n_zslots = 0;
+  std::vector<cudaEvent_t> ev_nz, ev_gz;
   // accept (the fields' chain, highest priority), GEMM, normals (lowest priority)
   cudaStream_t s_norm = nullptr, s_gemm = nullptr, s_acc = nullptr;
   cudaEvent_t ev_done = nullptr;
