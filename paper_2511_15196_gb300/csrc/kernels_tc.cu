@@ -391,7 +391,13 @@ static bool make_map(CUtensorMap* map, const void* ptr, int inner, int rows, int
 static cudaError_t launch(const CUtensorMap& a, const CUtensorMap& b, const Params& p, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   if (e != cudaSuccess) return e;
-  const int grid = std::min(sm_count(), p.num_tiles);
+  // persistent CTAs: one per SM, or PHI4_PROPOSE_CTAS of them (the SMs left over then run
+  // the accept of the previous sweep, which overlaps the GEMM on another stream)
+  static const int ctas = [] {
+    const char* v = getenv("PHI4_PROPOSE_CTAS");
+    return v ? std::max(1, atoi(v)) : 0;
+  }();
+  const int grid = std::min(ctas > 0 ? std::min(ctas, sm_count()) : sm_count(), p.num_tiles);
   if (grid < 1) return cudaSuccess;
   tc_gemm_kernel<<<grid, NUM_THREADS, SMEM_BYTES, s>>>(a, b, p);
   return cudaGetLastError();
