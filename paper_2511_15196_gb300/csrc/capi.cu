@@ -203,6 +203,30 @@ phi4_status status_to_error(uint32_t st) {
 // starts at chol_jitter_rel * 10^level * trace / D with the level that succeeded at
 // the previous outer step, and grows x10 per failed try (up to 6 tries).
 // refit_enqueue: covariance, ridge and the first factorisation attempt (no host sync).
+// The proposal normals of a temperature's first sweeps do not depend on the fields: the
+// pipelined mixed form draws them on its lowest-priority stream beside the Cholesky (whose
+// chain leaves most SMs' issue slots free), after the covariance; the previous
+// temperature's GEMMs, which read the ring's slots, finished before this stream's point.
+static phi4_status draw_normals_ahead(phi4_run* r) {
+  const phi4_config& c = r->cfg;
+  if (!(c.kind == PHI4_SMC_RW && c.precision == PHI4_MIXED_BF16 && c.L % 4 == 0 && r->Z2 && r->s_norm) ||
+      r->owner)
+    return PHI4_OK;  // batch members draw their normals in the batch's own sweeps
+  CUDA_TRY(cudaEventRecord(r->ev_start, r->stream));
+  CUDA_TRY(cudaStreamWaitEvent(r->s_norm, r->ev_start, 0));
+  const size_t zslot = (size_t)c.N * r->ldz * 2;
+  LaunchTimer* tn = r->timing ? &r->norm_timer : nullptr;
+  for (int sweep = 0; sweep < std::min(c.n_mcmc, r->n_zslots); ++sweep) {
+    cudaEvent_t a0 = tn ? tn->begin(r->s_norm) : nullptr;
+    CUDA_TRY(launch_normals(c.seed, c.stream_id, RNG_PROPOSE, (uint32_t)r->t, (uint32_t)sweep, 0, c.N, r->D, r->ldz,
+                            r->zdtype, (unsigned char*)r->Z + (size_t)sweep * zslot, r->s_norm));
+    if (tn) tn->end(r->s_norm, a0);
+    CUDA_TRY(cudaEventRecord(r->ev_nz[sweep], r->s_norm));
+    r->kernel_launches += 1;
+  }
+  return PHI4_OK;
+}
+
 phi4_status refit_enqueue(phi4_run* r, const void* pts, int n_pts) {
   const int D = r->D;
   cudaStream_t s = r->stream;
@@ -216,6 +240,8 @@ phi4_status refit_enqueue(phi4_run* r, const void* pts, int n_pts) {
     CUDA_TRY(launch_ridge(r->sigma, D, r->cfg.chol_jitter_rel * pow(10.0, r->ridge_level), r->scal + SC_RIDGE, s));
     r->kernel_launches += 4;
   }
+  phi4_status ps = draw_normals_ahead(r);
+  if (ps != PHI4_OK) return ps;
   return factor_attempt(r);
 }
 
@@ -310,24 +336,6 @@ phi4_status step_front(phi4_run* r, bool single_cta_bisect) {
   cudaStream_t s = r->stream;
   const uint32_t t = (uint32_t)(++r->t);
   double* out = r->scal + SC_OUT;
-  if (c.kind == PHI4_SMC_RW && c.precision == PHI4_MIXED_BF16 && c.L % 4 == 0 && r->Z2 && r->s_norm) {
-    // the proposal normals of the temperature's first sweeps do not depend on the fields:
-    // draw them now, on the lowest-priority stream, while the bisection, resampling and
-    // refit run (the previous temperature's GEMMs, which read the slots, finished before
-    // this stream's current point)
-    CUDA_TRY(cudaEventRecord(r->ev_start, s));
-    CUDA_TRY(cudaStreamWaitEvent(r->s_norm, r->ev_start, 0));
-    const size_t zslot = (size_t)N * r->ldz * 2;
-    LaunchTimer* tn = r->timing ? &r->norm_timer : nullptr;
-    for (int sweep = 0; sweep < std::min(c.n_mcmc, r->n_zslots); ++sweep) {
-      cudaEvent_t a0 = tn ? tn->begin(r->s_norm) : nullptr;
-      CUDA_TRY(launch_normals(c.seed, c.stream_id, RNG_PROPOSE, t, (uint32_t)sweep, 0, N, D, r->ldz, r->zdtype,
-                              (unsigned char*)r->Z + (size_t)sweep * zslot, r->s_norm));
-      if (tn) tn->end(r->s_norm, a0);
-      CUDA_TRY(cudaEventRecord(r->ev_nz[sweep], r->s_norm));
-      r->kernel_launches += 1;
-    }
-  }
   {
     StageScope sc(r, STG_BISECT);
     CUDA_TRY(launch_bisect(r->ell, N, r->scal + SC_BETA, c.ess_target, c.bisect_iters, r->w, out, r->bisect_scratch,
