@@ -136,6 +136,20 @@ CASES = [
     ("ridge level not carried to the next step", "oracle.covariance",
      [("for _ in range(start_level):", "for _ in range(0):")],
      [P(t_cov.test_regularised_cholesky_rank_deficient)]),
+    ("Gaussian-part covariance: reference weight 1 - beta when it is kept", "oracle.covariance",
+     [("a = 1.0 if keep_reference else 1.0 - beta", "a = 1.0 - beta")],
+     [P(t_cov.test_gaussian_part_covariance_inverts_the_hessian_of_the_tempered_target, L=4, beta=0.7,
+        keep=True)]),
+    ("Gaussian-part covariance: the factor 2 of the quadratic form dropped", "oracle.covariance",
+     [("P = a * np.eye(D) + 2.0 * beta * (c_kin * K + c_mass * m2 * np.eye(D))",
+       "P = a * np.eye(D) + beta * (c_kin * K + c_mass * m2 * np.eye(D))")],
+     [P(t_cov.test_gaussian_part_covariance_inverts_the_hessian_of_the_tempered_target, L=3, beta=1.0,
+        keep=False), P(t_cov.test_gaussian_part_covariance_spectrum_is_the_closed_form)]),
+    ("Gaussian-part covariance: one neighbour direction only", "oracle.covariance",
+     [("for rr, cc in (((r + 1) % L, c), ((r - 1) % L, c), (r, (c + 1) % L), (r, (c - 1) % L)):",
+       "for rr, cc in (((r + 1) % L, c), ((r - 1) % L, c)):")],
+     [P(t_cov.test_gaussian_part_covariance_inverts_the_hessian_of_the_tempered_target, L=4, beta=0.7,
+        keep=True), P(t_cov.test_gaussian_part_covariance_spectrum_is_the_closed_form)]),
     # ---- SMC driver ----
     ("resampling skipped after reweighting", "oracle.smc",
      [("self.phi, self.S, self.sq = self.phi[anc], self.S[anc], self.sq[anc]", "pass")],
