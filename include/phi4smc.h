@@ -229,8 +229,9 @@ phi4_status smc_load_particles(phi4_run* run, const void* src, size_t bytes);
  * particle, the run's scalar block (Kahan pair of log Z, beta, NS bookkeeping) and the
  * nested-sampling dead points. smc_restore_state into a run created with the identical
  * configuration (checked) continues bit for bit as the saved run would have; the
- * counters are restored too. Both synchronise the run's stream. Not for batch handles
- * (save and restore the members). */
+ * counters are restored too. Both synchronise the run's stream. A batch handle has no single
+ * state; a batch member can be saved but not restored (its buffers follow the batch's
+ * steps). */
 phi4_status phi4_state_bytes(const phi4_run* run, size_t* bytes);
 phi4_status smc_save_state(const phi4_run* run, void* host_dst, size_t bytes);
 phi4_status smc_restore_state(phi4_run* run, const void* host_src, size_t bytes);

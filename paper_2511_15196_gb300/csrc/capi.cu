@@ -827,7 +827,8 @@ phi4_status smc_save_state(const phi4_run* rc, void* host_dst, size_t bytes) {
 
 phi4_status smc_restore_state(phi4_run* r, const void* host_src, size_t bytes) {
   ARG_CHECK(r && host_src, "NULL argument");
-  ARG_CHECK(!r->batch, "a batch handle has no single state (restore its members)");
+  ARG_CHECK(!r->batch, "a batch handle has no single state");
+  ARG_CHECK(!r->owner, "a batch member's buffers follow the batch's steps: it cannot be restored");
   ARG_CHECK(bytes >= sizeof(StateHeader), "state buffer of %zu bytes is too small", bytes);
   StateHeader h;
   memcpy(&h, host_src, sizeof(h));
