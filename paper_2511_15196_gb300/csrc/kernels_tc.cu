@@ -24,13 +24,15 @@
 namespace phi4 {
 namespace tc {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;  // the grouped (batched) kernel's ring
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int TMEM_COLS = 2 * BN;
 constexpr int NUM_THREADS = 192;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* alignment */ + 256 /* barriers */;
+// shared memory of a ring of S stages
+__host__ __device__ constexpr int smem_bytes(int S) { return S * STAGE_BYTES + 1024 + 256; }
 
 // kind::f16 instruction descriptor: D fp32 (bits 4-5 = 1), A and B bf16 (bits 7-9,
 // 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
@@ -197,13 +199,13 @@ struct GroupedTiles {
 
 // Persistent CTAs (one per SM) walk units cid, cid + grid, ...; warp 0 = TMA producer,
 // warp 1 = MMA issuer and TMEM owner, warps 2..5 = epilogue (s * acc -> fp16 Delta).
-template <class Tiles>
+template <int S, class Tiles>
 PHI4_DEV void gemm_body(const Tiles& tiles, int num_units, uint32_t* status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-  uint64_t* empty = full + STAGES;
-  uint64_t* tfull = empty + STAGES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * STAGE_BYTES);
+  uint64_t* empty = full + S;
+  uint64_t* tfull = empty + S;
   uint64_t* tempty = tfull + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -211,7 +213,7 @@ PHI4_DEV void gemm_body(const Tiles& tiles, int num_units, uint32_t* status) {
   const int cid = blockIdx.x, ncl = gridDim.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -257,7 +259,7 @@ PHI4_DEV void gemm_body(const Tiles& tiles, int num_units, uint32_t* status) {
           mbar_expect_tx(&full[stage], STAGE_BYTES);
           tma_load_2d(t.ma, &full[stage], sa, kb * BK, t.mb * BM);
           tma_load_2d(t.mb_map, &full[stage], sa + A_BYTES, kb * BK, t.nb * BN);
-          if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+          if (++stage == S) { stage = 0; phase ^= 1u; }
         }
       }
     }
@@ -280,7 +282,7 @@ PHI4_DEV void gemm_body(const Tiles& tiles, int num_units, uint32_t* status) {
           for (int kk = 0; kk < BK / 16; ++kk)
             umma_bf16(d_tmem, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), (kb | kk) != 0);
           umma_commit(&empty[stage]);
-          if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+          if (++stage == S) { stage = 0; phase ^= 1u; }
         }
         if (!ok) break;
         umma_commit(&tfull[acc]);
@@ -344,17 +346,18 @@ PHI4_DEV void gemm_body(const Tiles& tiles, int num_units, uint32_t* status) {
   }
 }
 
+template <int S>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Params p) {
   SingleTiles tiles{&tmA, &tmB, &p};
-  gemm_body(tiles, p.num_tiles, p.status);
+  gemm_body<S>(tiles, p.num_tiles, p.status);
 }
 
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_gemm_grouped_kernel(const GemmRun* __restrict__ runs, int R, int num_units, uint32_t sweep,
                            uint32_t* status) {
   GroupedTiles tiles{runs, R, sweep};
-  gemm_body(tiles, num_units, status);
+  gemm_body<STAGES>(tiles, num_units, status);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -388,9 +391,14 @@ static bool make_map(CUtensorMap* map, const void* ptr, int inner, int rows, int
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Ring depth of the single-run proposal GEMM: 3 stages (144 KB of shared memory) leave room
+// on each SM for the fused accept of the previous sweep, which runs beside it on another
+// stream; PHI4_PROPOSE_STAGES=4 selects the deeper ring (192 KB).
 static cudaError_t launch(const CUtensorMap& a, const CUtensorMap& b, const Params& p, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-  if (e != cudaSuccess) return e;
+  static const int stages = [] {
+    const char* v = getenv("PHI4_PROPOSE_STAGES");
+    return (v && atoi(v) == 4) ? 4 : 3;
+  }();
   // persistent CTAs: one per SM, or PHI4_PROPOSE_CTAS of them (the SMs left over then run
   // the accept of the previous sweep, which overlaps the GEMM on another stream)
   static const int ctas = [] {
@@ -399,7 +407,15 @@ static cudaError_t launch(const CUtensorMap& a, const CUtensorMap& b, const Para
   }();
   const int grid = std::min(ctas > 0 ? std::min(ctas, sm_count()) : sm_count(), p.num_tiles);
   if (grid < 1) return cudaSuccess;
-  tc_gemm_kernel<<<grid, NUM_THREADS, SMEM_BYTES, s>>>(a, b, p);
+  if (stages == 4) {
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(4));
+    if (e != cudaSuccess) return e;
+    tc_gemm_kernel<4><<<grid, NUM_THREADS, smem_bytes(4), s>>>(a, b, p);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(3));
+    if (e != cudaSuccess) return e;
+    tc_gemm_kernel<3><<<grid, NUM_THREADS, smem_bytes(3), s>>>(a, b, p);
+  }
   return cudaGetLastError();
 }
 
