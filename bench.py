@@ -276,7 +276,8 @@ def peaks():
 
 def kernel_traffic(kernel):
     """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or None when the
-    kernel's source changed since the counters were taken."""
+    kernel's source changed since the counters were taken (the hash covers the source
+    section that holds the kernel: from the line `section_begin` to `section_end`)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
@@ -284,7 +285,16 @@ def kernel_traffic(kernel):
     if not d:
         return None
     src = os.path.join(ROOT, d["source"])
-    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != d["sha256_16"]:
+    if not os.path.exists(src):
+        return None
+    text = open(src, "rb").read()
+    if "section_begin" in d:
+        a = text.find(d["section_begin"].encode())
+        b = text.find(d["section_end"].encode(), a + 1)
+        if a < 0 or b < 0:
+            return None
+        text = text[a:b]
+    if hashlib.sha256(text).hexdigest()[:16] != d["sha256_16"]:
         return None
     return d["bytes_per_launch"]
 
