@@ -120,3 +120,25 @@ def test_batch_graph_sweeps_and_tuning_cache(tmp_path, monkeypatch):
         s.close()
     a.close()
     b.close()
+
+
+def test_batch_mixed_members_with_and_without_the_batched_sweeps():
+    # mixed-form members with L % 4 != 0 (10 x 10, 6 x 6) take their own streams' sweeps while
+    # the L % 4 == 0 ones take the batched graph sweeps; a single member and one particle
+    # block short of full (N = 1001) are covered; every member follows its single run
+    shapes = [(10, 600), (8, 1001), (6, 256), (16, 2048)]
+    cfgs = [p.Config(L=L, N=N, m2=-4.0, lam=8.0, precision=p.MIXED_BF16, n_mcmc=4, seed=90 + r)
+            for r, (L, N) in enumerate(shapes)]
+    for group in (cfgs, cfgs[1:2]):
+        batch = p.Batch(group)
+        singles = [p.Run(c) for c in group]
+        for _ in range(3):
+            batch.temper_step()
+            for s in singles:
+                s.temper_step()
+        for m, s in zip(batch.members, singles):
+            assert m.log_evidence()[0] == pytest.approx(s.log_evidence()[0], rel=1e-9, abs=1e-9)
+            assert np.abs(m.particles().cpu().numpy() - s.particles().cpu().numpy()).max() < 1e-4
+            assert m.observables()["n_steps"] == 3
+            s.close()
+        batch.close()

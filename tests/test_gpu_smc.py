@@ -332,6 +332,21 @@ def test_free_field_closed_form_each_form_with_the_free_kernel_covariance(precis
 
 
 @pytest.mark.slow
+def test_free_field_closed_form_mixed_form_at_the_32x32_size():
+    # the precision-check lattice itself (32 x 32, m2 = 1, N = 4096) in a setting where the
+    # sampler mixes: ESS 0.9 N, 640 sweeps per temperature, the exact Gaussian kernel
+    # covariance; the bf16-GEMM form's mean log Zhat + Var/2 over 32 seeds lands on the closed
+    # form -185.9853908122 within four of its errors (about 3.5 s per run)
+    lz = _gpu_runs(32, L=32, N=4096, m2=1.0, lam=0.0, ess_target=0.9, n_mcmc=640, precision=p.MIXED_BF16,
+                   flags=p.FLAG_FREE_KERNEL_COV)[:, 0]
+    est, err = _logz_plus_half_var(lz)
+    exact = cf.free_field_logz(32, 1.0)
+    print("free field L=32, mixed: log Zhat mean %.4f sd %.4f; mean + var/2 - exact = %+.4f (err %.4f)"
+          % (lz.mean(), lz.std(ddof=1), est - exact, err))
+    assert abs(est - exact) < 4.0 * err + 0.01
+
+
+@pytest.mark.slow
 def test_free_field_precision_forms_32_seeds():
     # the precision-check workload as configured: free field (lambda = 0, m2 = 1), L = 32
     # (D = 1024), N = 4096, ESS 0.5 N, 10 sweeps, the population's covariance. The three
