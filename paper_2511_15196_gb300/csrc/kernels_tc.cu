@@ -817,21 +817,26 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const int buf = it & 1;
       int mb, bj;
       get_tile(p, u, mb, bj);
-      if (!mbar_wait(tfull + buf, (tph >> buf) & 1u, abort_flag)) { give_up(); break; }
-      tc_fence_after();
       const int ir = mb * BM + r;  // row inside the trailing matrix
       const bool row_ok = ir < p.m;
-      const int ei = row_ok ? p.rexp[ir] : 0;
-      const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * ACC_COLS + grp * 16);
       double* arow = p.a + (size_t)(p.b0 + (row_ok ? ir : 0)) * p.D + p.b0;
       const int jc0 = bj * BN + grp * 16;
-      // prefetch the FP64 targets while the accumulators are combined
+      // load the FP64 targets and the exponents before waiting for the tile's products:
+      // the loads run while the MMAs finish and the accumulators are combined (no other
+      // tile of this launch, and no launch still running, writes these elements)
+      const int ei = row_ok ? p.rexp[ir] : 0;
       double av[16];
+      int ej[16];
 #pragma unroll
       for (int t = 0; t < 16; ++t) {
         const int jc = jc0 + t;
-        av[t] = (row_ok && jc < p.m && jc <= ir) ? arow[jc] : 0.0;
+        const bool on = row_ok && jc < p.m && jc <= ir;
+        av[t] = on ? arow[jc] : 0.0;
+        ej[t] = on ? p.rexp[jc] : 0;
       }
+      if (!mbar_wait(tfull + buf, (tph >> buf) & 1u, abort_flag)) { give_up(); break; }
+      tc_fence_after();
+      const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * ACC_COLS + grp * 16);
       float hi[16], lo[16];
       // (hi, lo) <- (hi, lo) 2^-7 + U  in double-float (TwoSum, then renormalise)
       auto horner = [&](const uint32_t(&ur)[16]) {
@@ -878,7 +883,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         for (int t = 0; t < 16; ++t) {
           const int jc = jc0 + t;
           if (jc < p.m && jc <= ir) {
-            const int n = ei + p.rexp[jc] - 14;
+            const int n = ei + ej[t] - 14;
             double v;
             // every partial is a multiple of 2^-42 below 2^24: for |n| < 900 both
             // halves scale to normal doubles exactly
