@@ -644,8 +644,12 @@ namespace emu {
 constexpr int BM = 128, BN = 32, KD = 64, ND = 8, NC = 8;
 constexpr int A_PLANE = BM * KD * 2;
 constexpr int B_PLANE = BN * KD * 2;
-constexpr int SMEM_DATA = ND * (A_PLANE + B_PLANE);  // 160 KB: leaves room on the SM for the panel kernels
-constexpr int SMEM_BYTES = SMEM_DATA + 1024 + 256;
+constexpr int SMEM_DATA = ND * (A_PLANE + B_PLANE);  // 160 KB
+constexpr int NUM_EPI_WARPS = 8;
+// per epilogue warp a 32 x 16 FP64 patch that turns its row-per-lane products into
+// row-contiguous half-warp accesses of the trailing matrix (coalesced loads and stores)
+constexpr int STAGE_BYTES = NUM_EPI_WARPS * 32 * 16 * 8;
+constexpr int SMEM_BYTES = SMEM_DATA + 256 + STAGE_BYTES + 1024;
 constexpr int ACC_COLS = NC * BN;  // one tile's eight group accumulators; two tiles fit in TMEM
 constexpr int BLK_COLS = KD / BN;  // tile columns per 64-column block
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
@@ -727,13 +731,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   uint64_t* tempty = full + 4;  // [2]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(full + 6);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  double* stage = reinterpret_cast<double*>(smem + SMEM_DATA + 256);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     mbar_init(full, 1);
     mbar_init(empty, 1);
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull + b, 1);
-      mbar_init(tempty + b, 8);
+      mbar_init(tempty + b, NUM_EPI_WARPS);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -808,32 +813,40 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       }
     }
   } else {
-    // two epilogue warpgroups: warps 2..5 take columns 0..15 of the tile, warps 6..9 columns 16..31
+    // two epilogue warpgroups: warps 2..5 take columns 0..15 of the tile, warps 6..9 columns 16..31.
+    // A lane holds one row's products (the TMEM lane); the trailing matrix is read and
+    // written through the warp's staging patch with a half-warp per row segment: pass k
+    // covers rows 2k and 2k + 1 of the warp's 32, lane (h, c) = (lane / 16, lane % 16)
+    // row 2k + h and column c.
     const int q = warp & 3, grp = (warp - 2) >> 2;
     const int r = q * 32 + lane;
+    const int hl = lane >> 4, cl = lane & 15;
+    double* stg = stage + (warp - 2) * 32 * 16;  // element (row, col) at row * 16 + (col ^ (row & 15))
     uint32_t tph = 0;
     int it = 0;
     for (int u = u_lo; u < u_hi; ++u, ++it) {
       const int buf = it & 1;
       int mb, bj;
       get_tile(p, u, mb, bj);
-      const int ir = mb * BM + r;  // row inside the trailing matrix
+      const int ir = mb * BM + r;  // this lane's row of products inside the trailing matrix
       const bool row_ok = ir < p.m;
-      double* arow = p.a + (size_t)(p.b0 + (row_ok ? ir : 0)) * p.D + p.b0;
       const int jc0 = bj * BN + grp * 16;
+      const int jc = jc0 + cl;  // this lane's column in the row-segment passes
+      const int ir0 = mb * BM + q * 32 + hl;  // its row in pass 0 (pass k: ir0 + 2k)
+      double* aseg = p.a + (size_t)(p.b0 + min(ir0, p.m - 1)) * p.D + p.b0 + jc;
       // load the FP64 targets and the exponents before waiting for the tile's products:
       // the loads run while the MMAs finish and the accumulators are combined (no other
       // tile of this launch, and no launch still running, writes these elements)
       const int ei = row_ok ? p.rexp[ir] : 0;
+      const int ejl = jc < p.m ? p.rexp[jc] : 0;  // exponent of column jc0 + (lane % 16)
       double av[16];
-      int ej[16];
 #pragma unroll
-      for (int t = 0; t < 16; ++t) {
-        const int jc = jc0 + t;
-        const bool on = row_ok && jc < p.m && jc <= ir;
-        av[t] = on ? arow[jc] : 0.0;
-        ej[t] = on ? p.rexp[jc] : 0;
+      for (int k = 0; k < 16; ++k) {
+        const int irk = ir0 + 2 * k;
+        const bool on = irk < p.m && jc < p.m && jc <= irk;
+        av[k] = on ? aseg[(size_t)(2 * k) * p.D] : 0.0;
       }
+
       if (!mbar_wait(tfull + buf, (tph >> buf) & 1u, abort_flag)) { give_up(); break; }
       tc_fence_after();
       const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * ACC_COLS + grp * 16);
@@ -878,24 +891,33 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty + buf);  // the accumulators are in registers now
       tph ^= 1u << buf;
-      if (row_ok) {
+      // the products (P P^T)_ij of this lane's row into the patch (values of rows and
+      // columns outside the matrix are never stored)
 #pragma unroll
-        for (int t = 0; t < 16; ++t) {
-          const int jc = jc0 + t;
-          if (jc < p.m && jc <= ir) {
-            const int n = ei + ej[t] - 14;
-            double v;
-            // every partial is a multiple of 2^-42 below 2^24: for |n| < 900 both
-            // halves scale to normal doubles exactly
-            if (n > -900 && n < 900) {
-              v = f2d_pow2(hi[t], n) + f2d_pow2(lo[t], n);
-            } else {
-              v = ((double)hi[t] + (double)lo[t]) * pow2(n);
-            }
-            arow[jc] = av[t] - v;
-          }
+      for (int t = 0; t < 16; ++t) {
+        const int n = ei + __shfl_sync(0xffffffffu, ejl, t) - 14;
+        double v;
+        // every partial is a multiple of 2^-42 below 2^24: for |n| < 900 both
+        // halves scale to normal doubles exactly
+        if (n > -900 && n < 900) {
+          v = f2d_pow2(hi[t], n) + f2d_pow2(lo[t], n);
+        } else {
+          v = ((double)hi[t] + (double)lo[t]) * pow2(n);
         }
+        stg[lane * 16 + (t ^ (lane & 15))] = v;
       }
+      __syncwarp();
+      // the pass stride, opaque to the compiler so that the sixteen row addresses are
+      // recomputed here rather than held in registers since the loads
+      long long pstride;
+      asm volatile("mov.b64 %0, %1;" : "=l"(pstride) : "l"(2ll * p.D));
+      double* dst = aseg;
+#pragma unroll
+      for (int k = 0; k < 16; ++k, dst += pstride) {
+        const int rr = 2 * k + hl, irk = ir0 + 2 * k;
+        if (irk < p.m && jc < p.m && jc <= irk) *dst = av[k] - stg[rr * 16 + (cl ^ (rr & 15))];
+      }
+      __syncwarp();  // the patch is read before the next tile writes it
     }
   }
   tc_fence_before();
