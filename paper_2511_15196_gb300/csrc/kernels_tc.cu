@@ -645,11 +645,17 @@ constexpr int BM = 128, BN = 32, KD = 64, ND = 8, NC = 8;
 constexpr int A_PLANE = BM * KD * 2;
 constexpr int B_PLANE = BN * KD * 2;
 constexpr int SMEM_DATA = ND * (A_PLANE + B_PLANE);  // 160 KB
-constexpr int NUM_EPI_WARPS = 8;
-// per epilogue warp a 32 x 16 FP64 patch that turns its row-per-lane products into
-// row-contiguous half-warp accesses of the trailing matrix (coalesced loads and stores)
-constexpr int STAGE_BYTES = NUM_EPI_WARPS * 32 * 16 * 8;
+constexpr int EC = 8;                         // tile columns per epilogue warp
+constexpr int RPP = 32 / EC;                  // rows per pass of the row-segment accesses
+constexpr int NUM_EPI_WARPS = 4 * (BN / EC);  // four TMEM lane quarters x column groups
+// per epilogue warp a 32 x EC FP64 patch that turns its row-per-lane products into
+// row-contiguous accesses of EC lanes to the trailing matrix (coalesced loads and stores);
+// element (row, col) at row EC + (col ^ swz(row)), free of bank conflicts both ways
+constexpr int STAGE_BYTES = NUM_EPI_WARPS * 32 * EC * 8;
+PHI4_DEV int swz(int row) { return (row >> 1) & 7; }
+static_assert(EC == 8, "swz is laid out for eight columns per warp");
 constexpr int SMEM_BYTES = SMEM_DATA + 256 + STAGE_BYTES + 1024;
+static_assert(SMEM_BYTES <= 227 * 1024, "shared memory of one CTA");
 constexpr int ACC_COLS = NC * BN;  // one tile's eight group accumulators; two tiles fit in TMEM
 constexpr int BLK_COLS = KD / BN;  // tile columns per 64-column block
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
@@ -663,23 +669,13 @@ struct Params {
   uint32_t* status;
 };
 
-// tcgen05.ld of 16 columns without the wait (the caller issues tmem_wait_ld before use)
-PHI4_DEV void tmem_ld16_nw(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+// tcgen05.ld of 8 columns without the wait (the caller issues tmem_wait_ld before use)
+PHI4_DEV void tmem_ld8_nw(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
                : "r"(taddr));
 }
 PHI4_DEV void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-PHI4_DEV void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-               : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 // Tile u of the launch's list: 128-row bands from the top, in each the lower tiles
 // whose column lies in [col_lo, col_hi).
@@ -715,7 +711,7 @@ PHI4_DEV double f2d_pow2(float x, int n) {
   return __longlong_as_double((long long)(sign | ex | man));
 }
 
-constexpr int NUM_THREADS = 320;  // TMA warp, MMA warp, two epilogue warpgroups
+constexpr int NUM_THREADS = 64 + 32 * NUM_EPI_WARPS;  // TMA warp, MMA warp, epilogue warps
 
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     chol_update_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Params p) {
@@ -813,15 +809,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       }
     }
   } else {
-    // two epilogue warpgroups: warps 2..5 take columns 0..15 of the tile, warps 6..9 columns 16..31.
-    // A lane holds one row's products (the TMEM lane); the trailing matrix is read and
-    // written through the warp's staging patch with a half-warp per row segment: pass k
-    // covers rows 2k and 2k + 1 of the warp's 32, lane (h, c) = (lane / 16, lane % 16)
-    // row 2k + h and column c.
+    // NUM_EPI_WARPS epilogue warps: warp w >= 2 reads TMEM lanes [32 (w % 4), 32 (w % 4) + 32)
+    // (rows of the tile) in columns [grp EC, grp EC + EC), grp = (w - 2) / 4. A lane holds one
+    // row's products (its TMEM lane); the trailing matrix is read and written through the
+    // warp's staging patch in row segments: in pass k, lane (h, c) = (lane / EC, lane % EC)
+    // takes row k RPP + h of the warp's 32 rows and column c, so EC lanes cover EC
+    // consecutive doubles of one row.
     const int q = warp & 3, grp = (warp - 2) >> 2;
     const int r = q * 32 + lane;
-    const int hl = lane >> 4, cl = lane & 15;
-    double* stg = stage + (warp - 2) * 32 * 16;  // element (row, col) at row * 16 + (col ^ (row & 15))
+    const int hl = lane / EC, cl = lane % EC;
+    double* stg = stage + (warp - 2) * 32 * EC;
     uint32_t tph = 0;
     int it = 0;
     for (int u = u_lo; u < u_hi; ++u, ++it) {
@@ -830,31 +827,31 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       get_tile(p, u, mb, bj);
       const int ir = mb * BM + r;  // this lane's row of products inside the trailing matrix
       const bool row_ok = ir < p.m;
-      const int jc0 = bj * BN + grp * 16;
+      const int jc0 = bj * BN + grp * EC;
       const int jc = jc0 + cl;  // this lane's column in the row-segment passes
-      const int ir0 = mb * BM + q * 32 + hl;  // its row in pass 0 (pass k: ir0 + 2k)
+      const int ir0 = mb * BM + q * 32 + hl;  // its row in pass 0 (pass k: ir0 + k RPP)
       double* aseg = p.a + (size_t)(p.b0 + min(ir0, p.m - 1)) * p.D + p.b0 + jc;
       // load the FP64 targets and the exponents before waiting for the tile's products:
       // the loads run while the MMAs finish and the accumulators are combined (no other
       // tile of this launch, and no launch still running, writes these elements)
       const int ei = row_ok ? p.rexp[ir] : 0;
-      const int ejl = jc < p.m ? p.rexp[jc] : 0;  // exponent of column jc0 + (lane % 16)
-      double av[16];
+      const int ejl = jc < p.m ? p.rexp[jc] : 0;  // exponent of column jc0 + (lane % EC)
+      double av[EC];
 #pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const int irk = ir0 + 2 * k;
+      for (int k = 0; k < EC; ++k) {
+        const int irk = ir0 + k * RPP;
         const bool on = irk < p.m && jc < p.m && jc <= irk;
-        av[k] = on ? aseg[(size_t)(2 * k) * p.D] : 0.0;
+        av[k] = on ? aseg[(size_t)(k * RPP) * p.D] : 0.0;
       }
 
       if (!mbar_wait(tfull + buf, (tph >> buf) & 1u, abort_flag)) { give_up(); break; }
       tc_fence_after();
-      const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * ACC_COLS + grp * 16);
-      float hi[16], lo[16];
+      const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * ACC_COLS + grp * EC);
+      float hi[EC], lo[EC];
       // (hi, lo) <- (hi, lo) 2^-7 + U  in double-float (TwoSum, then renormalise)
-      auto horner = [&](const uint32_t(&ur)[16]) {
+      auto horner = [&](const uint32_t(&ur)[EC]) {
 #pragma unroll
-        for (int t = 0; t < 16; ++t) {
+        for (int t = 0; t < EC; ++t) {
           const float uu = __uint_as_float(ur[t]);
           const float h = hi[t] * 0.0078125f, l = lo[t] * 0.0078125f;
           const float s = h + uu;
@@ -868,20 +865,20 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       };
       {
         // the eight group accumulators U_9 .. U_2, two loads in flight per wait
-        uint32_t r0[16], r1[16];
-        tmem_ld16_nw(trow + (uint32_t)((NC - 1) * BN), r0);
-        tmem_ld16_nw(trow + (uint32_t)((NC - 2) * BN), r1);
+        uint32_t r0[EC], r1[EC];
+        tmem_ld8_nw(trow + (uint32_t)((NC - 1) * BN), r0);
+        tmem_ld8_nw(trow + (uint32_t)((NC - 2) * BN), r1);
         tmem_wait_ld();
 #pragma unroll
-        for (int t = 0; t < 16; ++t) {
+        for (int t = 0; t < EC; ++t) {
           hi[t] = __uint_as_float(r0[t]);
           lo[t] = 0.f;
         }
         horner(r1);
 #pragma unroll 1
         for (int g = NC - 3; g >= 0; g -= 2) {
-          tmem_ld16_nw(trow + (uint32_t)(g * BN), r0);
-          tmem_ld16_nw(trow + (uint32_t)((g - 1) * BN), r1);
+          tmem_ld8_nw(trow + (uint32_t)(g * BN), r0);
+          tmem_ld8_nw(trow + (uint32_t)((g - 1) * BN), r1);
           tmem_wait_ld();
           horner(r0);
           horner(r1);
@@ -891,31 +888,46 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty + buf);  // the accumulators are in registers now
       tph ^= 1u << buf;
-      // the products (P P^T)_ij of this lane's row into the patch (values of rows and
-      // columns outside the matrix are never stored)
+      // The products (P P^T)_ij of this lane's row into the patch (values of rows and
+      // columns outside the matrix are never stored). Every partial of (hi, lo) is a
+      // multiple of 2^-49 below 2^24 in magnitude. While the row and column exponents
+      // are moderate (the usual case, decided for the whole warp) the row's scale
+      // 2^(e_i - 14) is applied here and the column's 2^(e_j) in the passes, as an
+      // integer added to the exponent field: every value stays a normal double, so the
+      // power-of-two scalings commute with the rounding of hi + lo and the result is the
+      // one of scaling by 2^(e_i + e_j - 14) at once.
+      const bool split = __all_sync(0xffffffffu, ei > -386 && ei < 414 && ejl > -400 && ejl < 400);
+      if (split) {
+        const int n = ei - 14;
 #pragma unroll
-      for (int t = 0; t < 16; ++t) {
-        const int n = ei + __shfl_sync(0xffffffffu, ejl, t) - 14;
-        double v;
-        // every partial is a multiple of 2^-42 below 2^24: for |n| < 900 both
-        // halves scale to normal doubles exactly
-        if (n > -900 && n < 900) {
-          v = f2d_pow2(hi[t], n) + f2d_pow2(lo[t], n);
-        } else {
-          v = ((double)hi[t] + (double)lo[t]) * pow2(n);
+        for (int t = 0; t < EC; ++t) stg[lane * EC + (t ^ swz(lane))] = f2d_pow2(hi[t], n) + f2d_pow2(lo[t], n);
+      } else {
+#pragma unroll
+        for (int t = 0; t < EC; ++t) {
+          const int n = ei + __shfl_sync(0xffffffffu, ejl, t) - 14;
+          double v;
+          if (n > -900 && n < 900) {
+            v = f2d_pow2(hi[t], n) + f2d_pow2(lo[t], n);
+          } else {
+            v = ((double)hi[t] + (double)lo[t]) * pow2(n);
+          }
+          stg[lane * EC + (t ^ swz(lane))] = v;
         }
-        stg[lane * 16 + (t ^ (lane & 15))] = v;
       }
       __syncwarp();
-      // the pass stride, opaque to the compiler so that the sixteen row addresses are
-      // recomputed here rather than held in registers since the loads
+      const long long eadd = split ? (long long)ejl << 52 : 0ll;
+      // the pass stride, opaque to the compiler so that the row addresses are recomputed
+      // here rather than held in registers since the loads
       long long pstride;
-      asm volatile("mov.b64 %0, %1;" : "=l"(pstride) : "l"(2ll * p.D));
+      asm volatile("mov.b64 %0, %1;" : "=l"(pstride) : "l"((long long)RPP * p.D));
       double* dst = aseg;
 #pragma unroll
-      for (int k = 0; k < 16; ++k, dst += pstride) {
-        const int rr = 2 * k + hl, irk = ir0 + 2 * k;
-        if (irk < p.m && jc < p.m && jc <= irk) *dst = av[k] - stg[rr * 16 + (cl ^ (rr & 15))];
+      for (int k = 0; k < EC; ++k, dst += pstride) {
+        const int rr = k * RPP + hl, irk = ir0 + k * RPP;
+        if (irk < p.m && jc < p.m && jc <= irk) {
+          const long long wb = __double_as_longlong(stg[rr * EC + (cl ^ swz(rr))]);
+          *dst = av[k] - __longlong_as_double((wb << 1) ? wb + eadd : wb);
+        }
       }
       __syncwarp();  // the patch is read before the next tile writes it
     }
