@@ -373,9 +373,9 @@ def test_free_field_precision_forms_32_seeds():
                          ids=["pipelined_sweeps", "pipelined_ragged", "sequential_sweeps"])
 def test_mixed_runs_are_deterministic(L, N):
     # L % 4 == 0: the sweeps' normals, proposal GEMM and accept overlap on three streams
-    # with double-buffered normals and increments; a buffer reused before its reader
+    # with a ring of normals buffers and double-buffered increments; a buffer reused before its reader
     # finished would make two identical runs differ. L = 20, N = 300: D = 400 and an odd
-    # number of 128-row tiles (the GEMM's two-CTA clusters pad the last pair). L = 10
+    # number of 128-row tiles (a ragged last tile in the GEMM and the accept). L = 10
     # takes the sequential path.
     cfg = gpu_cfg(L=L, N=N, n_mcmc=6, precision=p.MIXED_BF16, seed=5)
     runs = [p.Run(cfg) for _ in range(2)]
