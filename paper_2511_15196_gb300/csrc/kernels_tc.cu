@@ -669,24 +669,32 @@ struct Params {
   uint32_t* status;
 };
 
-// tcgen05.ld of 8 columns without the wait (the caller issues tmem_wait_ld before use)
+// tcgen05.ld of 8 or 16 columns without the wait (the caller issues tmem_wait_ld before use)
 PHI4_DEV void tmem_ld8_nw(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+PHI4_DEV void tmem_ld16_nw(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
                : "r"(taddr));
 }
 PHI4_DEV void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Tile u of the launch's list: 128-row bands from the top, in each the lower tiles
 // whose column lies in [col_lo, col_hi).
+// Tile columns are TBN wide (p.tiles_n, p.col_lo and p.col_hi count them).
+template <int TBN>
 PHI4_DEV int band_tiles(const Params& p, int mb) {
-  const int hi = min(min(p.col_hi, p.tiles_n), (mb * BM + BM - 1) / BN + 1);
+  const int hi = min(min(p.col_hi, p.tiles_n), (mb * BM + BM - 1) / TBN + 1);
   return max(0, hi - p.col_lo);
 }
+template <int TBN>
 PHI4_DEV void get_tile(const Params& p, int u, int& mb, int& bj) {
   int m = 0, base = 0;
   for (;;) {
-    const int cnt = band_tiles(p, m);
+    const int cnt = band_tiles<TBN>(p, m);
     if (u < base + cnt) break;
     base += cnt;
     ++m;
@@ -764,7 +772,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       int prev_mb = -1;
       for (int u = u_lo; u < u_hi && !*abort_flag; ++u) {
         int mb, bj;
-        get_tile(p, u, mb, bj);
+        get_tile<BN>(p, u, mb, bj);
         if (!mbar_wait(empty, phase ^ 1u, abort_flag)) { give_up(); break; }
         // the band's A digit planes stay in shared memory while the band lasts
         const bool load_a = mb != prev_mb;
@@ -824,7 +832,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     for (int u = u_lo; u < u_hi; ++u, ++it) {
       const int buf = it & 1;
       int mb, bj;
-      get_tile(p, u, mb, bj);
+      get_tile<BN>(p, u, mb, bj);
       const int ir = mb * BM + r;  // this lane's row of products inside the trailing matrix
       const bool row_ok = ir < p.m;
       const int jc0 = bj * BN + grp * EC;
@@ -939,6 +947,263 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512) : "memory");
   }
 }
+// The bulk of a panel's update in 128 x 64 tiles. An N = 64 MMA reads its 4 KB A slice for
+// 64 output columns, half the shared-memory operand traffic per product of the 128 x 32
+// form (whose MMA issue is bound by those operand reads). A tile's eight group accumulators
+// then take all 512 TMEM columns, so the MMA warp and the epilogue hand them over group by
+// group: the MMAs produce U_9 (eight digit pairs) first and U_2 (one pair) last, the order
+// in which the epilogue's Horner pass consumes them, and the next tile's group g waits only
+// for every epilogue warp to have read this tile's group g.
+namespace wide {
+constexpr int TBN = 64;
+constexpr int B_PLANE = TBN * KD * 2;                      // 8 KB
+constexpr int SMEM_DATA = ND * (A_PLANE + B_PLANE);         // 192 KB
+constexpr int EC = 16;                                      // tile columns per epilogue warp
+constexpr int NUM_EPI_WARPS = 4 * (TBN / EC);               // four TMEM lane quarters x four column groups
+constexpr int HALF = 8;                                     // columns per pass through the staging patch
+constexpr int RPP = 32 / HALF;                              // rows per row-segment access
+constexpr int STAGE_BYTES = NUM_EPI_WARPS * 32 * HALF * 8;  // 32 KB
+constexpr int SMEM_BYTES = SMEM_DATA + 256 + STAGE_BYTES + 1024;
+static_assert(SMEM_BYTES <= 227 * 1024, "shared memory of one CTA");
+static_assert(HALF == emu::EC, "the staging patch's swizzle is laid out for eight columns");
+constexpr int NUM_THREADS = 64 + 32 * NUM_EPI_WARPS;
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TBN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+}  // namespace wide
+
+__global__ void __launch_bounds__(wide::NUM_THREADS, 1)
+    chol_update_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                            Params p) {
+  using namespace tc;
+  pdl_trigger();  // the diagonal block's kernel (one CTA) may launch and wait for this one
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + ND * A_PLANE;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + wide::SMEM_DATA);
+  uint64_t* empty = full + 1;
+  uint64_t* gfull = full + 2;     // [NC] group g of the tile is in TMEM
+  uint64_t* gempty = gfull + NC;  // [NC] every epilogue warp has read group g
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gempty + NC);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  double* stage = reinterpret_cast<double*>(smem + wide::SMEM_DATA + 256);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    mbar_init(full, 1);
+    mbar_init(empty, 1);
+    for (int g = 0; g < NC; ++g) {
+      mbar_init(gfull + g, 1);
+      mbar_init(gempty + g, wide::NUM_EPI_WARPS);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  auto give_up = [&]() {
+    *abort_flag = 1;
+    atomicOr(p.status, ST_TIMEOUT);
+  };
+  const int chunk = (p.num_tiles + gridDim.x - 1) / gridDim.x;
+  const int u_lo = min(p.num_tiles, (int)blockIdx.x * chunk), u_hi = min(p.num_tiles, u_lo + chunk);
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t phase = 0;
+      int prev_mb = -1;
+      for (int u = u_lo; u < u_hi && !*abort_flag; ++u) {
+        int mb, bj;
+        get_tile<wide::TBN>(p, u, mb, bj);
+        if (!mbar_wait(empty, phase ^ 1u, abort_flag)) { give_up(); break; }
+        const bool load_a = mb != prev_mb;  // the band's A digit planes stay while the band lasts
+        mbar_expect_tx(full, load_a ? wide::SMEM_DATA : ND * wide::B_PLANE);
+        for (int k = 0; k < ND; ++k) {
+          if (load_a) tma_load_2d(&tmA, full, sA + k * A_PLANE, 0, k * p.m_pad + mb * BM);
+          tma_load_2d(&tmB, full, sB + k * wide::B_PLANE, 0, k * p.m_pad + bj * wide::TBN);
+        }
+        prev_mb = mb;
+        phase ^= 1u;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      uint32_t phase = 0;
+      int it = 0;
+      for (int u = u_lo; u < u_hi && !*abort_flag; ++u, ++it) {
+        if (!mbar_wait(full, phase, abort_flag)) { give_up(); break; }
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+        bool ok = true;
+        for (int c = NC + 1; c >= 2; --c) {
+          const int g = c - 2;
+          // group g's accumulator of the previous tile has been read by the epilogue
+          if (!mbar_wait(gempty + g, (uint32_t)(it & 1) ^ 1u, abort_flag)) { give_up(); ok = false; break; }
+          tc_fence_after();
+          const uint32_t acc = tmem_base + (uint32_t)(g * wide::TBN);
+          uint32_t accumulate = 0;
+          for (int k = max(1, c - ND); k <= min(ND, c - 1); ++k) {
+            const int l = c - k;
+#pragma unroll
+            for (int kk = 0; kk < KD / 16; ++kk) {
+              umma_idesc(acc, sdesc(a0 + (k - 1) * A_PLANE + kk * 32),
+                         sdesc(b0 + (l - 1) * wide::B_PLANE + kk * 32), wide::IDESC, accumulate);
+              accumulate = 1;
+            }
+          }
+          umma_commit(gfull + g);
+        }
+        if (!ok) break;
+        umma_commit(empty);
+        phase ^= 1u;
+      }
+    }
+  } else {
+    // Epilogue warp w >= 2: TMEM lanes [32 (w % 4), 32 (w % 4) + 32) (rows of the tile),
+    // columns [grp 16, grp 16 + 16), grp = (w - 2) / 4. The sixteen columns go through the
+    // warp's 32 x 8 staging patch in two halves; in pass k of a half, lane (h, c) =
+    // (lane / 8, lane % 8) takes row k RPP + h of the warp's 32 rows and column c.
+    const int q = warp & 3, grp = (warp - 2) >> 2;
+    const int r = q * 32 + lane;
+    const int hl = lane / wide::HALF, cl = lane % wide::HALF;
+    double* stg = stage + (warp - 2) * 32 * wide::HALF;
+    int it = 0;
+    for (int u = u_lo; u < u_hi; ++u, ++it) {
+      int mb, bj;
+      get_tile<wide::TBN>(p, u, mb, bj);
+      const int ir = mb * BM + r;
+      const bool row_ok = ir < p.m;
+      const int jc0 = bj * wide::TBN + grp * wide::EC;
+      const int ei = row_ok ? p.rexp[ir] : 0;
+      const uint32_t par = (uint32_t)(it & 1);
+      const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(grp * wide::EC);
+      float hi[wide::EC], lo[wide::EC];
+      bool ok = true;
+      // U_9 .. U_2 as the MMAs deliver them; (hi, lo) <- (hi, lo) 2^-7 + U in double-float
+#pragma unroll 1
+      for (int g = NC - 1; g >= 0; --g) {
+        if (!mbar_wait(gfull + g, par, abort_flag)) { give_up(); ok = false; break; }
+        tc_fence_after();
+        // the sixteen columns as two loads of eight (fewer registers in flight)
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          uint32_t ur[wide::HALF];
+          tmem_ld8_nw(trow + (uint32_t)(g * wide::TBN + hh * wide::HALF), ur);
+          tmem_wait_ld();
+          if (hh == 1) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(gempty + g);
+          }
+#pragma unroll
+          for (int tt = 0; tt < wide::HALF; ++tt) {
+            const int t = hh * wide::HALF + tt;
+            const float uu = __uint_as_float(ur[tt]);
+            if (g == NC - 1) {
+              hi[t] = uu;
+              lo[t] = 0.f;
+            } else {
+              const float h = hi[t] * 0.0078125f, l = lo[t] * 0.0078125f;
+              const float s = h + uu;
+              const float bb = s - h;
+              const float err = (h - (s - bb)) + (uu - bb);
+              const float l2 = l + err;
+              const float hs = s + l2;
+              lo[t] = l2 - (hs - s);
+              hi[t] = hs;
+            }
+          }
+        }
+      }
+      if (!ok) break;
+      const int ir0 = mb * BM + q * 32 + hl;  // this lane's row in pass 0 (pass k: ir0 + k RPP)
+      const size_t row0 = (size_t)(p.b0 + min(ir0, p.m - 1)) * p.D + p.b0;
+      // the targets of a half's passes (no other tile of this launch, and no launch still
+      // running, writes them)
+      auto load_half = [&](int h, double(&av)[wide::HALF]) {
+        const int jc = jc0 + h * wide::HALF + cl;
+        const double* src = p.a + row0 + jc;
+#pragma unroll
+        for (int k = 0; k < wide::HALF; ++k) {
+          const int irk = ir0 + k * wide::RPP;
+          av[k] = (irk < p.m && jc < p.m && jc <= irk) ? src[(size_t)(k * wide::RPP) * p.D] : 0.0;
+        }
+      };
+      double av0[wide::HALF], av1[wide::HALF];
+      // half h of the warp's sixteen columns into the patch; returns what the passes add
+      // to the exponent field of each staged value
+      auto stage_half = [&](const int h) -> long long {
+        const int jc = jc0 + h * wide::HALF + cl;  // this lane's column in the passes
+        const int ejl = jc < p.m ? p.rexp[jc] : 0;
+        // Every partial of (hi, lo) is a multiple of 2^-49 below 2^24 in magnitude. With
+        // moderate exponents (decided for the whole warp) the row's scale 2^(e_i - 14) is
+        // applied here and the column's 2^(e_j) in the passes as an integer added to the
+        // exponent field: every value stays a normal double, so the result equals scaling
+        // by 2^(e_i + e_j - 14) at once.
+        const bool split = __all_sync(0xffffffffu, ei > -386 && ei < 414 && ejl > -400 && ejl < 400);
+        if (split) {
+          const int n = ei - 14;
+#pragma unroll
+          for (int t = 0; t < wide::HALF; ++t)
+            stg[lane * wide::HALF + (t ^ swz(lane))] =
+                f2d_pow2(hi[h * wide::HALF + t], n) + f2d_pow2(lo[h * wide::HALF + t], n);
+        } else {
+#pragma unroll
+          for (int t = 0; t < wide::HALF; ++t) {
+            const int n = ei + __shfl_sync(0xffffffffu, ejl, t) - 14;
+            const float x = hi[h * wide::HALF + t], y = lo[h * wide::HALF + t];
+            const double v =
+                (n > -900 && n < 900) ? f2d_pow2(x, n) + f2d_pow2(y, n) : ((double)x + (double)y) * pow2(n);
+            stg[lane * wide::HALF + (t ^ swz(lane))] = v;
+          }
+        }
+        __syncwarp();
+        return split ? (long long)ejl << 52 : 0ll;
+      };
+      // row-segment passes of half h: target minus staged product
+      auto pass_half = [&](const int h, const double(&av)[wide::HALF], long long eadd) {
+        const int jc = jc0 + h * wide::HALF + cl;
+        // the pass stride, opaque to the compiler so that the row addresses are recomputed
+        // here rather than held in registers since the loads
+        long long pstride;
+        asm volatile("mov.b64 %0, %1;" : "=l"(pstride) : "l"((long long)wide::RPP * p.D));
+        double* dst = p.a + row0 + jc;
+#pragma unroll
+        for (int k = 0; k < wide::HALF; ++k, dst += pstride) {
+          const int rr = k * wide::RPP + hl, irk = ir0 + k * wide::RPP;
+          if (irk < p.m && jc < p.m && jc <= irk) {
+            const long long wb = __double_as_longlong(stg[rr * wide::HALF + (cl ^ swz(rr))]);
+            *dst = av[k] - __longlong_as_double((wb << 1) ? wb + eadd : wb);
+          }
+        }
+        __syncwarp();  // the patch is read before it is written again
+      };
+      // each half's targets load as one batch (eight loads in flight) while its products go
+      // into the patch; the second half's loads wait for the first half's passes, which
+      // keeps the live registers within the 96 of a 576-thread CTA
+      load_half(0, av0);
+      const long long e0 = stage_half(0);
+      pass_half(0, av0, e0);
+      load_half(1, av1);
+      const long long e1 = stage_half(1);
+      pass_half(1, av1, e1);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512) : "memory");
+  }
+}
 }  // namespace emu
 
 bool tc_available() { return tc::encode_fn() != nullptr; }
@@ -1018,8 +1283,20 @@ cudaError_t launch_gram_tc(const void* H, const void* Lo, int ldx, int D, int N,
 cudaError_t launch_chol_update_tc(double* a, int D, int b0, int m, const void* planes, int m_pad, const int* rexp,
                                   int blk_lo, int blk_hi, bool leave_sms, uint32_t* status, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
+  // 128 x 64 tiles (N = 64 MMAs) for updates of two or more 64-column blocks, the
+  // throughput-bound bulk; 128 x 32 tiles for one block column, the look-ahead chain's
+  // latency-bound step, where twice the tiles run side by side. PHI4_CHOL_WIDE=0 keeps
+  // every update in 128 x 32 tiles.
+  static const bool wide_ok = [] {
+    const char* v = getenv("PHI4_CHOL_WIDE");
+    return !(v && atoi(v) == 0);
+  }();
+  const bool whole = blk_hi >= (1 << 20);
+  const bool wide = wide_ok && (whole || blk_hi - blk_lo >= 2);
+  const int tbn = wide ? emu::wide::TBN : emu::BN;
+  const int per_blk = 64 / tbn;  // tile columns per 64-column block
   CUtensorMap ma, mb;
-  if (!tc::make_map(&ma, planes, 64, 8 * m_pad, 64, emu::BM) || !tc::make_map(&mb, planes, 64, 8 * m_pad, 64, emu::BN))
+  if (!tc::make_map(&ma, planes, 64, 8 * m_pad, 64, emu::BM) || !tc::make_map(&mb, planes, 64, 8 * m_pad, 64, tbn))
     return cudaErrorInvalidValue;
   emu::Params p{};
   p.a = a;
@@ -1028,20 +1305,22 @@ cudaError_t launch_chol_update_tc(double* a, int D, int b0, int m, const void* p
   p.m = m;
   p.m_pad = m_pad;
   p.tiles_m = (m + emu::BM - 1) / emu::BM;
-  p.tiles_n = (m + emu::BN - 1) / emu::BN;
-  p.col_lo = blk_lo * emu::BLK_COLS;
-  p.col_hi = blk_hi >= (1 << 20) ? (1 << 30) : blk_hi * emu::BLK_COLS;
+  p.tiles_n = (m + tbn - 1) / tbn;
+  p.col_lo = blk_lo * per_blk;
+  p.col_hi = whole ? (1 << 30) : blk_hi * per_blk;
   int count = 0;
   for (int mm = 0; mm < p.tiles_m; ++mm) {
-    const int hi = std::min(std::min(p.col_hi, p.tiles_n), (mm * emu::BM + emu::BM - 1) / emu::BN + 1);
+    const int hi = std::min(std::min(p.col_hi, p.tiles_n), (mm * emu::BM + emu::BM - 1) / tbn + 1);
     count += std::max(0, hi - p.col_lo);
   }
   p.num_tiles = count;
   p.rexp = rexp;
   p.status = status;
   if (p.num_tiles == 0) return cudaSuccess;
-  cudaError_t e =
-      cudaFuncSetAttribute(emu::chol_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, emu::SMEM_BYTES);
+  cudaError_t e = wide ? cudaFuncSetAttribute(emu::chol_update_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              emu::wide::SMEM_BYTES)
+                       : cudaFuncSetAttribute(emu::chol_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              emu::SMEM_BYTES);
   if (e != cudaSuccess) return e;
   // the bulk of the update may leave a few SMs to the look-ahead chain (diagonal
   // block, inverse, panel solve, next block columns), which would otherwise wait for
@@ -1052,7 +1331,10 @@ cudaError_t launch_chol_update_tc(double* a, int D, int b0, int m, const void* p
   }();
   const int avail = leave_sms ? std::max(1, sm_count() - reserve) : sm_count();
   const int grid = std::min(avail, p.num_tiles);
-  emu::chol_update_kernel<<<grid, emu::NUM_THREADS, emu::SMEM_BYTES, s>>>(ma, mb, p);
+  if (wide)
+    emu::chol_update_wide_kernel<<<grid, emu::wide::NUM_THREADS, emu::wide::SMEM_BYTES, s>>>(ma, mb, p);
+  else
+    emu::chol_update_kernel<<<grid, emu::NUM_THREADS, emu::SMEM_BYTES, s>>>(ma, mb, p);
   return cudaGetLastError();
 }
 
