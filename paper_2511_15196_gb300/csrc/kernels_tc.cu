@@ -635,11 +635,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 // groups weigh < 2^-47 of sum |x||y|, like the rounding of a length-64 FP64 dot
 // product); U_9 .. U_2 are combined by a Horner pass in double-float (two fp32)
 // and the result, scaled by 2^(e_i + e_j - 14), is subtracted in FP64.
-// Tiles of 128 rows x 32 columns of the lower trailing matrix (two tiles' group
+// A launch covers the 64-column blocks [blk_lo, blk_hi) of the lower trailing matrix,
+// each CTA a contiguous run of its tile list, so that the 128 KB of A digit planes are
+// loaded once per 128-row band rather than once per tile. Two tile forms with the same
+// arithmetic per element: 128 x 32 tiles (chol_update_kernel; two tiles' group
 // accumulators fit in TMEM, so the MMAs of one tile overlap the epilogue of the
-// previous one); a launch covers the 64-column blocks [blk_lo, blk_hi) of the
-// trailing matrix, each CTA a contiguous run of its tile list, so that the 128 KB of
-// A digit planes are loaded once per 128-row band rather than once per tile.
+// previous one) for a single block column, and 128 x 64 tiles (chol_update_wide_kernel;
+// N = 64 MMAs, half the shared-memory operand reads per product, the accumulators
+// handed to the epilogue group by group) for the bulk of a panel's update.
 namespace emu {
 constexpr int BM = 128, BN = 32, KD = 64, ND = 8, NC = 8;
 constexpr int A_PLANE = BM * KD * 2;
